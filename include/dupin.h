@@ -1,0 +1,228 @@
+/*
+ * dupin.h -- C ABI of the GB300 batch-peeling library (libdupin.so).
+ *
+ * The library finds dense subgraphs by Dupin's parallel batch peeling
+ * (arXiv 2504.09311, Algorithm 2, Sec. 4.1) on one NVIDIA GB300 (sm_103a):
+ * every round removes all live vertices whose peeling weight is at most
+ * k(1+eps) times the current density and keeps the densest prefix.
+ *
+ * Definitions (Sec. 2.1, Eq. 1 and Sec. 2.2):
+ *   f(S)    = sum_{u in S} a_u + sum_{(u,v) in E[S]} c_uv
+ *   g(S)    = f(S) / |S|
+ *   w_u(S)  = a_u + sum_{v in N(u) cap S} c_uv   (the drop of f when u leaves S)
+ * Metrics (Sec. 2.1): DUPIN_DG uses a = 0, c = 1 (supplied weights ignored);
+ * DUPIN_DW and DUPIN_FD use the supplied a and c (FD's c_e = 1/log(x + 5)
+ * with x the object vertex's degree is computed by the caller, as the
+ * paper's ESusp plug-in does in Listing 1).
+ *
+ * Numbers: every weight is Q32.32 fixed point in an int64 (value * 2^32),
+ * non-negative (Property 3.1).  f is kept exactly in 128 bits.  The round
+ * threshold is the exact integer floor(k (D+N) f / (D |S|)) for eps = N/D,
+ * so the per-round removal sets, the density trace and the best subgraph are
+ * fully determined and reproducible bit for bit.
+ *
+ * Readings of points the paper leaves open:
+ *   - k = k_mult (Algorithm 2 uses k = 2 for DG/DW/FD; k_mult = 1 gives the
+ *     (1+eps) g threshold).  If a round's threshold selects no vertex (only
+ *     possible when k(1+eps) < 2), every live vertex of minimum peeling
+ *     weight is removed instead, which keeps Thm 4.3's 2(1+eps) bound.
+ *   - Candidates for the best set are S_0 .. S_{R-1} (non-empty); ties keep
+ *     the earliest round (Algorithm 1's strict ">").
+ *   - DUPIN_GPO adds Algorithm 3's global threshold tau_max.
+ *
+ * Conventions for every function:
+ *   - returns DUPIN_OK (0) or a negative DUPIN_ERR_* code and never throws;
+ *     dupin_last_error() gives the calling thread's last message;
+ *   - 'stream' is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream); work is ordered on it;
+ *   - host pointers are read (or written) only during the call; the library
+ *     never keeps a caller pointer after returning.
+ */
+#ifndef DUPIN_H
+#define DUPIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define DUPIN_OK 0
+#define DUPIN_ERR_INVALID_ARG -1    /* bad CSR, id out of range, negative weight, bad eps/k */
+#define DUPIN_ERR_OVERFLOW -2       /* some initial peeling weight does not fit in int64 */
+#define DUPIN_ERR_OOM -3            /* device memory exhausted (or serving budget) */
+#define DUPIN_ERR_BUFFER_TOO_SMALL -4 /* trace_cap < n_rounds + 1 (n_rounds still filled) */
+#define DUPIN_ERR_NO_PROGRESS -5    /* max_rounds reached before S became empty */
+#define DUPIN_ERR_CUDA -6           /* CUDA runtime error; message has the CUDA text */
+#define DUPIN_ERR_TIMEOUT -7        /* an in-kernel wait hit its iteration limit */
+#define DUPIN_ERR_NOT_FOUND -8      /* unknown serving ticket */
+
+/* ----------------------------------------------------------------- metrics */
+#define DUPIN_DG 0
+#define DUPIN_DW 1
+#define DUPIN_FD 2
+
+/* --------------------------------------------------------- graph loading */
+
+/* dupin_graph_desc.flags */
+#define DUPIN_DEVICE_PTRS 1u /* the arrays below are device pointers (still copied) */
+
+typedef struct dupin_graph dupin_graph;
+
+/*
+ * A graph is given in one of two forms (Sec. 2.1: V, E, a_i, c_ij):
+ *
+ *  (a) bipartite users x items: n_left users, n_right > 0 items.  The CSR
+ *      (csr_ptr[n_left+1], csr_idx[m] item ids in [0, n_right), csr_w[m])
+ *      lists each user's items; the CSC (csc_ptr[n_right+1], csc_idx[m] user
+ *      ids in [0, n_left), csc_w[m]) lists each item's users and must hold
+ *      the same edge set with the same weights.  Vertex ids of the result are
+ *      users [0, n_left) then items [n_left, n_left + n_right).
+ *  (b) general undirected: n_right = 0, csr_* is a symmetric CSR over
+ *      n_left vertices (each edge in both rows, equal weights), csc_* NULL.
+ *
+ * csr_w / csc_w may be NULL (all c = 1.0); vertex_w (length n) may be NULL
+ * (all a = 0).  The edge set must be simple: no self-loops, no repeated
+ * pairs.  Offsets are int64 and start at 0; ids are int32.
+ */
+typedef struct {
+    int64_t n_left, n_right;
+    const int64_t *csr_ptr;
+    const int32_t *csr_idx;
+    const int64_t *csr_w;
+    const int64_t *csc_ptr;
+    const int32_t *csc_idx;
+    const int64_t *csc_w;
+    const int64_t *vertex_w;
+    uint32_t flags;
+} dupin_graph_desc;
+
+/*
+ * Copy a graph to the current CUDA device as one symmetric adjacency
+ * (int64 row offsets, int32 neighbour ids, int64 Q32.32 arc weights) and
+ * validate it (offsets monotone, ids in range, weights >= 0, every initial
+ * peeling weight a_u + sum_v c_uv < 2^63).  On success *out owns the device
+ * copy until dupin_graph_free.  Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
+ * Synchronises 'stream'.
+ */
+int dupin_graph_load(const dupin_graph_desc *desc, void *stream, dupin_graph **out);
+
+/* Release a graph and its cached peeling workspace.  NULL is accepted. */
+int dupin_graph_free(dupin_graph *g);
+
+/* n = vertices, m = undirected edges, arcs = 2m, device_bytes = bytes held. */
+int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs, int64_t *device_bytes);
+
+/* ----------------------------------------------------------------- peeling */
+
+/* dupin_params.flags */
+#define DUPIN_GPO 1u           /* Algorithm 3: global threshold tau_max (Sec. 5.1) */
+#define DUPIN_RESULT_DEVICE 8u /* best_mask / peel_round / trace_* are device pointers */
+
+typedef struct {
+    int32_t metric;     /* DUPIN_DG, DUPIN_DW or DUPIN_FD */
+    int32_t k_mult;     /* k of Algorithm 2, 1..64 (2 is the paper's value for DG/DW/FD) */
+    int64_t eps_num;    /* eps = eps_num / eps_den, eps_num >= 0 */
+    int64_t eps_den;    /* 1 .. 2^24 */
+    int64_t max_rounds; /* <= 0: n + 1 */
+    uint32_t flags;
+    int32_t tail_cap;   /* <= 0: automatic; else live-set size below which one CTA finishes */
+} dupin_params;
+
+/*
+ * Result of one peel.  Arrays are caller-owned (host memory, or device
+ * memory with DUPIN_RESULT_DEVICE); each may be NULL.
+ *   best_mask[n]   1 for the vertices of the densest prefix S_best
+ *   peel_round[n]  round (1..n_rounds) in which each vertex was removed
+ *   trace_*[i]     for i = 0..n_rounds: f(S_i) as (hi, lo) words, |S_i|,
+ *                  |U_i| (vertices removed in round i; 0 for i = 0)
+ * Scalars (always host): n_rounds R, best_round b (S_b = {u : peel_round[u]
+ * > b}), |S_b|, f(S_b) as (hi, lo), g(S_b) as a double (value, not Q32.32),
+ * and how many rounds used the minimum-weight rule.
+ */
+typedef struct {
+    uint8_t *best_mask;
+    int32_t *peel_round;
+    int64_t *trace_f_hi;
+    uint64_t *trace_f_lo;
+    int64_t *trace_size;
+    int64_t *trace_peeled;
+    int64_t trace_cap;
+    int64_t n_rounds;
+    int64_t best_round;
+    int64_t best_size;
+    int64_t best_f_hi;
+    uint64_t best_f_lo;
+    double best_density;
+    int64_t n_min_rule;
+} dupin_result;
+
+/*
+ * Algorithm 2 (Sec. 4.1) on a loaded graph: rounds i = 1, 2, ... remove
+ * U_i = {u in S_{i-1} : w_u(S_{i-1}) <= T_i} (minimum rule if empty) until S
+ * is empty; the result names the densest S_i.  Runs on 'stream' and returns
+ * when the result is complete.  Errors: INVALID_ARG (params), NO_PROGRESS
+ * (max_rounds), BUFFER_TOO_SMALL (trace_cap < n_rounds + 1 with a non-NULL
+ * trace; everything else is still filled), OOM, TIMEOUT, CUDA.
+ */
+int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result, void *stream);
+
+/*
+ * Peel 'count' independent graphs in few launches (one persistent launch
+ * for all graphs small enough for one CTA, the single-graph path for the
+ * rest).  params and results are arrays of length count; results are
+ * identical to 'count' separate dupin_peel calls.  A graph may appear more
+ * than once.  Errors as dupin_peel; the first failing index is named in
+ * the message.
+ */
+int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
+                     int64_t count, void *stream);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct dupin_server dupin_server;
+
+typedef struct {
+    int64_t memory_budget; /* device bytes the server may hold for per-request state (> 0) */
+    int32_t max_slots;     /* requests on the device at once, 1..4096 */
+    int32_t device;        /* CUDA device ordinal */
+} dupin_serve_config;
+
+typedef struct {
+    int64_t submitted, completed, rejected, in_flight, queued;
+    double p50_ms, p99_ms;   /* submit -> completion latency over completed requests */
+    double graphs_per_s;     /* completed / (last completion - first submit) */
+} dupin_serve_stats;
+
+/*
+ * Continuous-batching server over resident graphs.  submit() queues a peel
+ * of 'graph' (which must stay loaded until the ticket completes) and returns
+ * at once with a ticket; a worker thread admits queued requests into free
+ * slots while the device-memory budget allows, launches them alongside the
+ * requests already running, and writes each result into the caller's
+ * 'result' (host arrays) when it completes.  poll() reports completion,
+ * wait() blocks until it.  Results equal dupin_peel's exactly.
+ */
+int dupin_serve_create(const dupin_serve_config *cfg, dupin_server **out);
+int dupin_serve_submit(dupin_server *s, dupin_graph *graph, const dupin_params *params, dupin_result *result,
+                       uint64_t *ticket);
+int dupin_serve_poll(dupin_server *s, uint64_t ticket, int *done, int *status);
+int dupin_serve_wait(dupin_server *s, uint64_t ticket, int *status);
+int dupin_serve_stats(dupin_server *s, dupin_serve_stats *out);
+int dupin_serve_destroy(dupin_server *s);
+
+/* ------------------------------------------------------------------- misc */
+
+/* Copy the calling thread's last error message (NUL-terminated) into buf. */
+int dupin_last_error(char *buf, size_t cap);
+
+/* Library version as "major.minor.patch". */
+const char *dupin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUPIN_H */
