@@ -120,6 +120,7 @@ int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs
 /* dupin_params.flags */
 #define DUPIN_GPO 1u           /* Algorithm 3: global threshold tau_max (Sec. 5.1) */
 #define DUPIN_RESULT_DEVICE 8u /* best_mask / peel_round / trace_* are device pointers */
+#define DUPIN_TIMING 16u       /* fill the phase_ms[] durations (CUDA events on 'stream') */
 
 typedef struct {
     int32_t metric;     /* DUPIN_DG, DUPIN_DW or DUPIN_FD */
@@ -140,7 +141,10 @@ typedef struct {
  *                  |U_i| (vertices removed in round i; 0 for i = 0)
  * Scalars (always host): n_rounds R, best_round b (S_b = {u : peel_round[u]
  * > b}), |S_b|, f(S_b) as (hi, lo), g(S_b) as a double (value, not Q32.32),
- * and how many rounds used the minimum-weight rule.
+ * how many rounds used the minimum-weight rule, how many rounds ran in the
+ * grid-wide kernel (the rest ran in the one-CTA tail), and with DUPIN_TIMING
+ * the device time of each phase: [0] initial weights, [1] grid-wide rounds,
+ * [2] tail sub-graph build, [3] one-CTA rounds.
  */
 typedef struct {
     uint8_t *best_mask;
@@ -157,6 +161,8 @@ typedef struct {
     uint64_t best_f_lo;
     double best_density;
     int64_t n_min_rule;
+    int64_t n_bulk_rounds;
+    float phase_ms[4];
 } dupin_result;
 
 /*
@@ -194,7 +200,7 @@ typedef struct {
     int64_t submitted, completed, rejected, in_flight, queued;
     double p50_ms, p99_ms;   /* submit -> completion latency over completed requests */
     double graphs_per_s;     /* completed / (last completion - first submit) */
-} dupin_serve_stats;
+} dupin_serve_stats_t;
 
 /*
  * Continuous-batching server over resident graphs.  submit() queues a peel
@@ -210,7 +216,7 @@ int dupin_serve_submit(dupin_server *s, dupin_graph *graph, const dupin_params *
                        uint64_t *ticket);
 int dupin_serve_poll(dupin_server *s, uint64_t ticket, int *done, int *status);
 int dupin_serve_wait(dupin_server *s, uint64_t ticket, int *status);
-int dupin_serve_stats(dupin_server *s, dupin_serve_stats *out);
+int dupin_serve_stats(dupin_server *s, dupin_serve_stats_t *out);
 int dupin_serve_destroy(dupin_server *s);
 
 /* ------------------------------------------------------------------- misc */

@@ -1,0 +1,243 @@
+// dupin_common.cuh -- shared device/host definitions of libdupin (sm_103a).
+//
+// Data layout in HBM (one symmetric adjacency per graph, Sec. 2.1):
+//   rp[n+1]  int64  row offsets          col[A] int32 neighbour ids
+//   cw[A]    int64  Q32.32 arc weights (absent for DG: every arc weighs 1.0)
+//   a[n]     int64  Q32.32 vertex weights (absent: 0)
+// Peeling state (Algorithm 2, Sec. 4.1):
+//   w[n]  int64  current peeling weight w_u(S)      pr[n] int32 round u left S
+//   live lists (int32 ids), per-block staging, the round's frontier and the
+//   per-round trace.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dupin.h"
+
+typedef unsigned __int128 u128;
+
+#define DUPIN_Q_ONE (1LL << 32)
+#define DUPIN_LIVE 0x7fffffff
+
+// In-kernel waits give up after this many polls (about a second with the
+// back-off below) and report DUPIN_ERR_TIMEOUT instead of hanging.
+#define DUPIN_SPIN_LIMIT (1ll << 22)
+
+// Peeling phases recorded in PeelCtl::status
+#define ST_RUNNING 0
+#define ST_DONE 1
+#define ST_TAIL 2
+
+// Device-resident control block of one peel.  'bar_*' is the grid barrier;
+// the rest is the state after the last completed round.
+struct PeelCtl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int error;
+    int status;
+    long long round;
+    long long size;
+    unsigned long long f_lo, f_hi;
+    long long live_len;
+    int live_sel;
+    int pad0;
+    long long minw;
+    long long best_round, best_size;
+    unsigned long long bf_lo, bf_hi;
+    long long gpo_le;
+    long long n_min_rule;
+    long long scan_volume;
+    long long bulk_rounds;
+    unsigned long long init_lo, init_hi;  // sum over u of (w_u + a_u) = 2 f(V)
+    long long init_min;
+    int init_overflow;
+    int pad1;
+};
+
+// Per-block partial results of one bulk round (one 128-byte line each)
+struct BlockPart {
+    long long sel_cnt;    // vertices selected
+    long long stage_cnt;  // selected vertices with at least one arc (frontier entries)
+    long long sel_deg;    // their arcs
+    unsigned long long ws_lo, ws_hi;  // sum of their peeling weights
+    long long surv_cnt;   // live survivors in the block's range
+    long long min_surv;   // minimum survivor weight
+    unsigned long long in_lo, in_hi;  // expand: sum of c over arcs inside U
+    long long min_dec;    // expand: minimum weight after a decrement
+    long long pad[6];
+};
+
+struct DevGraph {
+    long long n;
+    long long arcs;
+    const long long *rp;
+    const int *col;
+    const long long *cw;  // nullptr: DG weights
+    const long long *a;   // nullptr: 0
+};
+
+struct PeelArgs {
+    DevGraph g;
+    long long *w;
+    int *pr;
+    int *live0, *live1;
+    int *stage_id;
+    long long *stage_start, *stage_off;
+    long long *fstart, *fbase;
+    long long *cstart;
+    BlockPart *part;
+    PeelCtl *ctl;
+    long long *tr_f_hi;
+    unsigned long long *tr_f_lo;
+    long long *tr_size, *tr_peeled;
+    long long tr_cap;
+    long long kD;       // k (D + N)
+    long long D;        // eps denominator
+    int use_min;        // k (1 + eps) < 2: the minimum rule can fire
+    int gpo;            // Algorithm 3
+    long long max_rounds;
+    long long tail_cap;
+    // tail sub-graph
+    int *loc;           // global id -> local id (valid for live vertices)
+    long long *tdeg;    // tail: full degree prefix [L+1]
+    long long *tlrp;    // tail: live-degree prefix [L+1]
+    int *tcnt;          // tail: per-row live-arc counts [L]
+    int *tfill;         // tail: per-row fill counters [L]
+    int *tcol;          // tail arcs: local neighbour ids
+    long long *tcw;     // tail arcs: weights (nullptr for DG)
+    long long tarc_cap;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__host__ __device__ __forceinline__ u128 mk128(unsigned long long lo, unsigned long long hi) {
+    return ((u128)hi << 64) | (u128)lo;
+}
+
+// exact threshold floor(num_mul * f / (den_mul * size)), saturated to INT64_MAX
+__device__ __forceinline__ long long floor_ratio(unsigned long long num_mul, u128 f, unsigned long long den_mul,
+                                                 long long size) {
+    u128 num = (u128)num_mul * f;
+    u128 den = (u128)den_mul * (u128)(unsigned long long)size;
+    u128 q = num / den;
+    if (q > (u128)0x7fffffffffffffffULL) return 0x7fffffffffffffffLL;
+    return (long long)q;
+}
+
+// a/b > c/d for the best-prefix rule (strict: earliest round wins ties)
+__device__ __forceinline__ bool frac_gt(u128 a, long long b, u128 c, long long d) {
+    return a * (u128)(unsigned long long)d > c * (u128)(unsigned long long)b;
+}
+
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long xlo,
+                                       unsigned long long xhi) {
+    unsigned long long s = lo + xlo;
+    hi += xhi + (s < lo ? 1ull : 0ull);
+    lo = s;
+}
+
+__device__ __forceinline__ void warp_sum128(unsigned long long &lo, unsigned long long &hi) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        unsigned long long olo = __shfl_down_sync(0xffffffffu, lo, d);
+        unsigned long long ohi = __shfl_down_sync(0xffffffffu, hi, d);
+        add128(lo, hi, olo, ohi);
+    }
+}
+
+__device__ __forceinline__ long long warp_sum64(long long x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
+    return x;
+}
+
+__device__ __forceinline__ long long warp_min64(long long x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        long long o = __shfl_down_sync(0xffffffffu, x, d);
+        x = o < x ? o : x;
+    }
+    return x;
+}
+
+// inclusive warp scan of a 64-bit value
+__device__ __forceinline__ long long warp_incl_scan64(long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long o = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += o;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void set_error(PeelCtl *ctl, int code) { atomicCAS(&ctl->error, 0, code); }
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p) {
+    return *(volatile const unsigned *)p;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
+
+// Grid-wide barrier for a cooperative launch (every block resident).
+// Sense is a generation counter read before arriving; the last block to
+// arrive resets the count and advances the generation.  Waiting is bounded:
+// after DUPIN_SPIN_LIMIT polls the block records DUPIN_ERR_TIMEOUT and every
+// block leaves at its next barrier.  Returns false when the peel must stop.
+__device__ __forceinline__ bool grid_barrier(PeelCtl *ctl, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned gen = ld_volatile_u32(&ctl->bar_gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (ld_volatile_u32(&ctl->bar_gen) == gen) {
+                if (++it > DUPIN_SPIN_LIMIT) {
+                    set_error(ctl, DUPIN_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (it > 64) __nanosleep(it > 4096 ? 256 : 32);
+            }
+        }
+        __threadfence();
+        s_ok = ok && ld_volatile_i32(&ctl->error) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Largest k in [0, U] with base[k] <= x, for non-decreasing base with
+// base[0] <= x.  One warp, 32 probes per step (log_32 U dependent loads).
+__device__ __forceinline__ long long warp_search_last_le(const long long *base, long long U, long long x) {
+    const int lane = threadIdx.x & 31;
+    long long lo = 0, hi = U;
+    while (lo < hi) {
+        long long span = hi - lo;  // candidates lo+1 .. hi
+        long long p;
+        if (span <= 32) p = lo + 1 + lane;
+        else p = lo + 1 + (long long)(((u128)(span - 1) * (unsigned)lane) / 31u);
+        bool valid = p <= hi;
+        bool le = valid && base[p] <= x;
+        unsigned m = __ballot_sync(0xffffffffu, le);
+        if (m == 0) {
+            long long p0 = __shfl_sync(0xffffffffu, p, 0);
+            hi = p0 - 1;
+        } else {
+            int L = 31 - __clz(m);
+            long long pl = __shfl_sync(0xffffffffu, p, L);
+            long long pn = __shfl_sync(0xffffffffu, p, L < 31 ? L + 1 : 31);
+            bool nvalid = __shfl_sync(0xffffffffu, (int)valid, L < 31 ? L + 1 : 31);
+            lo = pl;
+            if (L < 31 && nvalid) hi = pn - 1;
+        }
+    }
+    return lo;
+}

@@ -1,0 +1,84 @@
+// dupin_internal.h -- host-side internals of libdupin shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dupin.h"
+#include "dupin_common.cuh"
+
+// error text for the calling thread (dupin_last_error)
+void dupin_set_error(const std::string &msg);
+int dupin_fail(int code, const std::string &msg);
+// CUDA error -> DUPIN_ERR_CUDA with the runtime's text
+int dupin_cuda_fail(cudaError_t e, const char *what);
+
+#define DUPIN_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return dupin_cuda_fail(_e, #expr); \
+    } while (0)
+
+// Per-graph peeling workspace (device memory), allocated on first use and
+// reused by later peels of the same graph.
+struct PeelWorkspace {
+    long long n = 0, arcs = 0, tail_cap = 0, tr_cap = 0, tarc_cap = 0;
+    int grid = 0;  // blocks of the persistent kernel
+    long long *w = nullptr;
+    int *pr = nullptr;
+    int *live0 = nullptr, *live1 = nullptr;
+    int *stage_id = nullptr;
+    long long *stage_start = nullptr, *stage_off = nullptr;
+    long long *fstart = nullptr, *fbase = nullptr;
+    long long *cstart = nullptr;
+    BlockPart *part = nullptr;
+    PeelCtl *ctl = nullptr;
+    long long *tr_f_hi = nullptr;
+    unsigned long long *tr_f_lo = nullptr;
+    long long *tr_size = nullptr, *tr_peeled = nullptr;
+    int *loc = nullptr;
+    long long *tdeg = nullptr, *tlrp = nullptr;
+    int *tcnt = nullptr, *tfill = nullptr;
+    int *tcol = nullptr;
+    long long *tcw = nullptr;
+    uint8_t *mask = nullptr;
+    bool async = false;  // allocated with cudaMallocAsync (freed with cudaFreeAsync)
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // DUPIN_TIMING
+    long long bytes = 0;
+};
+
+struct dupin_graph {
+    int device = 0;
+    long long n_left = 0, n_right = 0, n = 0, m = 0, arcs = 0;
+    long long *rp = nullptr;
+    int *col = nullptr;
+    long long *cw = nullptr;
+    long long *a = nullptr;
+    long long bytes = 0;
+    PeelWorkspace *ws = nullptr;
+};
+
+DevGraph dev_graph(const dupin_graph *g, int metric);
+long long workspace_bytes(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap, int grid);
+PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap,
+                                bool async, cudaStream_t s, int *rc);
+void workspace_free(PeelWorkspace *ws);
+void workspace_free(PeelWorkspace *ws, cudaStream_t s);
+int workspace_ensure(dupin_graph *g, long long tail_cap, long long tr_cap);
+
+// the three steps of dupin_peel: caps from params, kernels on a stream, results
+int peel_resolve(const dupin_graph *g, const dupin_params *p, long long *tail_cap, long long *max_rounds,
+                 long long *tr_cap);
+int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, long long tail_cap,
+                 long long max_rounds, cudaStream_t s);
+int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, dupin_result *r, cudaStream_t s);
+
+// kernels shared by loading and peeling
+int launch_init_weights(const DevGraph &dg, int metric, long long *w, int *pr, int *live0, PeelCtl *ctl,
+                        bool check, cudaStream_t s);
+
+// the largest live set the single-CTA tail accepts, and the default cap
+long long tail_cap_limit();
+long long tail_cap_default();
+int peel_grid_size();

@@ -1,0 +1,253 @@
+// graph.cu -- loading a graph into HBM as one symmetric adjacency.
+//
+// Input forms (Sec. 2.1): a bipartite users x items graph as CSR (users ->
+// items) plus CSC (items -> users), or a general undirected graph as a
+// symmetric CSR.  The device copy is always one CSR over n = users + items
+// vertices: rows [0, n_left) are users whose neighbour ids are shifted by
+// n_left (items become vertices n_left + i), rows [n_left, n) are items.
+// Validation runs on the device: offsets monotone and starting at 0, ids in
+// range, no self-loops, weights >= 0 (Property 3.1), and every initial
+// peeling weight a_u + sum_v c_uv below 2^63 (checked with the same
+// segmented-sum kernel the peel uses).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string.h>
+
+#include <string>
+
+#include "dupin_internal.h"
+
+__global__ void k_add_offset_i64(long long *x, long long n, long long add) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += add;
+}
+
+__global__ void k_add_offset_i32(int *x, long long n, int add, int limit, int *bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int v = x[i];
+        if (v < 0 || v >= limit) atomicExch(bad, 1);
+        x[i] = v + add;
+    }
+}
+
+// offsets: rp[0] == 0, non-decreasing, rp[n] == arcs
+__global__ void k_check_offsets(const long long *rp, long long n, long long arcs, int *bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (rp[i] > rp[i + 1]) atomicExch(bad, 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != arcs)) atomicExch(bad, 1);
+}
+
+__global__ void k_fill_i64(long long *x, long long n, long long v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+__global__ void k_check_nonneg(const long long *x, long long n, int *bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (x[i] < 0) atomicExch(bad, 1);
+}
+
+static cudaMemcpyKind kind_of(bool dev) { return dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+
+static int read_last(const int64_t *p, long long idx, bool dev, long long *out) {
+    if (!p) return dupin_fail(DUPIN_ERR_INVALID_ARG, "offset array is NULL");
+    if (dev) {
+        cudaError_t e = cudaMemcpy(out, p + idx, sizeof(long long), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return dupin_cuda_fail(e, "reading an offset");
+    } else {
+        *out = p[idx];
+    }
+    return DUPIN_OK;
+}
+
+static void graph_release(dupin_graph *g) {
+    if (!g) return;
+    workspace_free(g->ws);
+    cudaFree(g->rp);
+    cudaFree(g->col);
+    cudaFree(g->cw);
+    cudaFree(g->a);
+    delete g;
+}
+
+extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_graph **out) {
+    if (!d || !out) return dupin_fail(DUPIN_ERR_INVALID_ARG, "desc or out is NULL");
+    *out = nullptr;
+    const bool dev = (d->flags & DUPIN_DEVICE_PTRS) != 0;
+    if (d->flags & ~DUPIN_DEVICE_PTRS) return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown graph flag");
+    const long long nL = d->n_left, nR = d->n_right;
+    if (nL < 0 || nR < 0 || nL + nR > 0x7ffffffeLL)
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "vertex counts must be >= 0 and n < 2^31 - 1");
+    const bool bip = nR > 0;
+    if (!d->csr_ptr || (!d->csr_idx && nL > 0)) return dupin_fail(DUPIN_ERR_INVALID_ARG, "csr_ptr / csr_idx missing");
+    if (bip && (!d->csc_ptr || !d->csc_idx)) return dupin_fail(DUPIN_ERR_INVALID_ARG, "bipartite graph needs csc_*");
+    if (bip && ((d->csr_w == nullptr) != (d->csc_w == nullptr)))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "csr_w and csc_w must both be given or both be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    long long m_csr = 0, m_csc = 0;
+    if ((rc = read_last(d->csr_ptr, nL, dev, &m_csr))) return rc;
+    if (bip && (rc = read_last(d->csc_ptr, nR, dev, &m_csc))) return rc;
+    if (m_csr < 0 || (bip && m_csc != m_csr))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "CSR and CSC hold different edge counts");
+    const long long n = nL + nR;
+    const long long arcs = bip ? 2 * m_csr : m_csr;
+    if (!bip && (arcs & 1)) return dupin_fail(DUPIN_ERR_INVALID_ARG, "a symmetric CSR has an even number of arcs");
+
+    dupin_graph *g = new dupin_graph();
+    cudaGetDevice(&g->device);
+    g->n_left = nL;
+    g->n_right = nR;
+    g->n = n;
+    g->arcs = arcs;
+    g->m = arcs / 2;
+    const bool has_w = d->csr_w != nullptr;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(p, bytes ? bytes : 8);
+        if (e == cudaSuccess) g->bytes += (long long)bytes;
+    };
+    alloc((void **)&g->rp, sizeof(long long) * (size_t)(n + 1));
+    alloc((void **)&g->col, sizeof(int) * (size_t)arcs);
+    if (has_w) alloc((void **)&g->cw, sizeof(long long) * (size_t)arcs);
+    if (d->vertex_w) alloc((void **)&g->a, sizeof(long long) * (size_t)n);
+    int *bad = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&bad, sizeof(int));
+    if (e != cudaSuccess) {
+        graph_release(g);
+        cudaFree(bad);
+        cudaGetLastError();
+        return dupin_fail(e == cudaErrorMemoryAllocation ? DUPIN_ERR_OOM : DUPIN_ERR_CUDA,
+                          std::string("graph allocation: ") + cudaGetErrorString(e));
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    const int grid = sms * 4;
+    const cudaMemcpyKind k = kind_of(dev);
+#define TRY(expr)                                    \
+    do {                                             \
+        cudaError_t _e = (expr);                     \
+        if (_e != cudaSuccess) {                     \
+            int _r = dupin_cuda_fail(_e, #expr);     \
+            graph_release(g);                        \
+            cudaFree(bad);                           \
+            return _r;                               \
+        }                                            \
+    } while (0)
+    TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    const long long m = m_csr;
+    if (bip) {
+        TRY(cudaMemcpyAsync(g->rp, d->csr_ptr, sizeof(long long) * (size_t)(nL + 1), k, s));
+        // item rows: csc_ptr[1..nR] + m
+        TRY(cudaMemcpyAsync(g->rp + nL + 1, d->csc_ptr + 1, sizeof(long long) * (size_t)nR, k, s));
+        k_add_offset_i64<<<grid, 256, 0, s>>>(g->rp + nL + 1, nR, m);
+        if (m > 0) {
+            TRY(cudaMemcpyAsync(g->col, d->csr_idx, sizeof(int) * (size_t)m, k, s));
+            TRY(cudaMemcpyAsync(g->col + m, d->csc_idx, sizeof(int) * (size_t)m, k, s));
+            k_add_offset_i32<<<grid, 256, 0, s>>>(g->col, m, (int)nL, (int)nR, bad);   // items -> global ids
+            k_add_offset_i32<<<grid, 256, 0, s>>>(g->col + m, m, 0, (int)nL, bad);     // users stay
+            if (has_w) {
+                TRY(cudaMemcpyAsync(g->cw, d->csr_w, sizeof(long long) * (size_t)m, k, s));
+                TRY(cudaMemcpyAsync(g->cw + m, d->csc_w, sizeof(long long) * (size_t)m, k, s));
+            }
+        }
+        // csc_ptr must itself start at 0
+        long long c0 = 0;
+        if (dev) TRY(cudaMemcpy(&c0, d->csc_ptr, sizeof(long long), cudaMemcpyDeviceToHost));
+        else c0 = d->csc_ptr[0];
+        if (c0 != 0) {
+            graph_release(g);
+            cudaFree(bad);
+            return dupin_fail(DUPIN_ERR_INVALID_ARG, "csc_ptr[0] must be 0");
+        }
+    } else {
+        TRY(cudaMemcpyAsync(g->rp, d->csr_ptr, sizeof(long long) * (size_t)(n + 1), k, s));
+        if (arcs > 0) {
+            TRY(cudaMemcpyAsync(g->col, d->csr_idx, sizeof(int) * (size_t)arcs, k, s));
+            if (has_w) TRY(cudaMemcpyAsync(g->cw, d->csr_w, sizeof(long long) * (size_t)arcs, k, s));
+        }
+    }
+    if (d->vertex_w) TRY(cudaMemcpyAsync(g->a, d->vertex_w, sizeof(long long) * (size_t)n, k, s));
+    k_check_offsets<<<grid, 256, 0, s>>>(g->rp, n, arcs, bad);
+    if (has_w) k_check_nonneg<<<grid, 256, 0, s>>>(g->cw, arcs, bad);
+    if (g->a) k_check_nonneg<<<grid, 256, 0, s>>>(g->a, n, bad);
+    int hbad = 0;
+    TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (hbad) {
+        graph_release(g);
+        cudaFree(bad);
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "invalid CSR: offsets, ids or weights out of range");
+    }
+    // ids in range, no self-loops, and w_u(V) < 2^63 for the weights given
+    {
+        long long *w = nullptr;
+        PeelCtl *ctl = nullptr;
+        TRY(cudaMalloc((void **)&w, sizeof(long long) * (size_t)(n > 0 ? n : 1)));
+        e = cudaMalloc((void **)&ctl, sizeof(PeelCtl));
+        if (e != cudaSuccess) {
+            cudaFree(w);
+            TRY(e);
+        }
+        PeelCtl hc;
+        memset(&hc, 0, sizeof(hc));
+        hc.init_min = 0x7fffffffffffffffLL;
+        cudaMemcpyAsync(ctl, &hc, sizeof(PeelCtl), cudaMemcpyHostToDevice, s);
+        DevGraph dg;
+        dg.n = n;
+        dg.arcs = arcs;
+        dg.rp = g->rp;
+        dg.col = g->col;
+        // without weights every arc is 1.0: validate ids with a temporary unit weight array
+        long long *unit = nullptr;
+        if (!has_w && arcs > 0) {
+            e = cudaMalloc((void **)&unit, sizeof(long long) * (size_t)arcs);
+            if (e == cudaSuccess) k_fill_i64<<<grid, 256, 0, s>>>(unit, arcs, 1LL << 32);
+        }
+        dg.cw = has_w ? g->cw : unit;
+        dg.a = g->a;
+        rc = DUPIN_OK;
+        if (e == cudaSuccess && dg.cw) rc = launch_init_weights(dg, DUPIN_DW, w, nullptr, nullptr, ctl, true, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(w);
+        cudaFree(ctl);
+        cudaFree(unit);
+        if (e != cudaSuccess || rc) {
+            int r2 = rc ? rc : dupin_cuda_fail(e, "graph validation");
+            graph_release(g);
+            cudaFree(bad);
+            return r2;
+        }
+        if (hc.init_overflow) {
+            graph_release(g);
+            cudaFree(bad);
+            if (hc.init_overflow == 2) return dupin_fail(DUPIN_ERR_INVALID_ARG, "negative vertex weight");
+            return dupin_fail(has_w ? DUPIN_ERR_OVERFLOW : DUPIN_ERR_INVALID_ARG,
+                              "invalid graph: a neighbour id out of range, a self-loop, a negative weight, or a "
+                              "peeling weight >= 2^63");
+        }
+    }
+#undef TRY
+    cudaFree(bad);
+    *out = g;
+    return DUPIN_OK;
+}
+
+extern "C" int dupin_graph_free(dupin_graph *g) {
+    if (!g) return DUPIN_OK;
+    cudaSetDevice(g->device);
+    graph_release(g);
+    return DUPIN_OK;
+}
+
+extern "C" int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs, int64_t *bytes) {
+    if (!g) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (arcs) *arcs = g->arcs;
+    if (bytes) *bytes = g->bytes + (g->ws ? g->ws->bytes : 0);
+    return DUPIN_OK;
+}

@@ -1,0 +1,1284 @@
+// peel.cu -- Dupin's parallel batch peeling (Algorithm 2, Sec. 4.1) on sm_103a.
+//
+// One peel = four stages, all on the caller's stream:
+//  (a) initial peeling weights w_u(V) = a_u + sum_v c_uv: an arc-balanced
+//      segmented sum over the CSR (each warp streams a contiguous arc range,
+//      carries the open row across chunks, so a hub row costs one atomic per
+//      warp), then f(V) = sum_u (w_u + a_u) / 2 and min_u w_u;
+//  (b)-(c) the bulk rounds in one persistent cooperative kernel, three grid
+//      barriers per round:
+//        A  select: scan this block's slice of the live list, peel every u
+//           with w_u <= T_i (T_i = floor(k (D+N) f / (D |S|)), or the minimum
+//           live weight when T_i selects nobody); stage the frontier with one
+//           packed (count, arcs) shared atomic per warp;
+//        B  place: prefix the per-block counts, write the frontier with its
+//           arc offsets, record where each consumer block's equal share of
+//           the round's arcs starts (merge path), compact the live list when
+//           it has halved;
+//        C  expand: walk this block's share of the frontier's arcs, subtract
+//           c_uv from every surviving neighbour with an int64 atomic, sum c
+//           over arcs inside U_i, and take the minimum post-decrement weight
+//           (the next round's minimum-rule candidate);
+//        D  (every block, redundantly) f_i = f_{i-1} - (sum_{u in U} w_u -
+//           internal/2), |S_i|, the best prefix, the trace;
+//  (d) once |S| <= tail_cap: the live vertices' induced subgraph is built
+//      (local ids, live arcs only) and one CTA runs the remaining rounds with
+//      w and the vertex states in shared memory.
+// Every step is exact integer arithmetic, so the per-round sets, the trace
+// and the best set equal the single-threaded oracle's bit for bit.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "dupin_internal.h"
+
+#define BULK_THREADS 512
+#define BULK_WARPS (BULK_THREADS / 32)
+#define WALK_WIN 1024
+#define INIT_THREADS 256
+#define INIT_WARPS (INIT_THREADS / 32)
+#define TAIL_THREADS 1024
+#define TAIL_WARPS (TAIL_THREADS / 32)
+#define SCAN_THREADS 1024
+
+// tail vertex states
+#define TS_LIVE 0
+#define TS_INU 1
+#define TS_DEAD 2
+
+static const long long kMaxLL = 0x7fffffffffffffffLL;
+
+// ------------------------------------------------------------ block helpers
+
+// Block-wide reduction of NV 64-bit sums, one u128 sum and one minimum.
+// All threads get the results.  Two __syncthreads.
+template <int NWARPS, int NV>
+struct BlockRed {
+    long long v[NV];
+    unsigned long long lo, hi;
+    long long mn;
+};
+
+template <int NWARPS, int NV>
+__device__ __forceinline__ void block_reduce(BlockRed<NWARPS, NV> &r, long long (*s_v)[NV], unsigned long long *s_lo,
+                                             unsigned long long *s_hi, long long *s_mn) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; j++) r.v[j] = warp_sum64(r.v[j]);
+    warp_sum128(r.lo, r.hi);
+    r.mn = warp_min64(r.mn);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; j++) s_v[wid][j] = r.v[j];
+        s_lo[wid] = r.lo;
+        s_hi[wid] = r.hi;
+        s_mn[wid] = r.mn;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        bool in = lane < NWARPS;
+#pragma unroll
+        for (int j = 0; j < NV; j++) r.v[j] = in ? s_v[lane][j] : 0;
+        r.lo = in ? s_lo[lane] : 0;
+        r.hi = in ? s_hi[lane] : 0;
+        r.mn = in ? s_mn[lane] : kMaxLL;
+#pragma unroll
+        for (int j = 0; j < NV; j++) r.v[j] = warp_sum64(r.v[j]);
+        warp_sum128(r.lo, r.hi);
+        r.mn = warp_min64(r.mn);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NV; j++) s_v[0][j] = r.v[j];
+            s_lo[0] = r.lo;
+            s_hi[0] = r.hi;
+            s_mn[0] = r.mn;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; j++) r.v[j] = s_v[0][j];
+    r.lo = s_lo[0];
+    r.hi = s_hi[0];
+    r.mn = s_mn[0];
+    __syncthreads();
+}
+
+// Exclusive block scan of one 64-bit value per thread; 'total' gets the sum.
+template <int NWARPS>
+__device__ __forceinline__ long long block_excl_scan(long long x, long long *s_w, long long &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = warp_incl_scan64(x);
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long v = lane < NWARPS ? s_w[lane] : 0;
+        v = warp_incl_scan64(v);
+        if (lane < NWARPS) s_w[lane] = v;
+    }
+    __syncthreads();
+    long long before = wid ? s_w[wid - 1] : 0;
+    total = s_w[NWARPS - 1];
+    __syncthreads();
+    return before + incl - x;
+}
+
+// last t in [0, n) with s[t] <= x (s non-decreasing, s[0] <= x)
+__device__ __forceinline__ int smem_last_le(const long long *s, int n, long long x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Walk the arcs [e0, e1) of a segmented arc space.  Entry k (0 <= k < U)
+// covers [base(k), base(k+1)) and its arcs sit at col positions start(k) + (x -
+// base(k)); base(U) is the total.  k0 must satisfy base(k0) <= e0.  The
+// block loads WALK_WIN entries at a time into shared memory and calls
+// fn(k, pos) once per arc, consecutive threads on consecutive arcs.
+template <class BaseF, class StartF, class ArcF>
+__device__ __forceinline__ void walk_arcs(BaseF base, StartF start, long long U, long long e0, long long e1,
+                                          long long k0, long long *s_base, long long *s_start, ArcF fn) {
+    long long e = e0, k = k0;
+    while (e < e1) {
+        __syncthreads();
+        for (int t = threadIdx.x; t <= WALK_WIN; t += blockDim.x) {
+            long long idx = k + t;
+            s_base[t] = idx <= U ? base(idx) : kMaxLL;
+            s_start[t] = idx < U ? start(idx) : 0;
+        }
+        __syncthreads();
+        long long wend = s_base[WALK_WIN];
+        long long hi = e1 < wend ? e1 : wend;
+        for (long long x = e + threadIdx.x; x < hi; x += blockDim.x) {
+            int t = smem_last_le(s_base, WALK_WIN, x);
+            fn(k + t, s_start[t] + (x - s_base[t]));
+        }
+        int t2 = smem_last_le(s_base, WALK_WIN + 1, hi);
+        k += t2;
+        e = hi;
+    }
+}
+
+// ------------------------------------------------------------- (a) init
+
+// w_u = a_u (DW/FD) or deg_u * 1.0 (DG); every vertex live; live list = ids.
+__global__ void k_init_vertex(DevGraph g, int dg, long long *w, int *pr, int *live0, PeelCtl *ctl) {
+    long long n = g.n;
+    unsigned long long lo = 0, hi = 0;
+    long long mn = kMaxLL;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+        long long wu;
+        if (dg) {
+            wu = (g.rp[u + 1] - g.rp[u]) << 32;
+            add128(lo, hi, (unsigned long long)wu, 0);
+            mn = wu < mn ? wu : mn;
+        } else {
+            wu = g.a ? g.a[u] : 0;
+            if (wu < 0) atomicExch(&ctl->init_overflow, 2);
+        }
+        w[u] = wu;
+        if (pr) pr[u] = DUPIN_LIVE;
+        if (live0) live0[u] = (int)u;
+    }
+    if (dg) {
+        warp_sum128(lo, hi);
+        mn = warp_min64(mn);
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long old = atomicAdd(&ctl->init_lo, lo);
+            if (old + lo < old) hi += 1;
+            if (hi) atomicAdd(&ctl->init_hi, hi);
+            atomicMin(&ctl->init_min, mn);
+        }
+    }
+}
+
+// Arc-balanced segmented sum: w_u += sum of c over row u.  The arc range is
+// split evenly over all warps of the grid; each warp walks its range in
+// 32-arc chunks, finds each arc's row from 32 cached row ends (5 shuffle
+// steps), reduces rows within the chunk with a segmented scan and keeps the
+// open last row in registers, so a row spanning many chunks is flushed once
+// per warp.  CHECK also validates ids, self-loops and int64 overflow.
+template <bool CHECK>
+__global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long long *w, PeelCtl *ctl) {
+    const int lane = threadIdx.x & 31;
+    const long long NW = (long long)gridDim.x * INIT_WARPS;
+    const long long W = blockIdx.x * (long long)INIT_WARPS + (threadIdx.x >> 5);
+    const long long A = g.arcs, n = g.n;
+    const long long we0 = (long long)(((u128)A * (unsigned long long)W) / (unsigned long long)NW);
+    const long long we1 = (long long)(((u128)A * (unsigned long long)(W + 1)) / (unsigned long long)NW);
+    if (we0 >= we1) return;
+    long long r = warp_search_last_le(g.rp, n, we0);  // row of the first arc
+    long long carry_own = -1, carry_val = 0;
+    bool bad = false;
+    for (long long x0 = we0; x0 < we1; x0 += 32) {
+        const long long x = x0 + lane;
+        const bool valid = x < we1;
+        long long val = 0;
+        if (valid) val = g.cw[x];
+        if (CHECK && valid) {
+            int v = g.col[x];
+            if (v < 0 || v >= n || val < 0) bad = true;
+        }
+        // Row of each lane's arc: with the 32 row ends rp[rr+1 .. rr+32] held
+        // one per lane, a lane whose arc x has rp[rr] <= x < rp[rr+32] lies in
+        // row rr + #{j : rp[rr+1+j] <= x} (5 shuffle steps).  Lanes further
+        // out wait while the window moves on by 32 rows.
+        long long owner = valid ? -1 : kMaxLL;
+        long long rr = r;
+        for (;;) {
+            const long long idx = rr + 1 + lane;
+            const long long bj = idx <= n ? g.rp[idx] : kMaxLL;
+            int lo = 0, hi = 32;
+#pragma unroll
+            for (int s = 0; s < 5; s++) {
+                int mid = (lo + hi) >> 1;
+                long long bm = __shfl_sync(0xffffffffu, bj, mid);
+                if (bm <= x) lo = mid + 1;
+                else hi = mid;
+            }
+            if (owner < 0 && lo < 32) owner = rr + lo;
+            if (!__any_sync(0xffffffffu, owner < 0)) break;
+            rr += 32;
+        }
+        if (CHECK && valid && g.col[x] == owner) bad = true;
+        // segmented inclusive scan by owner
+        long long sv = val;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            long long ov = __shfl_up_sync(0xffffffffu, sv, d);
+            long long oo = __shfl_up_sync(0xffffffffu, owner, d);
+            if (lane >= d && oo == owner) {
+                if (CHECK && (unsigned long long)sv + (unsigned long long)ov < (unsigned long long)sv) bad = true;
+                sv += ov;
+            }
+        }
+        long long on = __shfl_down_sync(0xffffffffu, owner, 1);
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const int last = 31 - __clz(vmask);
+        const bool is_end = valid && (lane == last || on != owner);
+        const long long o0 = __shfl_sync(0xffffffffu, owner, 0);
+        const long long oL = __shfl_sync(0xffffffffu, owner, last);
+        if (carry_own >= 0 && carry_own != o0) {
+            if (lane == 0) {
+                if (CHECK) {
+                    unsigned long long old = atomicAdd((unsigned long long *)&w[carry_own], (unsigned long long)carry_val);
+                    if (old + (unsigned long long)carry_val < old) bad = true;
+                } else {
+                    atomicAdd((unsigned long long *)&w[carry_own], (unsigned long long)carry_val);
+                }
+            }
+            carry_own = -1;
+            carry_val = 0;
+        }
+        const long long add = (carry_own == o0) ? carry_val : 0;
+        if (is_end && owner != oL) {
+            long long tot = sv + (owner == o0 ? add : 0);
+            if (CHECK) {
+                unsigned long long old = atomicAdd((unsigned long long *)&w[owner], (unsigned long long)tot);
+                if (old + (unsigned long long)tot < old) bad = true;
+            } else {
+                atomicAdd((unsigned long long *)&w[owner], (unsigned long long)tot);
+            }
+        }
+        long long lastsum = __shfl_sync(0xffffffffu, sv, last);
+        carry_val = lastsum + (oL == o0 ? add : 0);
+        carry_own = oL;
+        r = oL;  // the next chunk starts in this row or later
+    }
+    if (carry_own >= 0 && lane == 0) {
+        if (CHECK) {
+            unsigned long long old = atomicAdd((unsigned long long *)&w[carry_own], (unsigned long long)carry_val);
+            if (old + (unsigned long long)carry_val < old) bad = true;
+        } else {
+            atomicAdd((unsigned long long *)&w[carry_own], (unsigned long long)carry_val);
+        }
+    }
+    if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&ctl->init_overflow, 1);
+}
+
+// sum over u of (w_u + a_u) and min w (DW/FD)
+__global__ void k_init_reduce(DevGraph g, const long long *w, PeelCtl *ctl) {
+    unsigned long long lo = 0, hi = 0;
+    long long mn = kMaxLL;
+    bool bad = false;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < g.n; u += (long long)gridDim.x * blockDim.x) {
+        long long wu = w[u];
+        if (wu < 0) bad = true;  // wrapped past 2^63
+        add128(lo, hi, (unsigned long long)wu, 0);
+        if (g.a) add128(lo, hi, (unsigned long long)g.a[u], 0);
+        mn = wu < mn ? wu : mn;
+    }
+    warp_sum128(lo, hi);
+    mn = warp_min64(mn);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&ctl->init_overflow, 1);
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long old = atomicAdd(&ctl->init_lo, lo);
+        if (old + lo < old) hi += 1;
+        if (hi) atomicAdd(&ctl->init_hi, hi);
+        atomicMin(&ctl->init_min, mn);
+    }
+}
+
+int launch_init_weights(const DevGraph &dg, int metric, long long *w, int *pr, int *live0, PeelCtl *ctl, bool check,
+                        cudaStream_t s) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int vgrid = sms * 8;
+    const bool isdg = metric == DUPIN_DG || dg.cw == nullptr;
+    k_init_vertex<<<vgrid, 256, 0, s>>>(dg, isdg ? 1 : 0, w, pr, live0, ctl);
+    if (!isdg) {
+        if (dg.arcs > 0) {
+            int agrid = sms * 8;
+            if (check) k_init_arcs<true><<<agrid, INIT_THREADS, 0, s>>>(dg, w, ctl);
+            else k_init_arcs<false><<<agrid, INIT_THREADS, 0, s>>>(dg, w, ctl);
+        }
+        k_init_reduce<<<vgrid, 256, 0, s>>>(dg, w, ctl);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "init kernels");
+    return DUPIN_OK;
+}
+
+// f(V), |V|, round 0, best = S_0, trace entry 0
+__global__ void k_init_finish(PeelArgs A, long long n) {
+    PeelCtl *c = A.ctl;
+    u128 s = mk128(c->init_lo, c->init_hi);
+    u128 f = s >> 1;
+    c->round = 0;
+    c->size = n;
+    c->f_lo = (unsigned long long)f;
+    c->f_hi = (unsigned long long)(f >> 64);
+    c->live_len = n;
+    c->live_sel = 0;
+    c->minw = n > 0 ? c->init_min : 0;
+    c->best_round = 0;
+    c->best_size = n;
+    c->bf_lo = c->f_lo;
+    c->bf_hi = c->f_hi;
+    c->gpo_le = 0;
+    c->n_min_rule = 0;
+    c->scan_volume = 0;
+    c->bar_count = 0;
+    c->bar_gen = 0;
+    if (c->init_overflow) c->error = DUPIN_ERR_OVERFLOW;
+    c->status = n == 0 ? ST_DONE : (n <= A.tail_cap ? ST_TAIL : ST_RUNNING);
+    if (A.tr_cap > 0) {
+        A.tr_f_hi[0] = (long long)c->f_hi;
+        A.tr_f_lo[0] = c->f_lo;
+        A.tr_size[0] = n;
+        A.tr_peeled[0] = 0;
+    }
+}
+
+// ------------------------------------------------------ (b)-(c) bulk rounds
+
+struct RoundState {
+    long long round, size;
+    u128 f;
+    long long live_len;
+    int live_sel;
+    long long minw;
+    long long best_round, best_size;
+    u128 bf;
+    long long gpo_le, n_min_rule, scan;
+};
+
+__global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
+    __shared__ long long s_v[BULK_WARPS][6];
+    __shared__ unsigned long long s_lo[BULK_WARPS], s_hi[BULK_WARPS];
+    __shared__ long long s_mn[BULK_WARPS];
+    __shared__ unsigned long long s_pack;
+    __shared__ unsigned long long s_surv;
+    __shared__ long long s_base[WALK_WIN + 1];
+    __shared__ long long s_start[WALK_WIN + 1];
+
+    const unsigned G = gridDim.x;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    PeelCtl *ctl = A.ctl;
+    const DevGraph g = A.g;
+    const bool dg = g.cw == nullptr;
+
+    RoundState st;
+    st.round = ctl->round;
+    st.size = ctl->size;
+    st.f = mk128(ctl->f_lo, ctl->f_hi);
+    st.live_len = ctl->live_len;
+    st.live_sel = ctl->live_sel;
+    st.minw = ctl->minw;
+    st.best_round = ctl->best_round;
+    st.best_size = ctl->best_size;
+    st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
+    st.gpo_le = ctl->gpo_le;
+    st.n_min_rule = ctl->n_min_rule;
+    st.scan = ctl->scan_volume;
+    if (ctl->status != ST_RUNNING || ctl->error) return;
+
+    for (;;) {
+        if (st.size == 0 || st.size <= A.tail_cap) break;
+        if (st.round >= A.max_rounds) {
+            if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
+            break;
+        }
+        const long long i = st.round + 1;
+        long long T = floor_ratio((unsigned long long)A.kD, st.f, (unsigned long long)A.D, st.size);
+        if (A.gpo) {
+            long long le = floor_ratio((unsigned long long)A.D, st.f, (unsigned long long)A.kD, st.size);
+            st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
+            T = st.gpo_le > T ? st.gpo_le : T;
+        }
+        const bool minrule = A.use_min && st.minw > T;
+        const long long thr = minrule ? st.minw : T;
+
+        // ---------------- phase A: select
+        int *live = st.live_sel ? A.live1 : A.live0;
+        int *nlive = st.live_sel ? A.live0 : A.live1;
+        const long long L = st.live_len;
+        const long long j0 = (long long)(((u128)L * b) / G), j1 = (long long)(((u128)L * (b + 1)) / G);
+        if (tid == 0) s_pack = 0;
+        __syncthreads();
+        long long cnt = 0, surv = 0, minsurv = kMaxLL;
+        unsigned long long wlo = 0, whi = 0;
+        for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
+            const long long j = jb + lane;
+            int id = j < j1 ? live[j] : -1;
+            long long wv = 0;
+            if (id >= 0) wv = A.w[id];
+            const bool sel = id >= 0 && wv <= thr;
+            if (id >= 0 && !sel) {
+                surv++;
+                minsurv = wv < minsurv ? wv : minsurv;
+            }
+            long long start = 0, deg = 0;
+            if (sel) {
+                cnt++;
+                add128(wlo, whi, (unsigned long long)wv, 0);
+                A.pr[id] = (int)i;
+                live[j] = -1;
+                start = g.rp[id];
+                deg = g.rp[id + 1] - start;
+            }
+            const bool stage = sel && deg > 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, stage);
+            if (bal) {
+                long long incl = warp_incl_scan64(stage ? deg : 0);
+                long long tot = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&s_pack, ((unsigned long long)__popc(bal) << 40) | (unsigned long long)tot);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (stage) {
+                    long long slot = (long long)(base >> 40) + __popc(bal & ((1u << lane) - 1u));
+                    long long off = (long long)(base & ((1ull << 40) - 1)) + incl - deg;
+                    A.stage_start[j0 + slot] = start;
+                    A.stage_off[j0 + slot] = off;
+                }
+            }
+        }
+        {
+            BlockRed<BULK_WARPS, 6> r;
+            r.v[0] = cnt; r.v[1] = surv; r.v[2] = 0; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
+            r.lo = wlo; r.hi = whi; r.mn = minsurv;
+            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            if (tid == 0) {
+                BlockPart &p = A.part[b];
+                p.sel_cnt = r.v[0];
+                p.surv_cnt = r.v[1];
+                p.ws_lo = r.lo;
+                p.ws_hi = r.hi;
+                p.min_surv = r.mn;
+                p.stage_cnt = (long long)(s_pack >> 40);
+                p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
+            }
+        }
+        if (!grid_barrier(ctl, G)) return;
+
+        // ---------------- phase B: totals, frontier placement, compaction
+        long long U_sel, U_stage, totArcs, survTot, slotBase, arcBase, survBase, myStage, myDeg;
+        unsigned long long Wlo, Whi;
+        long long minSurvAll;
+        {
+            BlockRed<BULK_WARPS, 6> r;
+            for (int j = 0; j < 6; j++) r.v[j] = 0;
+            r.lo = 0; r.hi = 0; r.mn = kMaxLL;
+            // v: 0 sel_cnt, 1 stage_cnt, 2 sel_deg, 3 surv, 4 stage before b, 5 deg before b
+            long long survBefore = 0;
+            for (int t = tid; t < (int)G; t += BULK_THREADS) {
+                const BlockPart &p = A.part[t];
+                r.v[0] += p.sel_cnt;
+                r.v[1] += p.stage_cnt;
+                r.v[2] += p.sel_deg;
+                r.v[3] += p.surv_cnt;
+                if (t < b) {
+                    r.v[4] += p.stage_cnt;
+                    r.v[5] += p.sel_deg;
+                    survBefore += p.surv_cnt;
+                }
+                add128(r.lo, r.hi, p.ws_lo, p.ws_hi);
+                r.mn = p.min_surv < r.mn ? p.min_surv : r.mn;
+            }
+            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            U_sel = r.v[0]; U_stage = r.v[1]; totArcs = r.v[2]; survTot = r.v[3];
+            slotBase = r.v[4]; arcBase = r.v[5];
+            Wlo = r.lo; Whi = r.hi; minSurvAll = r.mn;
+            // survivors before b: one more (cheap) reduction
+            BlockRed<BULK_WARPS, 6> r2;
+            for (int j = 0; j < 6; j++) r2.v[j] = 0;
+            r2.v[0] = survBefore;
+            r2.lo = 0; r2.hi = 0; r2.mn = kMaxLL;
+            block_reduce<BULK_WARPS, 6>(r2, s_v, s_lo, s_hi, s_mn);
+            survBase = r2.v[0];
+            myStage = A.part[b].stage_cnt;
+            myDeg = A.part[b].sel_deg;
+        }
+        const long long newSize = st.size - U_sel;
+        const bool compact = newSize > 0 && (2 * newSize <= L || newSize <= A.tail_cap);
+        for (long long q = tid; q < myStage; q += BULK_THREADS) {
+            const long long gs = slotBase + q;
+            const long long off = A.stage_off[j0 + q];
+            const long long goff = arcBase + off;
+            A.fstart[gs] = A.stage_start[j0 + q];
+            A.fbase[gs] = goff;
+            const long long nxt = (q + 1 < myStage) ? A.stage_off[j0 + q + 1] : myDeg;
+            const long long gend = arcBase + nxt;
+            // consumer blocks whose share starts inside [goff, gend)
+            long long c = (long long)(((u128)goff * G + (unsigned long long)totArcs - 1) / (unsigned long long)totArcs);
+            for (; c < (long long)G; c++) {
+                long long e0c = (long long)(((u128)totArcs * (unsigned long long)c) / G);
+                if (e0c >= gend) break;
+                A.cstart[c] = gs;
+            }
+        }
+        if (b == 0 && tid == 0) A.fbase[U_stage] = totArcs;
+        if (compact) {
+            if (tid == 0) s_surv = 0;
+            __syncthreads();
+            for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
+                const long long j = jb + lane;
+                int id = j < j1 ? live[j] : -1;
+                const bool keep = id >= 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (bal) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&s_surv, (unsigned long long)__popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (keep) nlive[survBase + (long long)base + __popc(bal & ((1u << lane) - 1u))] = id;
+                }
+            }
+        }
+        (void)survTot;
+        if (!grid_barrier(ctl, G)) return;
+
+        // ---------------- phase C: expand
+        long long mindec = kMaxLL;
+        unsigned long long ilo = 0, ihi = 0;
+        if (totArcs > 0) {
+            const long long E0 = (long long)(((u128)totArcs * (unsigned long long)b) / G);
+            const long long E1 = (long long)(((u128)totArcs * (unsigned long long)(b + 1)) / G);
+            if (E0 < E1) {
+                const long long k0 = A.cstart[b];
+                const long long *fb = A.fbase;
+                const long long *fs = A.fstart;
+                const int *col = g.col;
+                const long long *cw = g.cw;
+                int *pr = A.pr;
+                long long *w = A.w;
+                const bool use_min = A.use_min != 0;
+                walk_arcs([=](long long k) { return fb[k]; },
+                          [=](long long k) { return fs[k]; }, U_stage, E0, E1, k0, s_base, s_start,
+                          [&](long long k, long long pos) {
+                              (void)k;
+                              const int v = col[pos];
+                              const long long c = dg ? DUPIN_Q_ONE : cw[pos];
+                              const int p = pr[v];
+                              if (p > (int)i) {
+                                  if (use_min) {
+                                      long long old = (long long)atomicAdd((unsigned long long *)&w[v],
+                                                                           (unsigned long long)(-c));
+                                      long long nw = old - c;
+                                      mindec = nw < mindec ? nw : mindec;
+                                  } else {
+                                      atomicAdd((unsigned long long *)&w[v], (unsigned long long)(-c));
+                                  }
+                              } else if (p == (int)i) {
+                                  add128(ilo, ihi, (unsigned long long)c, 0);
+                              }
+                          });
+            }
+        }
+        {
+            BlockRed<BULK_WARPS, 6> r;
+            for (int j = 0; j < 6; j++) r.v[j] = 0;
+            r.lo = ilo; r.hi = ihi; r.mn = mindec;
+            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            if (tid == 0) {
+                A.part[b].in_lo = r.lo;
+                A.part[b].in_hi = r.hi;
+                A.part[b].min_dec = r.mn;
+            }
+        }
+        if (!grid_barrier(ctl, G)) return;
+
+        // ---------------- phase D: close the round (every block)
+        {
+            BlockRed<BULK_WARPS, 6> r;
+            for (int j = 0; j < 6; j++) r.v[j] = 0;
+            r.lo = 0; r.hi = 0; r.mn = kMaxLL;
+            for (int t = tid; t < (int)G; t += BULK_THREADS) {
+                add128(r.lo, r.hi, A.part[t].in_lo, A.part[t].in_hi);
+                r.mn = A.part[t].min_dec < r.mn ? A.part[t].min_dec : r.mn;
+            }
+            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            const u128 internal = mk128(r.lo, r.hi);
+            const u128 wsel = mk128(Wlo, Whi);
+            st.f = st.f - (wsel - (internal >> 1));
+            st.scan += L;
+            st.size = newSize;
+            st.round = i;
+            st.n_min_rule += minrule ? 1 : 0;
+            if (A.use_min) st.minw = minSurvAll < r.mn ? minSurvAll : r.mn;
+            if (compact) {
+                st.live_sel ^= 1;
+                st.live_len = newSize;
+            }
+            if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
+                st.bf = st.f;
+                st.best_size = st.size;
+                st.best_round = i;
+            }
+            if (b == 0 && tid == 0) {
+                if (i < A.tr_cap) {
+                    A.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
+                    A.tr_f_lo[i] = (unsigned long long)st.f;
+                    A.tr_size[i] = st.size;
+                    A.tr_peeled[i] = U_sel;
+                }
+            }
+        }
+    }
+    if (b == 0 && tid == 0) {
+        ctl->round = st.round;
+        ctl->size = st.size;
+        ctl->f_lo = (unsigned long long)st.f;
+        ctl->f_hi = (unsigned long long)(st.f >> 64);
+        ctl->live_len = st.live_len;
+        ctl->live_sel = st.live_sel;
+        ctl->minw = st.minw;
+        ctl->best_round = st.best_round;
+        ctl->best_size = st.best_size;
+        ctl->bf_lo = (unsigned long long)st.bf;
+        ctl->bf_hi = (unsigned long long)(st.bf >> 64);
+        ctl->gpo_le = st.gpo_le;
+        ctl->n_min_rule = st.n_min_rule;
+        ctl->scan_volume = st.scan;
+        ctl->bulk_rounds = st.round;
+        if (ctl->error == 0) ctl->status = st.size == 0 ? ST_DONE : ST_TAIL;
+    }
+}
+
+// ------------------------------------------------------- (d) tail sub-graph
+
+// local ids and full degrees of the live vertices
+__global__ void k_tail_prep(PeelArgs A) {
+    const PeelCtl *c = A.ctl;
+    if (c->status != ST_TAIL || c->error) return;
+    const long long L = c->live_len;
+    const int *live = c->live_sel ? A.live1 : A.live0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L; p += (long long)gridDim.x * blockDim.x) {
+        int gid = live[p];
+        A.loc[gid] = (int)p;
+        A.tdeg[p] = A.g.rp[gid + 1] - A.g.rp[gid];
+    }
+}
+
+// exclusive prefix of x[0..L) in place, x[L] = total (one block)
+__global__ void __launch_bounds__(SCAN_THREADS) k_tail_scan(PeelArgs A, long long *x, const int *cnt) {
+    __shared__ long long s_w[SCAN_THREADS / 32];
+    const PeelCtl *c = A.ctl;
+    if (c->status != ST_TAIL || c->error) return;
+    const long long L = c->live_len;
+    long long carry = 0;
+    for (long long b0 = 0; b0 < L; b0 += SCAN_THREADS) {
+        long long p = b0 + threadIdx.x;
+        long long v = p < L ? (cnt ? (long long)cnt[p] : x[p]) : 0;
+        long long tot;
+        long long ex = block_excl_scan<SCAN_THREADS / 32>(v, s_w, tot);
+        if (p < L) x[p] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        x[L] = carry;
+        if (cnt && carry > A.tarc_cap) set_error(A.ctl, DUPIN_ERR_OOM);
+    }
+}
+
+// pass 0: count live neighbours per live vertex; pass 1: fill local arcs
+template <int PASS>
+__global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
+    __shared__ long long s_base[WALK_WIN + 1];
+    __shared__ long long s_start[WALK_WIN + 1];
+    __shared__ long long s_k0;
+    const PeelCtl *c = A.ctl;
+    if (c->status != ST_TAIL || c->error) return;
+    const long long L = c->live_len;
+    const int *live = c->live_sel ? A.live1 : A.live0;
+    const long long tot = A.tdeg[L];
+    const unsigned G = gridDim.x;
+    const long long e0 = (long long)(((u128)tot * blockIdx.x) / G);
+    const long long e1 = (long long)(((u128)tot * (blockIdx.x + 1)) / G);
+    if (e0 >= e1) return;
+    const long long *tdeg = A.tdeg;
+    const long long *rp = A.g.rp;
+    if (threadIdx.x < 32) {
+        long long k = warp_search_last_le(tdeg, L, e0);
+        if (threadIdx.x == 0) s_k0 = k;
+    }
+    __syncthreads();
+    const long long k0 = s_k0;
+    const int *col = A.g.col;
+    const long long *cw = A.g.cw;
+    const int *pr = A.pr;
+    walk_arcs([=](long long k) { return tdeg[k]; },
+              [=](long long k) { return rp[live[k]]; }, L, e0, e1, k0, s_base, s_start,
+              [&](long long k, long long pos) {
+                  const int v = col[pos];
+                  if (pr[v] != DUPIN_LIVE) return;
+                  if (PASS == 0) {
+                      atomicAdd(&A.tcnt[k], 1);
+                  } else {
+                      long long slot = A.tlrp[k] + atomicAdd(&A.tfill[k], 1);
+                      A.tcol[slot] = A.loc[v];
+                      if (A.tcw) A.tcw[slot] = cw ? cw[pos] : DUPIN_Q_ONE;
+                  }
+              });
+}
+
+// One CTA finishes the peel on the live sub-graph held in shared memory:
+// tw[L] weights, ts[L] states, tf[L] the round's frontier (local ids).
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_v[TAIL_WARPS][2];
+    __shared__ unsigned long long s_lo[TAIL_WARPS], s_hi[TAIL_WARPS];
+    __shared__ long long s_mn[TAIL_WARPS];
+    __shared__ long long s_w[TAIL_WARPS];
+    __shared__ long long s_pref[TAIL_THREADS + 1];
+    __shared__ int s_F;
+    __shared__ unsigned long long s_lo2[TAIL_WARPS], s_hi2[TAIL_WARPS];
+    __shared__ long long s_mn2[TAIL_WARPS];
+
+    PeelCtl *ctl = A.ctl;
+    if (ctl->status != ST_TAIL || ctl->error) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long long L = ctl->live_len;
+    long long *tw = (long long *)smem;
+    unsigned char *ts = smem + 8 * L;
+    unsigned short *tf = (unsigned short *)(smem + ((9 * L + 15) & ~15LL));
+    const int *live = ctl->live_sel ? A.live1 : A.live0;
+    const bool dg = A.tcw == nullptr;
+
+    RoundState st;
+    st.round = ctl->round;
+    st.size = ctl->size;
+    st.f = mk128(ctl->f_lo, ctl->f_hi);
+    st.minw = ctl->minw;
+    st.best_round = ctl->best_round;
+    st.best_size = ctl->best_size;
+    st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
+    st.gpo_le = ctl->gpo_le;
+    st.n_min_rule = ctl->n_min_rule;
+    st.scan = ctl->scan_volume;
+    for (long long p = tid; p < L; p += TAIL_THREADS) {
+        tw[p] = A.w[live[p]];
+        ts[p] = TS_LIVE;
+    }
+    if (tid == 0) s_F = 0;
+    __syncthreads();
+    int err = 0;
+    while (st.size > 0) {
+        if (st.round >= A.max_rounds) {
+            err = DUPIN_ERR_NO_PROGRESS;
+            break;
+        }
+        const long long i = st.round + 1;
+        long long T = floor_ratio((unsigned long long)A.kD, st.f, (unsigned long long)A.D, st.size);
+        if (A.gpo) {
+            long long le = floor_ratio((unsigned long long)A.D, st.f, (unsigned long long)A.kD, st.size);
+            st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
+            T = st.gpo_le > T ? st.gpo_le : T;
+        }
+        const bool minrule = A.use_min && st.minw > T;
+        const long long thr = minrule ? st.minw : T;
+        // select
+        unsigned long long wlo = 0, whi = 0;
+        long long minsurv = kMaxLL;
+        for (long long p0 = wid * 32; p0 < L; p0 += TAIL_THREADS) {
+            const long long p = p0 + lane;
+            bool sel = false;
+            if (p < L && ts[p] == TS_LIVE) {
+                const long long wv = tw[p];
+                if (wv <= thr) {
+                    sel = true;
+                    ts[p] = TS_INU;
+                    add128(wlo, whi, (unsigned long long)wv, 0);
+                } else {
+                    minsurv = wv < minsurv ? wv : minsurv;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, sel);
+            if (bal) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_F, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (sel) tf[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)p;
+            }
+        }
+        __syncthreads();
+        const int F = s_F;
+        // expand the frontier in chunks of TAIL_THREADS entries
+        long long mindec = kMaxLL;
+        unsigned long long ilo = 0, ihi = 0;
+        for (int c0 = 0; c0 < F; c0 += TAIL_THREADS) {
+            const int q = c0 + tid;
+            long long deg = 0;
+            if (q < F) {
+                const int p = tf[q];
+                deg = A.tlrp[p + 1] - A.tlrp[p];
+            }
+            long long tot;
+            long long ex = block_excl_scan<TAIL_WARPS>(deg, s_w, tot);
+            s_pref[tid] = ex;
+            const int nq = (F - c0) < TAIL_THREADS ? (F - c0) : TAIL_THREADS;
+            if (tid == 0) s_pref[nq] = tot;
+            __syncthreads();
+            for (long long x = tid; x < tot; x += TAIL_THREADS) {
+                int e = smem_last_le(s_pref, nq, x);
+                // zero-degree entries share a base with the next one: take the last
+                const int p = tf[c0 + e];
+                const long long pos = A.tlrp[p] + (x - s_pref[e]);
+                const int v = A.tcol[pos];
+                const long long c = dg ? DUPIN_Q_ONE : A.tcw[pos];
+                const unsigned char s = ts[v];
+                if (s == TS_LIVE) {
+                    long long old = (long long)atomicAdd((unsigned long long *)&tw[v], (unsigned long long)(-c));
+                    long long nw = old - c;
+                    mindec = nw < mindec ? nw : mindec;
+                } else if (s == TS_INU) {
+                    add128(ilo, ihi, (unsigned long long)c, 0);
+                }
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < F; q += TAIL_THREADS) {
+            const int p = tf[q];
+            ts[p] = TS_DEAD;
+            A.pr[live[p]] = (int)i;
+        }
+        // reduce: weights of U, internal arcs, minima
+        warp_sum128(wlo, whi);
+        warp_sum128(ilo, ihi);
+        minsurv = warp_min64(minsurv);
+        mindec = warp_min64(mindec);
+        if (lane == 0) {
+            s_lo[wid] = wlo; s_hi[wid] = whi;
+            s_lo2[wid] = ilo; s_hi2[wid] = ihi;
+            s_mn[wid] = minsurv; s_mn2[wid] = mindec;
+        }
+        __syncthreads();
+        unsigned long long Wl = 0, Wh = 0, Il = 0, Ih = 0;
+        long long ms = kMaxLL, md = kMaxLL;
+        for (int t = 0; t < TAIL_WARPS; t++) {
+            add128(Wl, Wh, s_lo[t], s_hi[t]);
+            add128(Il, Ih, s_lo2[t], s_hi2[t]);
+            ms = s_mn[t] < ms ? s_mn[t] : ms;
+            md = s_mn2[t] < md ? s_mn2[t] : md;
+        }
+        __syncthreads();
+        if (tid == 0) s_F = 0;
+        const u128 wsel = mk128(Wl, Wh), internal = mk128(Il, Ih);
+        st.f = st.f - (wsel - (internal >> 1));
+        st.scan += L;
+        st.size -= F;
+        st.round = i;
+        st.n_min_rule += minrule ? 1 : 0;
+        if (A.use_min) st.minw = ms < md ? ms : md;
+        if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
+            st.bf = st.f;
+            st.best_size = st.size;
+            st.best_round = i;
+        }
+        if (tid == 0 && i < A.tr_cap) {
+            A.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
+            A.tr_f_lo[i] = (unsigned long long)st.f;
+            A.tr_size[i] = st.size;
+            A.tr_peeled[i] = F;
+        }
+        (void)s_v;
+        (void)s_mn;
+    }
+    if (tid == 0) {
+        if (err) set_error(ctl, err);
+        ctl->round = st.round;
+        ctl->size = st.size;
+        ctl->f_lo = (unsigned long long)st.f;
+        ctl->f_hi = (unsigned long long)(st.f >> 64);
+        ctl->minw = st.minw;
+        ctl->best_round = st.best_round;
+        ctl->best_size = st.best_size;
+        ctl->bf_lo = (unsigned long long)st.bf;
+        ctl->bf_hi = (unsigned long long)(st.bf >> 64);
+        ctl->gpo_le = st.gpo_le;
+        ctl->n_min_rule = st.n_min_rule;
+        ctl->scan_volume = st.scan;
+        if (!err) ctl->status = ST_DONE;
+    }
+}
+
+// best_mask[u] = (peel_round[u] > best_round)
+__global__ void k_finalize(const int *pr, long long n, const PeelCtl *ctl, uint8_t *mask) {
+    const long long br = ctl->best_round;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        mask[u] = (long long)pr[u] > br ? 1 : 0;
+}
+
+// ------------------------------------------------------------------- host
+
+long long tail_cap_limit() {
+    int dev = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // static shared memory of k_peel_tail is about 22 KB; 11 bytes per vertex
+    long long avail = (long long)smem - 24 * 1024;
+    long long cap = avail / 11;
+    if (cap > 65535) cap = 65535;
+    return cap < 0 ? 0 : cap;
+}
+
+long long tail_cap_default() {
+    long long lim = tail_cap_limit();
+    return lim < 16384 ? lim : 16384;
+}
+
+int peel_grid_size() {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel_bulk, BULK_THREADS, 0);
+    if (occ < 1) occ = 1;
+    if (occ > 2) occ = 2;
+    return sms * occ;
+}
+
+static int set_tail_smem() {
+    static int done = -1;
+    if (done == 0) return DUPIN_OK;
+    int dev = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_peel_tail);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaFuncGetAttributes(k_peel_tail)");
+    int dyn = smem - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(k_peel_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaFuncSetAttribute(k_peel_tail)");
+    done = 0;
+    return DUPIN_OK;
+}
+
+static long long tail_smem_bytes(long long cap) { return ((9 * cap + 15) & ~15LL) + 2 * cap + 16; }
+
+static int check_params(const dupin_graph *g, const dupin_params *p) {
+    if (!p) return dupin_fail(DUPIN_ERR_INVALID_ARG, "params is NULL");
+    if (p->metric < DUPIN_DG || p->metric > DUPIN_FD) return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown metric");
+    if (p->k_mult < 1 || p->k_mult > 64) return dupin_fail(DUPIN_ERR_INVALID_ARG, "k_mult must be in 1..64");
+    if (p->eps_den < 1 || p->eps_den > (1LL << 24) || p->eps_num < 0 || p->eps_num > (1LL << 30))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "eps must be eps_num/eps_den with 0 <= eps_num <= 2^30, 1 <= eps_den <= 2^24");
+    if (p->flags & ~(uint32_t)(DUPIN_GPO | DUPIN_RESULT_DEVICE | DUPIN_TIMING))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown flag");
+    if (p->metric != DUPIN_DG && g->cw == nullptr)
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "DW/FD need edge weights; the graph was loaded without them");
+    return DUPIN_OK;
+}
+
+DevGraph dev_graph(const dupin_graph *g, int metric) {
+    DevGraph d;
+    d.n = g->n;
+    d.arcs = g->arcs;
+    d.rp = g->rp;
+    d.col = g->col;
+    d.cw = metric == DUPIN_DG ? nullptr : g->cw;
+    d.a = metric == DUPIN_DG ? nullptr : g->a;
+    return d;
+}
+
+long long workspace_bytes(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap, int grid) {
+    const long long tarc = std::min<long long>(arcs, tail_cap * (tail_cap > 0 ? tail_cap - 1 : 0));
+    long long b = 0;
+    b += n * (8 + 4 + 4 + 4 + 4 + 8 + 8 + 8 + 4 + 1) + 8 * (n + 1);
+    b += 8 * (grid + 1) + (long long)sizeof(BlockPart) * grid + (long long)sizeof(PeelCtl);
+    b += 32 * tr_cap;
+    b += (tail_cap + 1) * (8 + 8 + 4 + 4);
+    b += tarc * (4 + (has_cw ? 8 : 0));
+    return b;
+}
+
+void workspace_free(PeelWorkspace *ws, cudaStream_t s) {
+    if (!ws) return;
+    void *ptrs[] = {ws->w, ws->pr, ws->live0, ws->live1, ws->stage_id, ws->stage_start, ws->stage_off,
+                    ws->fstart, ws->fbase, ws->cstart, ws->part, ws->ctl, ws->tr_f_hi, ws->tr_f_lo,
+                    ws->tr_size, ws->tr_peeled, ws->loc, ws->tdeg, ws->tlrp, ws->tcnt, ws->tfill,
+                    ws->tcol, ws->tcw, ws->mask};
+    for (void *q : ptrs) {
+        if (!q) continue;
+        if (ws->async) cudaFreeAsync(q, s);
+        else cudaFree(q);
+    }
+    for (int j = 0; j < 5; j++)
+        if (ws->ev[j]) cudaEventDestroy(ws->ev[j]);
+    delete ws;
+}
+
+void workspace_free(PeelWorkspace *ws) { workspace_free(ws, 0); }
+
+PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap,
+                                bool async, cudaStream_t s, int *rc) {
+    PeelWorkspace *ws = new PeelWorkspace();
+    ws->n = n;
+    ws->arcs = arcs;
+    ws->tail_cap = tail_cap;
+    ws->tr_cap = tr_cap;
+    ws->tarc_cap = std::min<long long>(arcs, tail_cap * (tail_cap > 0 ? tail_cap - 1 : 0));
+    ws->grid = peel_grid_size();
+    ws->async = async;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto **ptr, long long count) {
+        if (e != cudaSuccess) return;
+        size_t sz = sizeof(**ptr) * (size_t)(count > 0 ? count : 1);
+        e = async ? cudaMallocAsync((void **)ptr, sz, s) : cudaMalloc((void **)ptr, sz);
+        if (e == cudaSuccess) ws->bytes += (long long)sz;
+    };
+    A(&ws->w, n);
+    A(&ws->pr, n);
+    A(&ws->live0, n);
+    A(&ws->live1, n);
+    A(&ws->stage_id, 1);
+    A(&ws->stage_start, n);
+    A(&ws->stage_off, n);
+    A(&ws->fstart, n);
+    A(&ws->fbase, n + 1);
+    A(&ws->cstart, ws->grid + 1);
+    A(&ws->part, ws->grid);
+    A(&ws->ctl, 1);
+    A(&ws->tr_f_hi, tr_cap);
+    A(&ws->tr_f_lo, tr_cap);
+    A(&ws->tr_size, tr_cap);
+    A(&ws->tr_peeled, tr_cap);
+    A(&ws->loc, n);
+    A(&ws->tdeg, tail_cap + 1);
+    A(&ws->tlrp, tail_cap + 1);
+    A(&ws->tcnt, tail_cap + 1);
+    A(&ws->tfill, tail_cap + 1);
+    A(&ws->tcol, ws->tarc_cap);
+    if (has_cw) A(&ws->tcw, ws->tarc_cap);
+    A(&ws->mask, n);
+    if (e != cudaSuccess) {
+        workspace_free(ws, s);
+        cudaGetLastError();
+        *rc = dupin_fail(e == cudaErrorMemoryAllocation ? DUPIN_ERR_OOM : DUPIN_ERR_CUDA,
+                         std::string("peel workspace allocation failed: ") + cudaGetErrorString(e));
+        return nullptr;
+    }
+    *rc = DUPIN_OK;
+    return ws;
+}
+
+int workspace_ensure(dupin_graph *g, long long tail_cap, long long tr_cap) {
+    PeelWorkspace *ws = g->ws;
+    if (ws && ws->tail_cap >= tail_cap && ws->tr_cap >= tr_cap) return DUPIN_OK;
+    if (ws) {
+        tail_cap = std::max(tail_cap, ws->tail_cap);
+        tr_cap = std::max(tr_cap, ws->tr_cap);
+        workspace_free(ws);
+        g->ws = nullptr;
+    }
+    int rc;
+    g->ws = workspace_create(g->n, g->arcs, g->cw != nullptr, tail_cap, tr_cap, false, 0, &rc);
+    return rc;
+}
+
+static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const dupin_params *p, long long tail_cap,
+                          long long max_rounds) {
+    PeelArgs A;
+    A.g = dev_graph(g, p->metric);
+    A.w = ws->w;
+    A.pr = ws->pr;
+    A.live0 = ws->live0;
+    A.live1 = ws->live1;
+    A.stage_id = ws->stage_id;
+    A.stage_start = ws->stage_start;
+    A.stage_off = ws->stage_off;
+    A.fstart = ws->fstart;
+    A.fbase = ws->fbase;
+    A.cstart = ws->cstart;
+    A.part = ws->part;
+    A.ctl = ws->ctl;
+    A.tr_f_hi = ws->tr_f_hi;
+    A.tr_f_lo = ws->tr_f_lo;
+    A.tr_size = ws->tr_size;
+    A.tr_peeled = ws->tr_peeled;
+    A.tr_cap = ws->tr_cap;
+    A.kD = (long long)p->k_mult * (p->eps_den + p->eps_num);
+    A.D = p->eps_den;
+    A.use_min = A.kD < 2 * A.D ? 1 : 0;
+    A.gpo = (p->flags & DUPIN_GPO) ? 1 : 0;
+    A.max_rounds = max_rounds;
+    A.tail_cap = tail_cap;
+    A.loc = ws->loc;
+    A.tdeg = ws->tdeg;
+    A.tlrp = ws->tlrp;
+    A.tcnt = ws->tcnt;
+    A.tfill = ws->tfill;
+    A.tcol = ws->tcol;
+    A.tcw = p->metric == DUPIN_DG ? nullptr : ws->tcw;
+    A.tarc_cap = ws->tarc_cap;
+    return A;
+}
+
+// Enqueue a whole peel on 'stream' (no host synchronisation).
+__global__ void k_ctl_reset(PeelCtl *c) {
+    PeelCtl z;
+    memset(&z, 0, sizeof(z));
+    z.init_min = kMaxLL;
+    *c = z;
+}
+
+int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, long long tail_cap,
+                 long long max_rounds, cudaStream_t s) {
+    PeelArgs A = make_args(g, ws, p, tail_cap, max_rounds);
+    const bool timing = (p->flags & DUPIN_TIMING) != 0;
+    if (timing && !ws->ev[0]) {
+        for (int j = 0; j < 5; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
+    }
+    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[0], s));
+    k_ctl_reset<<<1, 1, 0, s>>>(ws->ctl);
+    int rc = launch_init_weights(A.g, p->metric, ws->w, ws->pr, ws->live0, ws->ctl, false, s);
+    if (rc) return rc;
+    k_init_finish<<<1, 1, 0, s>>>(A, g->n);
+    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[1], s));
+    if (g->n > tail_cap) {
+        void *args[] = {&A};
+        cudaError_t e = cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(ws->grid), dim3(BULK_THREADS), args, 0, s);
+        if (e != cudaSuccess) return dupin_cuda_fail(e, "cooperative launch of k_peel_bulk");
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
+    DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tcnt, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
+    DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tfill, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
+    k_tail_prep<<<sms * 2, 256, 0, s>>>(A);
+    k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A, ws->tdeg, nullptr);
+    k_tail_arcs<0><<<sms * 2, BULK_THREADS, 0, s>>>(A);
+    // tcnt -> tlrp
+    PeelArgs A2 = A;
+    k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A2, ws->tlrp, ws->tcnt);
+    k_tail_arcs<1><<<sms * 2, BULK_THREADS, 0, s>>>(A);
+    rc = set_tail_smem();
+    if (rc) return rc;
+    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[3], s));
+    k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(tail_cap), s>>>(A);
+    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[4], s));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "peel kernels");
+    return DUPIN_OK;
+}
+
+int peel_resolve(const dupin_graph *g, const dupin_params *p, long long *tail_cap, long long *max_rounds,
+                 long long *tr_cap) {
+    int rc = check_params(g, p);
+    if (rc) return rc;
+    long long lim = tail_cap_limit();
+    *tail_cap = p->tail_cap > 0 ? std::min<long long>(p->tail_cap, lim) : tail_cap_default();
+    *max_rounds = p->max_rounds > 0 ? p->max_rounds : g->n + 1;
+    *tr_cap = std::min<long long>(*max_rounds, g->n) + 1;
+    return DUPIN_OK;
+}
+
+int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, dupin_result *r, cudaStream_t s) {
+    PeelCtl c;
+    DUPIN_CUDA_TRY(cudaMemcpyAsync(&c, ws->ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    DUPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    r->n_rounds = c.round;
+    r->n_min_rule = c.n_min_rule;
+    r->n_bulk_rounds = c.bulk_rounds;
+    for (int j = 0; j < 4; j++) r->phase_ms[j] = 0.f;
+    if ((p->flags & DUPIN_TIMING) && ws->ev[0]) {
+        for (int j = 0; j < 4; j++) cudaEventElapsedTime(&r->phase_ms[j], ws->ev[j], ws->ev[j + 1]);
+    }
+    if (c.error) {
+        const char *why = c.error == DUPIN_ERR_NO_PROGRESS ? "max_rounds reached before the set became empty"
+                          : c.error == DUPIN_ERR_TIMEOUT   ? "an in-kernel grid barrier timed out"
+                          : c.error == DUPIN_ERR_OVERFLOW  ? "peeling weight overflow"
+                          : c.error == DUPIN_ERR_OOM       ? "tail sub-graph exceeds its buffer"
+                                                           : "peel failed";
+        return dupin_fail(c.error, why);
+    }
+    if (c.status != ST_DONE) return dupin_fail(DUPIN_ERR_CUDA, "peel did not complete");
+    r->best_round = c.best_round;
+    r->best_size = c.best_size;
+    r->best_f_hi = (long long)c.bf_hi;
+    r->best_f_lo = c.bf_lo;
+    {
+        u128 bf = mk128(c.bf_lo, c.bf_hi);
+        r->best_density = c.best_size > 0 ? (double)bf / 4294967296.0 / (double)c.best_size : 0.0;
+    }
+    const bool dev = (p->flags & DUPIN_RESULT_DEVICE) != 0;
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const long long n = g->n;
+    if (r->best_mask && n > 0) {
+        int sms = 0, d = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        uint8_t *dst = dev ? r->best_mask : ws->mask;
+        k_finalize<<<sms * 4, 256, 0, s>>>(ws->pr, n, ws->ctl, dst);
+        if (!dev) DUPIN_CUDA_TRY(cudaMemcpyAsync(r->best_mask, ws->mask, (size_t)n, cudaMemcpyDeviceToHost, s));
+    }
+    if (r->peel_round && n > 0)
+        DUPIN_CUDA_TRY(cudaMemcpyAsync(r->peel_round, ws->pr, sizeof(int) * (size_t)n, kind, s));
+    const long long nt = c.round + 1;
+    bool trace_short = false;
+    if (r->trace_f_hi || r->trace_f_lo || r->trace_size || r->trace_peeled) {
+        long long cnt = std::min<long long>(nt, (long long)r->trace_cap);
+        if (r->trace_cap < nt) trace_short = true;
+        if (cnt > 0) {
+            if (r->trace_f_hi) DUPIN_CUDA_TRY(cudaMemcpyAsync(r->trace_f_hi, ws->tr_f_hi, 8 * (size_t)cnt, kind, s));
+            if (r->trace_f_lo) DUPIN_CUDA_TRY(cudaMemcpyAsync(r->trace_f_lo, ws->tr_f_lo, 8 * (size_t)cnt, kind, s));
+            if (r->trace_size) DUPIN_CUDA_TRY(cudaMemcpyAsync(r->trace_size, ws->tr_size, 8 * (size_t)cnt, kind, s));
+            if (r->trace_peeled) DUPIN_CUDA_TRY(cudaMemcpyAsync(r->trace_peeled, ws->tr_peeled, 8 * (size_t)cnt, kind, s));
+        }
+    }
+    DUPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (trace_short)
+        return dupin_fail(DUPIN_ERR_BUFFER_TOO_SMALL, "trace_cap < n_rounds + 1 (n_rounds is filled)");
+    return DUPIN_OK;
+}
+
+extern "C" int dupin_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, void *stream) {
+    if (!g) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph is NULL");
+    if (!r) return dupin_fail(DUPIN_ERR_INVALID_ARG, "result is NULL");
+    long long tail_cap, max_rounds, tr_cap;
+    int rc = peel_resolve(g, p, &tail_cap, &max_rounds, &tr_cap);
+    if (rc) return rc;
+    DUPIN_CUDA_TRY(cudaSetDevice(g->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = workspace_ensure(g, tail_cap, tr_cap);
+    if (rc) return rc;
+    rc = enqueue_peel(g, g->ws, p, tail_cap, max_rounds, s);
+    if (rc) return rc;
+    return peel_finish(g, g->ws, p, r, s);
+}

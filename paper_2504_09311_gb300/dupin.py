@@ -1,0 +1,344 @@
+"""Thin ctypes binding of libdupin.so (include/dupin.h): argument marshalling only.
+
+Every step of the peel runs in the library's CUDA kernels; this module only
+packs pointers and sizes.  Device buffers are torch tensors (torch is used for
+device memory and streams), host buffers are numpy arrays.  There is no CPU
+fallback: if the library is missing, importing ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdupin.so")
+
+DG, DW, FD = 0, 1, 2
+METRICS = {"dg": DG, "dw": DW, "fd": FD}
+DEVICE_PTRS = 1
+GPO = 1
+RESULT_DEVICE = 8
+TIMING = 16
+
+OK = 0
+ERR_INVALID_ARG, ERR_OVERFLOW, ERR_OOM, ERR_BUFFER_TOO_SMALL = -1, -2, -3, -4
+ERR_NO_PROGRESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_FOUND = -5, -6, -7, -8
+
+
+class DupinError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dupin error {code}: {msg}")
+        self.code = code
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_left", ctypes.c_int64), ("n_right", ctypes.c_int64),
+                ("csr_ptr", ctypes.c_void_p), ("csr_idx", ctypes.c_void_p), ("csr_w", ctypes.c_void_p),
+                ("csc_ptr", ctypes.c_void_p), ("csc_idx", ctypes.c_void_p), ("csc_w", ctypes.c_void_p),
+                ("vertex_w", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("metric", ctypes.c_int32), ("k_mult", ctypes.c_int32), ("eps_num", ctypes.c_int64),
+                ("eps_den", ctypes.c_int64), ("max_rounds", ctypes.c_int64), ("flags", ctypes.c_uint32),
+                ("tail_cap", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("best_mask", ctypes.c_void_p), ("peel_round", ctypes.c_void_p),
+                ("trace_f_hi", ctypes.c_void_p), ("trace_f_lo", ctypes.c_void_p), ("trace_size", ctypes.c_void_p),
+                ("trace_peeled", ctypes.c_void_p), ("trace_cap", ctypes.c_int64), ("n_rounds", ctypes.c_int64),
+                ("best_round", ctypes.c_int64), ("best_size", ctypes.c_int64), ("best_f_hi", ctypes.c_int64),
+                ("best_f_lo", ctypes.c_uint64), ("best_density", ctypes.c_double), ("n_min_rule", ctypes.c_int64),
+                ("n_bulk_rounds", ctypes.c_int64), ("phase_ms", ctypes.c_float * 4)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("queued", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("graphs_per_s", ctypes.c_double)]
+
+
+# every symbol include/dupin.h declares
+EXPORTS = ["dupin_graph_load", "dupin_graph_free", "dupin_graph_info", "dupin_peel", "dupin_peel_batch",
+           "dupin_serve_create", "dupin_serve_submit", "dupin_serve_poll", "dupin_serve_wait", "dupin_serve_stats",
+           "dupin_serve_destroy", "dupin_last_error", "dupin_version"]
+
+_lib = None
+
+
+def lib():
+    """Load libdupin.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libdupin.so not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.dupin_graph_load.argtypes = [ctypes.POINTER(GraphDesc), P, ctypes.POINTER(P)]
+        L.dupin_graph_free.argtypes = [P]
+        L.dupin_graph_info.argtypes = [P, P, P, P, P]
+        L.dupin_peel.argtypes = [P, ctypes.POINTER(Params), ctypes.POINTER(Result), P]
+        L.dupin_peel_batch.argtypes = [P, P, P, i64, P]
+        L.dupin_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]
+        L.dupin_serve_submit.argtypes = [P, P, ctypes.POINTER(Params), ctypes.POINTER(Result),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.dupin_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.dupin_serve_wait.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+        L.dupin_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
+        L.dupin_serve_destroy.argtypes = [P]
+        L.dupin_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+        L.dupin_version.restype = ctypes.c_char_p
+        for nm in EXPORTS:
+            if nm != "dupin_version":
+                getattr(L, nm).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().dupin_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(rc: int):
+    if rc != OK:
+        raise DupinError(rc, last_error())
+
+
+def _addr(x) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return x.data_ptr()  # torch tensor
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """A graph resident in device memory (dupin_graph)."""
+
+    def __init__(self, handle: int, n: int, m: int, n_left: int, n_right: int):
+        self._h = ctypes.c_void_p(handle)
+        self.n, self.m, self.n_left, self.n_right = n, m, n_left, n_right
+
+    @property
+    def handle(self):
+        return self._h
+
+    @classmethod
+    def load_bipartite(cls, n_left, n_right, csr_ptr, csr_idx, csr_w, csc_ptr, csc_idx, csc_w, vertex_w=None,
+                       device_ptrs=False, stream=None) -> "Graph":
+        keep = [csr_ptr, csr_idx, csr_w, csc_ptr, csc_idx, csc_w, vertex_w]
+        d = GraphDesc(n_left, n_right, _addr(csr_ptr), _addr(csr_idx), _addr(csr_w), _addr(csc_ptr),
+                      _addr(csc_idx), _addr(csc_w), _addr(vertex_w), DEVICE_PTRS if device_ptrs else 0)
+        h = ctypes.c_void_p()
+        check(lib().dupin_graph_load(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        del keep
+        m = int(csr_ptr[-1]) if not device_ptrs else int(csr_ptr[-1].item())
+        return cls(h.value, n_left + n_right, m, n_left, n_right)
+
+    @classmethod
+    def load_symmetric(cls, n, row_ptr, col_idx, w=None, vertex_w=None, device_ptrs=False, stream=None) -> "Graph":
+        keep = [row_ptr, col_idx, w, vertex_w]
+        d = GraphDesc(n, 0, _addr(row_ptr), _addr(col_idx), _addr(w), None, None, None, _addr(vertex_w),
+                      DEVICE_PTRS if device_ptrs else 0)
+        h = ctypes.c_void_p()
+        check(lib().dupin_graph_load(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        del keep
+        arcs = int(row_ptr[-1]) if not device_ptrs else int(row_ptr[-1].item())
+        return cls(h.value, n, arcs // 2, n, 0)
+
+    @classmethod
+    def from_synth(cls, g, stream=None) -> "Graph":
+        """Load a synth.SynthGraph from host arrays (bipartite as CSR + CSC)."""
+        if g.bipartite:
+            csr_ptr, csr_idx, csr_w, csc_ptr, csc_idx, csc_w = g.bipartite_csr()
+            return cls.load_bipartite(g.n_left, g.n_right, csr_ptr, csr_idx, csr_w, csc_ptr, csc_idx, csc_w, g.a,
+                                      stream=stream)
+        ptr, idx, w = g.symmetric_csr()
+        return cls.load_symmetric(g.n, ptr, idx, w, g.a, stream=stream)
+
+    def info(self):
+        n, m, a, b = (ctypes.c_int64() for _ in range(4))
+        check(lib().dupin_graph_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(a), ctypes.byref(b)))
+        return {"n": n.value, "m": m.value, "arcs": a.value, "device_bytes": b.value}
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().dupin_graph_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_params(metric="dg", k_mult=1, eps=(1, 10), max_rounds=0, flags=0, tail_cap=0) -> Params:
+    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+    return Params(m, k_mult, eps[0], eps[1], max_rounds, flags, tail_cap)
+
+
+@dataclass
+class PeelOutput:
+    n_rounds: int
+    best_round: int
+    best_size: int
+    best_f: int
+    best_density: float
+    n_min_rule: int
+    peel_round: Optional[object] = None
+    best_mask: Optional[object] = None
+    trace_f: Optional[list] = None
+    trace_size: Optional[object] = None
+    trace_peeled: Optional[object] = None
+
+
+def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> Result:
+    r = Result()
+    r.best_mask = _addr(best_mask)
+    r.peel_round = _addr(peel_round)
+    if trace is not None:
+        r.trace_f_hi, r.trace_f_lo, r.trace_size, r.trace_peeled = (_addr(t) for t in trace)
+    r.trace_cap = trace_cap
+    return r
+
+
+def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
+    out = PeelOutput(r.n_rounds, r.best_round, r.best_size, (int(r.best_f_hi) << 64) + int(r.best_f_lo),
+                     r.best_density, r.n_min_rule, peel_round, best_mask)
+    if trace is not None:
+        R = r.n_rounds + 1
+        fh, fl, sz, pe = trace
+        if isinstance(fh, np.ndarray):
+            out.trace_f = [(int(fh[i]) << 64) + int(np.uint64(fl[i])) for i in range(R)]
+            out.trace_size, out.trace_peeled = sz[:R], pe[:R]
+    return out
+
+
+def peel(g: Graph, metric="dg", k_mult=1, eps=(1, 10), flags=0, max_rounds=0, tail_cap=0, want_rounds=True,
+         want_mask=True, want_trace=True, stream=None) -> PeelOutput:
+    """dupin_peel with host result buffers (numpy)."""
+    p = make_params(metric, k_mult, eps, max_rounds, flags, tail_cap)
+    pr = np.empty(g.n, np.int32) if want_rounds else None
+    mk = np.empty(g.n, np.uint8) if want_mask else None
+    trace = None
+    cap = 0
+    if want_trace:
+        cap = g.n + 2
+        trace = (np.zeros(cap, np.int64), np.zeros(cap, np.uint64), np.zeros(cap, np.int64), np.zeros(cap, np.int64))
+    r = _result_struct(pr, mk, trace, cap)
+    check(lib().dupin_peel(g.handle, ctypes.byref(p), ctypes.byref(r), _stream(stream)))
+    return _output(r, pr, mk, trace)
+
+
+def peel_device(g: Graph, params: Params, peel_round=None, best_mask=None, stream=None) -> Result:
+    """dupin_peel writing peel_round / best_mask into device tensors (DUPIN_RESULT_DEVICE)."""
+    p = Params.from_buffer_copy(params)
+    p.flags |= RESULT_DEVICE
+    r = _result_struct(peel_round, best_mask, None, 0)
+    check(lib().dupin_peel(g.handle, ctypes.byref(p), ctypes.byref(r), _stream(stream)))
+    return r
+
+
+def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=True, want_trace=False, stream=None):
+    """dupin_peel_batch with host result buffers; returns a list of PeelOutput."""
+    k = len(graphs)
+    G = (ctypes.c_void_p * k)(*[g.handle.value for g in graphs])
+    P = (Params * k)(*params)
+    R = (Result * k)()
+    keep = []
+    for j, g in enumerate(graphs):
+        pr = np.empty(g.n, np.int32) if want_rounds else None
+        trace = None
+        cap = 0
+        if want_trace:
+            cap = g.n + 2
+            trace = (np.zeros(cap, np.int64), np.zeros(cap, np.uint64), np.zeros(cap, np.int64),
+                     np.zeros(cap, np.int64))
+        R[j] = _result_struct(pr, None, trace, cap)
+        keep.append((pr, trace))
+    check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
+                                 ctypes.cast(R, ctypes.c_void_p), k, _stream(stream)))
+    return [_output(R[j], keep[j][0], None, keep[j][1]) for j in range(k)]
+
+
+class Server:
+    """dupin_serve_*: continuous batching of peel requests over resident graphs."""
+
+    def __init__(self, memory_budget: int, max_slots: int = 64, device: int = 0):
+        cfg = ServeConfig(memory_budget, max_slots, device)
+        h = ctypes.c_void_p()
+        check(lib().dupin_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._pending = {}
+
+    def submit(self, g: Graph, params: Params, want_rounds=True, want_trace=False) -> int:
+        pr = np.empty(g.n, np.int32) if want_rounds else None
+        trace = None
+        cap = 0
+        if want_trace:
+            cap = g.n + 2
+            trace = (np.zeros(cap, np.int64), np.zeros(cap, np.uint64), np.zeros(cap, np.int64),
+                     np.zeros(cap, np.int64))
+        r = _result_struct(pr, None, trace, cap)
+        p = Params.from_buffer_copy(params)
+        t = ctypes.c_uint64()
+        check(lib().dupin_serve_submit(self._h, g.handle, ctypes.byref(p), ctypes.byref(r), ctypes.byref(t)))
+        self._pending[t.value] = (r, p, pr, trace)
+        return t.value
+
+    def poll(self, ticket: int):
+        done, st = ctypes.c_int(), ctypes.c_int()
+        check(lib().dupin_serve_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(st)))
+        return bool(done.value), st.value
+
+    def wait(self, ticket: int) -> PeelOutput:
+        st = ctypes.c_int()
+        check(lib().dupin_serve_wait(self._h, ticket, ctypes.byref(st)))
+        r, p, pr, trace = self._pending.pop(ticket)
+        if st.value != OK:
+            raise DupinError(st.value, f"request {ticket} failed")
+        return _output(r, pr, None, trace)
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        check(lib().dupin_serve_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            check(lib().dupin_serve_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,74 @@
+"""The C-ABI library loads without a GPU and exports every symbol include/dupin.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2504_09311_gb300", "libdupin.so")
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dupin.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dupin_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libdupin():
+    if not os.path.exists(LIB):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    return ctypes.CDLL(LIB)
+
+
+def test_header_declares_expected_api():
+    names = declared_functions()
+    for must in ("dupin_graph_load", "dupin_peel", "dupin_peel_batch", "dupin_serve_create", "dupin_serve_submit"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(libdupin):
+    for name in declared_functions():
+        assert hasattr(libdupin, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2504_09311_gb300 import dupin
+
+    assert sorted(dupin.EXPORTS) == declared_functions()
+
+
+def test_version_and_errors_without_gpu(libdupin):
+    libdupin.dupin_version.restype = ctypes.c_char_p
+    assert libdupin.dupin_version().decode().count(".") == 2
+    # argument validation happens before any device work
+    from paper_2504_09311_gb300 import dupin
+
+    h = ctypes.c_void_p()
+    rc = dupin.lib().dupin_graph_load(None, None, ctypes.byref(h))
+    assert rc == dupin.ERR_INVALID_ARG
+    assert "NULL" in dupin.last_error()
+
+
+def test_struct_layouts_match_header():
+    from paper_2504_09311_gb300 import dupin
+
+    # 2 int64 + 7 pointers + uint32 (+ padding)
+    assert ctypes.sizeof(dupin.GraphDesc) == 2 * 8 + 7 * 8 + 8
+    assert ctypes.sizeof(dupin.Params) == 4 + 4 + 8 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(dupin.Result) == 6 * 8 + 9 * 8 + 4 * 4
+
+
+def test_product_path_does_not_import_oracle():
+    """The package and bench's timed path never reach the oracle."""
+    import glob
+
+    for path in glob.glob(os.path.join(ROOT, "paper_2504_09311_gb300", "**", "*.py"), recursive=True):
+        src = open(path).read()
+        assert "import oracle" not in src and "from oracle" not in src, path
+    for path in glob.glob(os.path.join(ROOT, "paper_2504_09311_gb300", "csrc", "*")):
+        src = open(path).read()
+        assert "dupin_oracle" not in src and "liboracle" not in src, path
