@@ -235,13 +235,16 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
         for (;;) {
             const long long idx = rr + 1 + lane;
             const long long bj = idx <= n ? g.rp[idx] : kMaxLL;
+            // count in [0, 32]: 33 outcomes, so six halving steps
             int lo = 0, hi = 32;
 #pragma unroll
-            for (int s = 0; s < 5; s++) {
-                int mid = (lo + hi) >> 1;
-                long long bm = __shfl_sync(0xffffffffu, bj, mid);
-                if (bm <= x) lo = mid + 1;
-                else hi = mid;
+            for (int s = 0; s < 6; s++) {
+                const int mid = (lo + hi) >> 1;
+                const long long bm = __shfl_sync(0xffffffffu, bj, mid & 31);
+                if (lo < hi) {
+                    if (bm <= x) lo = mid + 1;
+                    else hi = mid;
+                }
             }
             if (owner < 0 && lo < 32) owner = rr + lo;
             if (!__any_sync(0xffffffffu, owner < 0)) break;
@@ -898,8 +901,10 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             ms = s_mn[t] < ms ? s_mn[t] : ms;
             md = s_mn2[t] < md ? s_mn2[t] : md;
         }
-        __syncthreads();
+        // every thread read F right after the select; reset it before the
+        // barrier that precedes the next round's select
         if (tid == 0) s_F = 0;
+        __syncthreads();
         const u128 wsel = mk128(Wl, Wh), internal = mk128(Il, Ih);
         st.f = st.f - (wsel - (internal >> 1));
         st.scan += L;
