@@ -186,6 +186,34 @@ int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result,
 int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
                      int64_t count, void *stream);
 
+/* ------------------------------------------------- peel without allocation */
+
+/*
+ * No counterpart in the paper: an entry point for callers that may not
+ * allocate device memory once running (services that reserve all GPU memory
+ * up front in their own pool, latency-critical loops where cudaMalloc /
+ * cudaFree would synchronise the device and stall other work, plug-ins in a
+ * process whose allocator owns the device).  It runs the same peel as
+ * dupin_peel on a graph of at most DUPIN_NOALLOC_MAX_N vertices given as a
+ * symmetric CSR in DEVICE memory (row_ptr[n+1] int64, col_idx[row_ptr[n]]
+ * int32, arc_w Q32.32 or NULL for DG, vertex_w or NULL), writes peel_round[n]
+ * (device), the scalars of *result, and -- when non-NULL -- result->best_mask
+ * and result->trace_* (device pointers, trace_cap entries).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: its working state is
+ * one fixed file-scope device array (about 100 KB, held by every GPU that
+ * loads the library until exit).  Every call on a device shares that array
+ * and it keeps the last call's contents: calls that overlap on the GPU race
+ * and must be serialised by the caller.  The first call on a device performs
+ * set-up (looks up the array's device address, sets a kernel's shared-memory
+ * limit); make it before any stream capture.  Errors: INVALID_ARG (n outside
+ * 1..DUPIN_NOALLOC_MAX_N, bad CSR or params), OVERFLOW, NO_PROGRESS,
+ * BUFFER_TOO_SMALL, CUDA.  Synchronises 'stream'.
+ */
+#define DUPIN_NOALLOC_MAX_N 8192
+int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const int64_t *arc_w,
+                       const int64_t *vertex_w, const dupin_params *params, int32_t *peel_round,
+                       dupin_result *result, void *stream);
+
 /* ----------------------------------------------------------------- serving */
 
 typedef struct dupin_server dupin_server;

@@ -78,6 +78,9 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
 int launch_init_weights(const DevGraph &dg, int metric, long long *w, int *pr, int *live0, PeelCtl *ctl,
                         bool check, cudaStream_t s);
 
+// a whole peel of a small graph with caller-supplied buffers (no allocation)
+int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStream_t s);
+
 // the largest live set the single-CTA tail accepts, and the default cap
 long long tail_cap_limit();
 long long tail_cap_default();

@@ -1273,6 +1273,22 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
     return DUPIN_OK;
 }
 
+// A whole peel of a graph small enough for the one-CTA kernel, every buffer
+// supplied by the caller through A (no allocation): reset the control block,
+// initial weights (validated when 'check'), round 0, then all rounds in one CTA.
+int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStream_t s) {
+    k_ctl_reset<<<1, 1, 0, s>>>(A.ctl);
+    int rc = launch_init_weights(A.g, metric, A.w, A.pr, A.live0, A.ctl, check, s);
+    if (rc) return rc;
+    k_init_finish<<<1, 1, 0, s>>>(A, A.g.n);
+    rc = set_tail_smem();
+    if (rc) return rc;
+    k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(A.tail_cap), s>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "small-graph peel kernels");
+    return DUPIN_OK;
+}
+
 extern "C" int dupin_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, void *stream) {
     if (!g) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph is NULL");
     if (!r) return dupin_fail(DUPIN_ERR_INVALID_ARG, "result is NULL");

@@ -70,7 +70,9 @@ class ServeStats(ctypes.Structure):
 # every symbol include/dupin.h declares
 EXPORTS = ["dupin_graph_load", "dupin_graph_free", "dupin_graph_info", "dupin_peel", "dupin_peel_batch",
            "dupin_serve_create", "dupin_serve_submit", "dupin_serve_poll", "dupin_serve_wait", "dupin_serve_stats",
-           "dupin_serve_destroy", "dupin_last_error", "dupin_version"]
+           "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc"]
+
+NOALLOC_MAX_N = 8192
 
 _lib = None
 
@@ -96,6 +98,7 @@ def lib():
         L.dupin_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
         L.dupin_serve_destroy.argtypes = [P]
         L.dupin_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+        L.dupin_peel_noalloc.argtypes = [i64, P, P, P, P, ctypes.POINTER(Params), P, ctypes.POINTER(Result), P]
         L.dupin_version.restype = ctypes.c_char_p
         for nm in EXPORTS:
             if nm != "dupin_version":
@@ -287,6 +290,15 @@ def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=Tr
     check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
                                  ctypes.cast(R, ctypes.c_void_p), k, _stream(stream)))
     return [_output(R[j], keep[j][0], None, keep[j][1]) for j in range(k)]
+
+
+def peel_noalloc(n, row_ptr, col_idx, arc_w, vertex_w, params: Params, peel_round, best_mask=None, trace=None,
+                 stream=None) -> Result:
+    """dupin_peel_noalloc: graph (symmetric CSR), peel_round, best_mask and trace are device tensors."""
+    r = _result_struct(None, best_mask, trace, 0 if trace is None else int(trace[0].shape[0]))
+    check(lib().dupin_peel_noalloc(n, _addr(row_ptr), _addr(col_idx), _addr(arc_w), _addr(vertex_w),
+                                   ctypes.byref(params), _addr(peel_round), ctypes.byref(r), _stream(stream)))
+    return r
 
 
 class Server:
