@@ -67,14 +67,25 @@ struct BlockPart {
     long long pad[6];
 };
 
+// Hubs: up to DUPIN_HUB_MAX highest-degree vertices (degree >= DUPIN_HUB_MIN_DEG).
+// An arc whose head is hub number h is stored in col[] as -(h + 1), so the
+// expand can aggregate a round's decrements of a hub in shared memory.
+#define DUPIN_HUB_MAX 1024
+#define DUPIN_HUB_MIN_DEG 1024
+
 struct DevGraph {
     long long n;
     long long arcs;
     const long long *rp;
-    const int *col;
+    const int *col;       // neighbour ids; -(h + 1) for hub number h
     const long long *cw;  // nullptr: DG weights
     const long long *a;   // nullptr: 0
+    const int *hubs;      // hub number -> vertex id
+    int n_hubs;
 };
+
+// neighbour id of an arc's stored column value
+__device__ __forceinline__ int arc_head(int cv, const int *hubs) { return cv >= 0 ? cv : hubs[-cv - 1]; }
 
 struct PeelArgs {
     DevGraph g;
@@ -114,14 +125,42 @@ __host__ __device__ __forceinline__ u128 mk128(unsigned long long lo, unsigned l
     return ((u128)hi << 64) | (u128)lo;
 }
 
+// floor(X / Y) for 1 <= Y < 2^64, saturated to INT64_MAX, with integer
+// operations only (binary long division of the last 63 quotient bits; the
+// quotient is below 2^63 once saturation is ruled out).  Used once per round.
+__device__ __forceinline__ long long floor_div_sat(u128 X, unsigned long long Y) {
+    if (X >= ((u128)Y << 63)) return 0x7fffffffffffffffLL;
+    u128 rem = X >> 63;  // < Y
+    unsigned long long q = 0;
+    for (int b = 62; b >= 0; --b) {
+        rem = (rem << 1) | (u128)((unsigned long long)(X >> b) & 1ull);
+        q <<= 1;
+        if (rem >= (u128)Y) {
+            rem -= Y;
+            q |= 1ull;
+        }
+    }
+    return (long long)q;
+}
+
 // exact threshold floor(num_mul * f / (den_mul * size)), saturated to INT64_MAX
 __device__ __forceinline__ long long floor_ratio(unsigned long long num_mul, u128 f, unsigned long long den_mul,
                                                  long long size) {
-    u128 num = (u128)num_mul * f;
-    u128 den = (u128)den_mul * (u128)(unsigned long long)size;
-    u128 q = num / den;
-    if (q > (u128)0x7fffffffffffffffULL) return 0x7fffffffffffffffLL;
-    return (long long)q;
+    const u128 num = (u128)num_mul * f;
+    const u128 den = (u128)den_mul * (u128)(unsigned long long)size;
+    if (den >> 64) {  // only when den_mul * size >= 2^64 (not reached with the limits on eps and n)
+        u128 q = num / den;
+        return q > (u128)0x7fffffffffffffffULL ? 0x7fffffffffffffffLL : (long long)q;
+    }
+    return floor_div_sat(num, (unsigned long long)den);
+}
+
+// w * Y <= X exactly, for 0 <= w < 2^63 (the division-free form of w <= floor(X / Y))
+__device__ __forceinline__ bool mul_le(long long w, unsigned long long Y, unsigned long long Xhi,
+                                       unsigned long long Xlo) {
+    const unsigned long long lo = (unsigned long long)w * Y;
+    const unsigned long long hi = __umul64hi((unsigned long long)w, Y);
+    return hi < Xhi || (hi == Xhi && lo <= Xlo);
 }
 
 // a/b > c/d for the best-prefix rule (strict: earliest round wins ties)

@@ -55,6 +55,8 @@ struct dupin_graph {
     int *col = nullptr;
     long long *cw = nullptr;
     long long *a = nullptr;
+    int *hubs = nullptr;  // hub number -> vertex id (arcs to hubs are stored as -(h + 1))
+    int n_hubs = 0;
     long long bytes = 0;
     PeelWorkspace *ws = nullptr;
 };

@@ -61,9 +61,97 @@ static int read_last(const int64_t *p, long long idx, bool dev, long long *out) 
     return DUPIN_OK;
 }
 
+// log2 histogram of degrees >= DUPIN_HUB_MIN_DEG
+__global__ void k_deg_hist(const long long *rp, long long n, unsigned long long *hist) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+        const long long d = rp[u + 1] - rp[u];
+        if (d >= DUPIN_HUB_MIN_DEG) atomicAdd(&hist[63 - __clzll(d)], 1ull);
+    }
+}
+
+// hubs[] holds 'cap' entries: exactly the number of vertices with degree >= thr
+__global__ void k_pick_hubs(const long long *rp, long long n, long long thr, int *slot_of, int *hubs, int *nh,
+                            int cap) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+        const long long d = rp[u + 1] - rp[u];
+        if (d >= thr) {
+            const int h = atomicAdd(nh, 1);
+            if (h < cap) {
+                hubs[h] = (int)u;
+                slot_of[u] = h;
+            }
+        }
+    }
+}
+
+__global__ void k_encode_hub_arcs(int *col, long long arcs, const int *slot_of) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < arcs; p += (long long)gridDim.x * blockDim.x) {
+        const int h = slot_of[col[p]];
+        if (h >= 0) col[p] = -(h + 1);
+    }
+}
+
+__global__ void k_fill_i32(int *x, long long n, int v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+// Pick the hubs (at most DUPIN_HUB_MAX vertices, highest degrees first, degree
+// >= DUPIN_HUB_MIN_DEG, threshold a power of two) and re-code their arcs.
+static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
+    if (g->arcs == 0 || g->n == 0) return DUPIN_OK;
+    unsigned long long *hist = nullptr;
+    int *nh = nullptr, *slot_of = nullptr;
+    unsigned long long h[64];
+    cudaError_t e = cudaMalloc((void **)&hist, 64 * sizeof(unsigned long long) + sizeof(int));
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "hub histogram");
+    nh = (int *)(hist + 64);
+    e = cudaMemsetAsync(hist, 0, 64 * sizeof(unsigned long long) + sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_deg_hist<<<grid, 256, 0, s>>>(g->rp, g->n, hist);
+        e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(hist);
+        return dupin_cuda_fail(e, "hub histogram");
+    }
+    // smallest power-of-two threshold >= DUPIN_HUB_MIN_DEG keeping at most
+    // DUPIN_HUB_MAX vertices; cum = number of vertices with degree >= 2^bstar
+    const int bmin = 63 - __builtin_clzll((unsigned long long)DUPIN_HUB_MIN_DEG);
+    int bstar = -1;
+    unsigned long long cum = 0;
+    for (int b = 63; b >= bmin; b--) {
+        if (cum + h[b] > DUPIN_HUB_MAX) break;
+        cum += h[b];
+        bstar = b;
+    }
+    if (bstar < 0 || cum == 0) {
+        cudaFree(hist);
+        return DUPIN_OK;
+    }
+    const long long thr = 1LL << bstar;
+    e = cudaMalloc((void **)&g->hubs, sizeof(int) * (size_t)cum);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&slot_of, sizeof(int) * (size_t)g->n);
+    if (e == cudaSuccess) {
+        k_fill_i32<<<grid, 256, 0, s>>>(slot_of, g->n, -1);
+        k_pick_hubs<<<grid, 256, 0, s>>>(g->rp, g->n, thr, slot_of, g->hubs, nh, (int)cum);
+        k_encode_hub_arcs<<<grid, 256, 0, s>>>(g->col, g->arcs, slot_of);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(slot_of);
+    cudaFree(hist);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "hub selection");
+    g->n_hubs = (int)cum;
+    g->bytes += (long long)sizeof(int) * (long long)cum;
+    return DUPIN_OK;
+}
+
 static void graph_release(dupin_graph *g) {
     if (!g) return;
     workspace_free(g->ws);
+    cudaFree(g->hubs);
     cudaFree(g->rp);
     cudaFree(g->col);
     cudaFree(g->cw);
@@ -195,7 +283,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         memset(&hc, 0, sizeof(hc));
         hc.init_min = 0x7fffffffffffffffLL;
         cudaMemcpyAsync(ctl, &hc, sizeof(PeelCtl), cudaMemcpyHostToDevice, s);
-        DevGraph dg;
+        DevGraph dg = {};
         dg.n = n;
         dg.arcs = arcs;
         dg.rp = g->rp;
@@ -232,6 +320,11 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
     }
 #undef TRY
     cudaFree(bad);
+    rc = select_hubs(g, grid, s);
+    if (rc) {
+        graph_release(g);
+        return rc;
+    }
     *out = g;
     return DUPIN_OK;
 }

@@ -41,7 +41,9 @@
 #define WALK_WIN 1024
 #define INIT_THREADS 256
 #define INIT_WARPS (INIT_THREADS / 32)
-#define TAIL_THREADS 1024
+#ifndef TAIL_THREADS
+#define TAIL_THREADS 512
+#endif
 #define TAIL_WARPS (TAIL_THREADS / 32)
 #define SCAN_THREADS 1024
 
@@ -217,6 +219,8 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
     long long r = warp_search_last_le(g.rp, n, we0);  // row of the first arc
     long long carry_own = -1, carry_val = 0;
     bool bad = false;
+    long long r_end = g.rp[r + 1];  // end of row r
+    long long lacc = 0;             // per-lane partial sum of row r over whole-row chunks
     for (long long x0 = we0; x0 < we1; x0 += 32) {
         const long long x = x0 + lane;
         const bool valid = x < we1;
@@ -225,6 +229,29 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
         if (CHECK && valid) {
             int v = g.col[x];
             if (v < 0 || v >= n || val < 0) bad = true;
+        }
+        // fast path: the whole chunk lies in row r (long rows, hubs)
+        const long long cend = x0 + 32 < we1 ? x0 + 32 : we1;
+        if (cend <= r_end) {
+            if (CHECK && valid && g.col[x] == r) bad = true;  // self-loop
+            if (CHECK && (unsigned long long)lacc + (unsigned long long)val < (unsigned long long)lacc) bad = true;
+            lacc += val;
+            continue;
+        }
+        // leaving row r inside this chunk: fold the lanes' partials into the carry
+        {
+            long long sum = warp_sum64(lacc);
+            sum = __shfl_sync(0xffffffffu, sum, 0);
+            lacc = 0;
+            if (sum != 0) {
+                if (carry_own == r) carry_val += sum;
+                else {
+                    if (carry_own >= 0 && lane == 0)
+                        atomicAdd((unsigned long long *)&w[carry_own], (unsigned long long)carry_val);
+                    carry_own = r;
+                    carry_val = sum;
+                }
+            }
         }
         // Row of each lane's arc: with the 32 row ends rp[rr+1 .. rr+32] held
         // one per lane, a lane whose arc x has rp[rr] <= x < rp[rr+32] lies in
@@ -294,6 +321,20 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
         carry_val = lastsum + (oL == o0 ? add : 0);
         carry_own = oL;
         r = oL;  // the next chunk starts in this row or later
+        r_end = g.rp[r + 1];
+    }
+    {
+        long long sum = warp_sum64(lacc);
+        sum = __shfl_sync(0xffffffffu, sum, 0);
+        if (sum != 0) {
+            if (carry_own == r) carry_val += sum;
+            else {
+                if (carry_own >= 0 && lane == 0)
+                    atomicAdd((unsigned long long *)&w[carry_own], (unsigned long long)carry_val);
+                carry_own = r;
+                carry_val = sum;
+            }
+        }
     }
     if (carry_own >= 0 && lane == 0) {
         if (CHECK) {
@@ -394,7 +435,7 @@ struct RoundState {
     long long gpo_le, n_min_rule, scan;
 };
 
-__global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
+__global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
     __shared__ long long s_v[BULK_WARPS][6];
     __shared__ unsigned long long s_lo[BULK_WARPS], s_hi[BULK_WARPS];
     __shared__ long long s_mn[BULK_WARPS];
@@ -402,12 +443,20 @@ __global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
     __shared__ unsigned long long s_surv;
     __shared__ long long s_base[WALK_WIN + 1];
     __shared__ long long s_start[WALK_WIN + 1];
+    __shared__ int s_hub[DUPIN_HUB_MAX];
+    __shared__ unsigned long long s_hacc[DUPIN_HUB_MAX];
 
     const unsigned G = gridDim.x;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     PeelCtl *ctl = A.ctl;
     const DevGraph g = A.g;
     const bool dg = g.cw == nullptr;
+    const int nh = g.n_hubs;
+    for (int h = tid; h < nh; h += BULK_THREADS) {
+        s_hub[h] = g.hubs[h];
+        s_hacc[h] = 0;
+    }
+    __syncthreads();
 
     RoundState st;
     st.round = ctl->round;
@@ -437,106 +486,114 @@ __global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
             st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
             T = st.gpo_le > T ? st.gpo_le : T;
         }
-        const bool minrule = A.use_min && st.minw > T;
-        const long long thr = minrule ? st.minw : T;
-
-        // ---------------- phase A: select
         int *live = st.live_sel ? A.live1 : A.live0;
         int *nlive = st.live_sel ? A.live0 : A.live1;
         const long long L = st.live_len;
         const long long j0 = (long long)(((u128)L * b) / G), j1 = (long long)(((u128)L * (b + 1)) / G);
-        if (tid == 0) s_pack = 0;
-        __syncthreads();
-        long long cnt = 0, surv = 0, minsurv = kMaxLL;
-        unsigned long long wlo = 0, whi = 0;
-        for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
-            const long long j = jb + lane;
-            int id = j < j1 ? live[j] : -1;
-            long long wv = 0;
-            if (id >= 0) wv = A.w[id];
-            const bool sel = id >= 0 && wv <= thr;
-            if (id >= 0 && !sel) {
-                surv++;
-                minsurv = wv < minsurv ? wv : minsurv;
-            }
-            long long start = 0, deg = 0;
-            if (sel) {
-                cnt++;
-                add128(wlo, whi, (unsigned long long)wv, 0);
-                A.pr[id] = (int)i;
-                live[j] = -1;
-                start = g.rp[id];
-                deg = g.rp[id + 1] - start;
-            }
-            const bool stage = sel && deg > 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, stage);
-            if (bal) {
-                long long incl = warp_incl_scan64(stage ? deg : 0);
-                long long tot = __shfl_sync(0xffffffffu, incl, 31);
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&s_pack, ((unsigned long long)__popc(bal) << 40) | (unsigned long long)tot);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (stage) {
-                    long long slot = (long long)(base >> 40) + __popc(bal & ((1u << lane) - 1u));
-                    long long off = (long long)(base & ((1ull << 40) - 1)) + incl - deg;
-                    A.stage_start[j0 + slot] = start;
-                    A.stage_off[j0 + slot] = off;
+        // Phase A selects w <= T.  If no block selected anything (possible only
+        // when k(1+eps) < 2), the round takes the minimum rule: phase A runs a
+        // second time with the minimum live weight, which the first pass found.
+        long long thr = T;
+        bool minrule = false;
+        long long U_sel = 0, U_stage = 0, totArcs = 0, slotBase = 0, arcBase = 0, survBase = 0;
+        unsigned long long Wlo = 0, Whi = 0;
+        for (int pass = 0;; pass++) {
+            // ---------------- phase A: select
+            if (tid == 0) s_pack = 0;
+            __syncthreads();
+            long long cnt = 0, surv = 0, minsurv = kMaxLL;
+            unsigned long long wlo = 0, whi = 0;
+            for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
+                const long long j = jb + lane;
+                int id = j < j1 ? live[j] : -1;
+                long long wv = 0;
+                if (id >= 0) wv = A.w[id];
+                const bool sel = id >= 0 && wv <= thr;
+                if (id >= 0 && !sel) {
+                    surv++;
+                    minsurv = wv < minsurv ? wv : minsurv;
+                }
+                long long start = 0, deg = 0;
+                if (sel) {
+                    cnt++;
+                    add128(wlo, whi, (unsigned long long)wv, 0);
+                    A.pr[id] = (int)i;
+                    live[j] = -1;
+                    start = g.rp[id];
+                    deg = g.rp[id + 1] - start;
+                }
+                const bool stage = sel && deg > 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, stage);
+                if (bal) {
+                    long long incl = warp_incl_scan64(stage ? deg : 0);
+                    long long tot = __shfl_sync(0xffffffffu, incl, 31);
+                    unsigned long long base = 0;
+                    if (lane == 0)
+                        base = atomicAdd(&s_pack, ((unsigned long long)__popc(bal) << 40) | (unsigned long long)tot);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (stage) {
+                        long long slot = (long long)(base >> 40) + __popc(bal & ((1u << lane) - 1u));
+                        long long off = (long long)(base & ((1ull << 40) - 1)) + incl - deg;
+                        A.stage_start[j0 + slot] = start;
+                        A.stage_off[j0 + slot] = off;
+                    }
                 }
             }
-        }
-        {
-            BlockRed<BULK_WARPS, 6> r;
-            r.v[0] = cnt; r.v[1] = surv; r.v[2] = 0; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
-            r.lo = wlo; r.hi = whi; r.mn = minsurv;
-            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
-            if (tid == 0) {
-                BlockPart &p = A.part[b];
-                p.sel_cnt = r.v[0];
-                p.surv_cnt = r.v[1];
-                p.ws_lo = r.lo;
-                p.ws_hi = r.hi;
-                p.min_surv = r.mn;
-                p.stage_cnt = (long long)(s_pack >> 40);
-                p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
-            }
-        }
-        if (!grid_barrier(ctl, G)) return;
-
-        // ---------------- phase B: totals, frontier placement, compaction
-        long long U_sel, U_stage, totArcs, survTot, slotBase, arcBase, survBase, myStage, myDeg;
-        unsigned long long Wlo, Whi;
-        long long minSurvAll;
-        {
-            BlockRed<BULK_WARPS, 6> r;
-            for (int j = 0; j < 6; j++) r.v[j] = 0;
-            r.lo = 0; r.hi = 0; r.mn = kMaxLL;
-            // v: 0 sel_cnt, 1 stage_cnt, 2 sel_deg, 3 surv, 4 stage before b, 5 deg before b
-            long long survBefore = 0;
-            for (int t = tid; t < (int)G; t += BULK_THREADS) {
-                const BlockPart &p = A.part[t];
-                r.v[0] += p.sel_cnt;
-                r.v[1] += p.stage_cnt;
-                r.v[2] += p.sel_deg;
-                r.v[3] += p.surv_cnt;
-                if (t < b) {
-                    r.v[4] += p.stage_cnt;
-                    r.v[5] += p.sel_deg;
-                    survBefore += p.surv_cnt;
+            {
+                BlockRed<BULK_WARPS, 6> r;
+                r.v[0] = cnt; r.v[1] = surv; r.v[2] = 0; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
+                r.lo = wlo; r.hi = whi; r.mn = minsurv;
+                block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+                if (tid == 0) {
+                    BlockPart &p = A.part[b];
+                    p.sel_cnt = r.v[0];
+                    p.surv_cnt = r.v[1];
+                    p.ws_lo = r.lo;
+                    p.ws_hi = r.hi;
+                    p.min_surv = r.mn;
+                    p.stage_cnt = (long long)(s_pack >> 40);
+                    p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
                 }
-                add128(r.lo, r.hi, p.ws_lo, p.ws_hi);
-                r.mn = p.min_surv < r.mn ? p.min_surv : r.mn;
             }
-            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
-            U_sel = r.v[0]; U_stage = r.v[1]; totArcs = r.v[2]; survTot = r.v[3];
-            slotBase = r.v[4]; arcBase = r.v[5];
-            Wlo = r.lo; Whi = r.hi; minSurvAll = r.mn;
-            // survivors before b: one more (cheap) reduction
-            BlockRed<BULK_WARPS, 6> r2;
-            for (int j = 0; j < 6; j++) r2.v[j] = 0;
-            r2.v[0] = survBefore;
-            r2.lo = 0; r2.hi = 0; r2.mn = kMaxLL;
-            block_reduce<BULK_WARPS, 6>(r2, s_v, s_lo, s_hi, s_mn);
-            survBase = r2.v[0];
+            if (!grid_barrier(ctl, G)) return;
+            // ---------------- phase B (part 1): totals and this block's offsets
+            long long minSurvAll;
+            {
+                BlockRed<BULK_WARPS, 6> r;
+                for (int j = 0; j < 6; j++) r.v[j] = 0;
+                r.lo = 0; r.hi = 0; r.mn = kMaxLL;
+                // v: 0 sel_cnt, 1 stage_cnt, 2 sel_deg, 3 survivors before b,
+                //    4 stage entries before b, 5 arcs before b
+                for (int t = tid; t < (int)G; t += BULK_THREADS) {
+                    const BlockPart &p = A.part[t];
+                    r.v[0] += p.sel_cnt;
+                    r.v[1] += p.stage_cnt;
+                    r.v[2] += p.sel_deg;
+                    if (t < b) {
+                        r.v[3] += p.surv_cnt;
+                        r.v[4] += p.stage_cnt;
+                        r.v[5] += p.sel_deg;
+                    }
+                    add128(r.lo, r.hi, p.ws_lo, p.ws_hi);
+                    r.mn = p.min_surv < r.mn ? p.min_surv : r.mn;
+                }
+                block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+                U_sel = r.v[0]; U_stage = r.v[1]; totArcs = r.v[2];
+                survBase = r.v[3]; slotBase = r.v[4]; arcBase = r.v[5];
+                Wlo = r.lo; Whi = r.hi; minSurvAll = r.mn;
+            }
+            if (U_sel > 0 || pass > 0 || !A.use_min || minSurvAll == kMaxLL) break;
+            thr = minSurvAll;  // every live vertex survived the threshold: minimum rule
+            minrule = true;
+            // every block has read the partials before the second pass rewrites them
+            if (!grid_barrier(ctl, G)) return;
+        }
+        if (U_sel == 0) {  // cannot happen (Lemma 4.2 / minimum rule): stop rather than spin
+            if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
+            return;
+        }
+        long long myStage, myDeg;
+        {
             myStage = A.part[b].stage_cnt;
             myDeg = A.part[b].sel_deg;
         }
@@ -575,7 +632,6 @@ __global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
                 }
             }
         }
-        (void)survTot;
         if (!grid_barrier(ctl, G)) return;
 
         // ---------------- phase C: expand
@@ -592,27 +648,37 @@ __global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
                 const long long *cw = g.cw;
                 int *pr = A.pr;
                 long long *w = A.w;
-                const bool use_min = A.use_min != 0;
                 walk_arcs([=](long long k) { return fb[k]; },
                           [=](long long k) { return fs[k]; }, U_stage, E0, E1, k0, s_base, s_start,
                           [&](long long k, long long pos) {
                               (void)k;
-                              const int v = col[pos];
+                              const int cv = col[pos];
                               const long long c = dg ? DUPIN_Q_ONE : cw[pos];
-                              const int p = pr[v];
-                              if (p > (int)i) {
-                                  if (use_min) {
-                                      long long old = (long long)atomicAdd((unsigned long long *)&w[v],
-                                                                           (unsigned long long)(-c));
-                                      long long nw = old - c;
-                                      mindec = nw < mindec ? nw : mindec;
-                                  } else {
-                                      atomicAdd((unsigned long long *)&w[v], (unsigned long long)(-c));
+                              if (cv >= 0) {
+                                  const int p = pr[cv];
+                                  if (p > (int)i) {
+                                      // result unused: a fire-and-forget reduction
+                                      atomicAdd((unsigned long long *)&w[cv], (unsigned long long)(-c));
+                                  } else if (p == (int)i) {
+                                      add128(ilo, ihi, (unsigned long long)c, 0);
                                   }
-                              } else if (p == (int)i) {
-                                  add128(ilo, ihi, (unsigned long long)c, 0);
+                              } else {  // hub head: aggregate in shared memory
+                                  const int h = -cv - 1;
+                                  const int p = pr[s_hub[h]];
+                                  if (p > (int)i) atomicAdd(&s_hacc[h], (unsigned long long)c);
+                                  else if (p == (int)i) add128(ilo, ihi, (unsigned long long)c, 0);
                               }
                           });
+            }
+        }
+        if (nh > 0) {  // one reduction per hub touched by this block
+            __syncthreads();
+            for (int h = tid; h < nh; h += BULK_THREADS) {
+                const unsigned long long a = s_hacc[h];
+                if (a) {
+                    atomicAdd((unsigned long long *)&A.w[s_hub[h]], (unsigned long long)0 - a);
+                    s_hacc[h] = 0;
+                }
             }
         }
         {
@@ -645,7 +711,6 @@ __global__ void __launch_bounds__(BULK_THREADS) k_peel_bulk(PeelArgs A) {
             st.size = newSize;
             st.round = i;
             st.n_min_rule += minrule ? 1 : 0;
-            if (A.use_min) st.minw = minSurvAll < r.mn ? minSurvAll : r.mn;
             if (compact) {
                 st.live_sel ^= 1;
                 st.live_len = newSize;
@@ -745,12 +810,13 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
     __syncthreads();
     const long long k0 = s_k0;
     const int *col = A.g.col;
+    const int *hubs = A.g.hubs;
     const long long *cw = A.g.cw;
     const int *pr = A.pr;
     walk_arcs([=](long long k) { return tdeg[k]; },
               [=](long long k) { return rp[live[k]]; }, L, e0, e1, k0, s_base, s_start,
               [&](long long k, long long pos) {
-                  const int v = col[pos];
+                  const int v = arc_head(col[pos], hubs);
                   if (pr[v] != DUPIN_LIVE) return;
                   if (PASS == 0) {
                       atomicAdd(&A.tcnt[k], 1);
@@ -762,156 +828,258 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
               });
 }
 
-// One CTA finishes the peel on the live sub-graph held in shared memory:
-// tw[L] weights, ts[L] states, tf[L] the round's frontier (local ids).
+// Shared accumulator of one tail round (double-buffered by round parity).
+struct TailAcc {
+    unsigned long long wlo, whi;  // sum of the removed vertices' weights
+    unsigned long long ilo, ihi;  // sum of c over arcs inside U
+    unsigned int F;               // |U_i|
+    unsigned int pad;
+};
+
+// The parameters of one round, computed identically by every warp.
+struct TailRound {
+    long long i;                  // round number
+    unsigned long long Xhi, Xlo;  // X = k (D+N) f
+    unsigned long long Y;         // Y = D |S|
+    long long gle;                // Algorithm 3's floor(tau_max), -1 without GPO
+    long long minw;               // minimum live weight
+    int minrule;                  // threshold selects nobody: take the minimum
+    int done;                     // S is empty
+};
+
+__device__ __forceinline__ void acc_add128(unsigned long long *lo, unsigned long long *hi, unsigned long long xlo,
+                                           unsigned long long xhi) {
+    if (xlo) {
+        unsigned long long old = atomicAdd(lo, xlo);
+        if (old + xlo < old) xhi += 1;
+    }
+    if (xhi) atomicAdd(hi, xhi);
+}
+
+#define TAIL_FAST 32
+#define TAIL_SEG 64  // vertices per segment (one warp, two per lane)
+
+// can segment minimum sm hold a vertex that round R selects?
+__device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) {
+    if (sm == kMaxLL) return false;
+    return R.minrule ? sm == R.minw : (sm <= R.gle || mul_le(sm, R.Y, R.Xhi, R.Xlo));
+}
+
+// Every warp (all lanes, identical result): plan round st.round + 1 from the
+// state and the segment minima -- thresholds, minimum live weight, minimum rule.
+__device__ __forceinline__ TailRound tail_plan(const PeelArgs &A, RoundState &st, const long long *segmin,
+                                               int nseg) {
+    const int lane = threadIdx.x & 31;
+    long long m = kMaxLL;
+    for (int q = lane; q < nseg; q += 32) m = segmin[q] < m ? segmin[q] : m;
+    m = warp_min64(m);
+    m = __shfl_sync(0xffffffffu, m, 0);
+    const u128 X = (u128)(unsigned long long)A.kD * st.f;
+    TailRound R;
+    R.i = st.round + 1;
+    R.Xhi = (unsigned long long)(X >> 64);
+    R.Xlo = (unsigned long long)X;
+    R.Y = (unsigned long long)A.D * (unsigned long long)st.size;
+    R.gle = -1;
+    if (A.gpo && st.size > 0) {
+        long long le = floor_ratio((unsigned long long)A.D, st.f, (unsigned long long)A.kD, st.size);
+        st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
+        R.gle = st.gpo_le;
+    }
+    R.minw = m;
+    R.minrule = (A.use_min && st.size > 0 && !mul_le(m, R.Y, R.Xhi, R.Xlo) && m > R.gle) ? 1 : 0;
+    R.done = st.size == 0 ? 1 : 0;
+    return R;
+}
+
+// One CTA finishes the peel on the live sub-graph held in shared memory.
+// tw[p] is the peeling weight of local vertex p while it is live (>= 0) and
+// -i once it left in round i.  The live vertices are grouped in segments of
+// 64 with an exact minimum per segment, kept in two buffers by round parity:
+// round i reads its thresholds from one buffer and writes the new minima to
+// the other (recomputed for segments that lose vertices, lowered by
+// atomicMin on every decrement).  A round scans only segments that can hold
+// selected vertices, expands the frontier's arcs (from L2) with shared-memory
+// atomics, and then every warp closes the round and plans the next one
+// itself from the same shared data: two block barriers per round.
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_v[TAIL_WARPS][2];
-    __shared__ unsigned long long s_lo[TAIL_WARPS], s_hi[TAIL_WARPS];
-    __shared__ long long s_mn[TAIL_WARPS];
+    __shared__ TailAcc s_acc[2];
     __shared__ long long s_w[TAIL_WARPS];
     __shared__ long long s_pref[TAIL_THREADS + 1];
-    __shared__ int s_F;
-    __shared__ unsigned long long s_lo2[TAIL_WARPS], s_hi2[TAIL_WARPS];
-    __shared__ long long s_mn2[TAIL_WARPS];
 
     PeelCtl *ctl = A.ctl;
     if (ctl->status != ST_TAIL || ctl->error) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long L = ctl->live_len;
-    long long *tw = (long long *)smem;
-    unsigned char *ts = smem + 8 * L;
-    unsigned short *tf = (unsigned short *)(smem + ((9 * L + 15) & ~15LL));
+    const int nseg = (int)((L + TAIL_SEG - 1) / TAIL_SEG);
+    const long long LP = (long long)nseg * TAIL_SEG;
+    long long *tw = (long long *)smem;                                  // [LP]
+    long long *segbuf = (long long *)(smem + 8 * LP);                   // [2 nseg]
+    int *toff = (int *)(smem + 8 * LP + 16 * nseg);                     // [L+1]
+    unsigned short *tf = (unsigned short *)(smem + 8 * LP + 16 * nseg + 4 * (L + 1));  // [L]
     const int *live = ctl->live_sel ? A.live1 : A.live0;
     const bool dg = A.tcw == nullptr;
+    const int *tcol = A.tcol;
+    const long long *tcw = A.tcw;
 
-    RoundState st;
+    RoundState st;  // identical in every thread
     st.round = ctl->round;
     st.size = ctl->size;
     st.f = mk128(ctl->f_lo, ctl->f_hi);
-    st.minw = ctl->minw;
     st.best_round = ctl->best_round;
     st.best_size = ctl->best_size;
     st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
     st.gpo_le = ctl->gpo_le;
     st.n_min_rule = ctl->n_min_rule;
     st.scan = ctl->scan_volume;
-    for (long long p = tid; p < L; p += TAIL_THREADS) {
-        tw[p] = A.w[live[p]];
-        ts[p] = TS_LIVE;
+    for (long long p = tid; p <= L; p += TAIL_THREADS) toff[p] = (int)A.tlrp[p];
+    for (long long p = tid; p < LP; p += TAIL_THREADS) tw[p] = p < L ? A.w[live[p]] : -1;  // pads: gone
+    if (tid < 2) {
+        TailAcc z = {0, 0, 0, 0, 0, 0};
+        s_acc[tid] = z;
     }
-    if (tid == 0) s_F = 0;
     __syncthreads();
+    // round i reads the minima in buffer (i & 1): fill the first round's buffer
+    long long *first = segbuf + ((st.round + 1) & 1) * nseg;
+    for (int q = wid; q < nseg; q += TAIL_WARPS) {
+        const longlong2 v = *(const longlong2 *)&tw[(long long)q * TAIL_SEG + 2 * lane];
+        long long m = kMaxLL;
+        if (v.x >= 0) m = v.x;
+        if (v.y >= 0 && v.y < m) m = v.y;
+        m = warp_min64(m);
+        if (lane == 0) first[q] = m;
+    }
+    __syncthreads();
+    TailRound R = tail_plan(A, st, first, nseg);
     int err = 0;
-    while (st.size > 0) {
-        if (st.round >= A.max_rounds) {
+    while (!R.done) {
+        if (R.i > A.max_rounds) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        const long long i = st.round + 1;
-        long long T = floor_ratio((unsigned long long)A.kD, st.f, (unsigned long long)A.D, st.size);
-        if (A.gpo) {
-            long long le = floor_ratio((unsigned long long)A.D, st.f, (unsigned long long)A.kD, st.size);
-            st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
-            T = st.gpo_le > T ? st.gpo_le : T;
-        }
-        const bool minrule = A.use_min && st.minw > T;
-        const long long thr = minrule ? st.minw : T;
-        // select
+        const long long i = R.i;
+        const long long *cur = segbuf + (i & 1) * nseg;  // minima at the start of round i
+        long long *nxt = segbuf + ((i + 1) & 1) * nseg;  // minima after round i
+        TailAcc &acc = s_acc[i & 1];
+        // ---- select: lanes test segments in parallel; a candidate segment
+        // is then scanned by its warp (two vertices per lane)
         unsigned long long wlo = 0, whi = 0;
-        long long minsurv = kMaxLL;
-        for (long long p0 = wid * 32; p0 < L; p0 += TAIL_THREADS) {
-            const long long p = p0 + lane;
-            bool sel = false;
-            if (p < L && ts[p] == TS_LIVE) {
-                const long long wv = tw[p];
-                if (wv <= thr) {
-                    sel = true;
-                    ts[p] = TS_INU;
-                    add128(wlo, whi, (unsigned long long)wv, 0);
+        for (int q0 = wid * 32; q0 < nseg; q0 += TAIL_THREADS) {
+            const int q = q0 + lane;
+            const long long sm = q < nseg ? cur[q] : kMaxLL;
+            if (q < nseg) nxt[q] = sm;
+            unsigned cm = __ballot_sync(0xffffffffu, seg_candidate(sm, R));
+            __syncwarp();
+            while (cm) {
+                const int qq = q0 + __ffs(cm) - 1;
+                cm &= cm - 1;
+                const long long p = (long long)qq * TAIL_SEG + 2 * lane;
+                const longlong2 v = *(const longlong2 *)&tw[p];
+                bool s0, s1;
+                if (R.minrule) {
+                    s0 = v.x >= 0 && v.x <= R.minw;
+                    s1 = v.y >= 0 && v.y <= R.minw;
                 } else {
-                    minsurv = wv < minsurv ? wv : minsurv;
+                    s0 = v.x >= 0 && (v.x <= R.gle || mul_le(v.x, R.Y, R.Xhi, R.Xlo));
+                    s1 = v.y >= 0 && (v.y <= R.gle || mul_le(v.y, R.Y, R.Xhi, R.Xlo));
+                }
+                long long m = kMaxLL;  // the segment's minimum over its survivors
+                if (v.x >= 0 && !s0) m = v.x;
+                if (v.y >= 0 && !s1 && v.y < m) m = v.y;
+                m = warp_min64(m);
+                if (lane == 0) nxt[qq] = m;
+                const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
+                if (b0 | b1) {
+                    unsigned base = 0;
+                    if (lane == 0) base = atomicAdd(&acc.F, (unsigned)(__popc(b0) + __popc(b1)));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const unsigned lt = (1u << lane) - 1u;
+                    unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
+                    if (s0) {
+                        tw[p] = -i;
+                        add128(wlo, whi, (unsigned long long)v.x, 0);
+                        tf[slot++] = (unsigned short)p;
+                    }
+                    if (s1) {
+                        tw[p + 1] = -i;
+                        add128(wlo, whi, (unsigned long long)v.y, 0);
+                        tf[slot] = (unsigned short)(p + 1);
+                    }
                 }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, sel);
-            if (bal) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&s_F, __popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (sel) tf[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)p;
-            }
         }
-        __syncthreads();
-        const int F = s_F;
-        // expand the frontier in chunks of TAIL_THREADS entries
-        long long mindec = kMaxLL;
-        unsigned long long ilo = 0, ihi = 0;
-        for (int c0 = 0; c0 < F; c0 += TAIL_THREADS) {
-            const int q = c0 + tid;
-            long long deg = 0;
-            if (q < F) {
-                const int p = tf[q];
-                deg = A.tlrp[p + 1] - A.tlrp[p];
-            }
-            long long tot;
-            long long ex = block_excl_scan<TAIL_WARPS>(deg, s_w, tot);
-            s_pref[tid] = ex;
-            const int nq = (F - c0) < TAIL_THREADS ? (F - c0) : TAIL_THREADS;
-            if (tid == 0) s_pref[nq] = tot;
-            __syncthreads();
-            for (long long x = tid; x < tot; x += TAIL_THREADS) {
-                int e = smem_last_le(s_pref, nq, x);
-                // zero-degree entries share a base with the next one: take the last
-                const int p = tf[c0 + e];
-                const long long pos = A.tlrp[p] + (x - s_pref[e]);
-                const int v = A.tcol[pos];
-                const long long c = dg ? DUPIN_Q_ONE : A.tcw[pos];
-                const unsigned char s = ts[v];
-                if (s == TS_LIVE) {
-                    long long old = (long long)atomicAdd((unsigned long long *)&tw[v], (unsigned long long)(-c));
-                    long long nw = old - c;
-                    mindec = nw < mindec ? nw : mindec;
-                } else if (s == TS_INU) {
-                    add128(ilo, ihi, (unsigned long long)c, 0);
-                }
-            }
-            __syncthreads();
-        }
-        for (int q = tid; q < F; q += TAIL_THREADS) {
-            const int p = tf[q];
-            ts[p] = TS_DEAD;
-            A.pr[live[p]] = (int)i;
-        }
-        // reduce: weights of U, internal arcs, minima
         warp_sum128(wlo, whi);
+        if (lane == 0) acc_add128(&acc.wlo, &acc.whi, wlo, whi);
+        __syncthreads();
+        // round i+1's accumulator was last read in round i-1: reset it now
+        if (tid == 0) {
+            TailAcc z = {0, 0, 0, 0, 0, 0};
+            s_acc[(i + 1) & 1] = z;
+        }
+        const int F = (int)acc.F;
+        // ---- expand
+        unsigned long long ilo = 0, ihi = 0;
+        auto arc = [&](long long pos) {
+            const int v = tcol[pos];
+            const long long c = dg ? DUPIN_Q_ONE : tcw[pos];
+            const long long wv = tw[v];
+            if (wv >= 0) {
+                const long long old = (long long)atomicAdd((unsigned long long *)&tw[v], (unsigned long long)(-c));
+                atomicMin(&nxt[v / TAIL_SEG], old - c);
+            } else if (wv == -i) {
+                add128(ilo, ihi, (unsigned long long)c, 0);
+            }
+        };
+        if (F <= TAIL_FAST) {
+            // every thread walks the concatenation of the F arc ranges
+            // (offsets in shared memory), advancing a running offset
+            int q = 0, qp = F > 0 ? tf[0] : 0;
+            long long qs = 0, ql = F > 0 ? toff[qp + 1] - toff[qp] : 0;
+            for (long long x = tid;; x += TAIL_THREADS) {
+                while (q < F && x >= qs + ql) {
+                    qs += ql;
+                    q++;
+                    if (q < F) {
+                        qp = tf[q];
+                        ql = toff[qp + 1] - toff[qp];
+                    }
+                }
+                if (q >= F) break;
+                arc(toff[qp] + (x - qs));
+            }
+        } else {
+            for (int c0 = 0; c0 < F; c0 += TAIL_THREADS) {
+                const int qq = c0 + tid;
+                long long deg = 0;
+                if (qq < F) {
+                    const int p = tf[qq];
+                    deg = toff[p + 1] - toff[p];
+                }
+                long long tot;
+                long long ex = block_excl_scan<TAIL_WARPS>(deg, s_w, tot);
+                s_pref[tid] = ex;
+                const int nq = (F - c0) < TAIL_THREADS ? (F - c0) : TAIL_THREADS;
+                if (tid == 0) s_pref[nq] = tot;
+                __syncthreads();
+                for (long long x = tid; x < tot; x += TAIL_THREADS) {
+                    const int e = smem_last_le(s_pref, nq, x);
+                    const int p = tf[c0 + e];
+                    arc(toff[p] + (x - s_pref[e]));
+                }
+                __syncthreads();
+            }
+        }
         warp_sum128(ilo, ihi);
-        minsurv = warp_min64(minsurv);
-        mindec = warp_min64(mindec);
-        if (lane == 0) {
-            s_lo[wid] = wlo; s_hi[wid] = whi;
-            s_lo2[wid] = ilo; s_hi2[wid] = ihi;
-            s_mn[wid] = minsurv; s_mn2[wid] = mindec;
-        }
+        if (lane == 0) acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
         __syncthreads();
-        unsigned long long Wl = 0, Wh = 0, Il = 0, Ih = 0;
-        long long ms = kMaxLL, md = kMaxLL;
-        for (int t = 0; t < TAIL_WARPS; t++) {
-            add128(Wl, Wh, s_lo[t], s_hi[t]);
-            add128(Il, Ih, s_lo2[t], s_hi2[t]);
-            ms = s_mn[t] < ms ? s_mn[t] : ms;
-            md = s_mn2[t] < md ? s_mn2[t] : md;
-        }
-        // every thread read F right after the select; reset it before the
-        // barrier that precedes the next round's select
-        if (tid == 0) s_F = 0;
-        __syncthreads();
-        const u128 wsel = mk128(Wl, Wh), internal = mk128(Il, Ih);
+        // ---- every warp: close round i and plan round i + 1 (same values everywhere)
+        const u128 wsel = mk128(acc.wlo, acc.whi), internal = mk128(acc.ilo, acc.ihi);
         st.f = st.f - (wsel - (internal >> 1));
         st.scan += L;
         st.size -= F;
         st.round = i;
-        st.n_min_rule += minrule ? 1 : 0;
-        if (A.use_min) st.minw = ms < md ? ms : md;
+        st.n_min_rule += R.minrule ? 1 : 0;
         if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
             st.bf = st.f;
             st.best_size = st.size;
@@ -923,8 +1091,16 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             A.tr_size[i] = st.size;
             A.tr_peeled[i] = F;
         }
-        (void)s_v;
-        (void)s_mn;
+        if (F == 0) {  // cannot happen (Lemma 4.2 / minimum rule); stop instead of spinning
+            err = DUPIN_ERR_NO_PROGRESS;
+            break;
+        }
+        R = tail_plan(A, st, nxt, nseg);
+    }
+    __syncthreads();
+    for (long long p = tid; p < L; p += TAIL_THREADS) {
+        const long long wv = tw[p];
+        if (wv < 0) A.pr[live[p]] = (int)(-wv);
     }
     if (tid == 0) {
         if (err) set_error(ctl, err);
@@ -932,7 +1108,6 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         ctl->size = st.size;
         ctl->f_lo = (unsigned long long)st.f;
         ctl->f_hi = (unsigned long long)(st.f >> 64);
-        ctl->minw = st.minw;
         ctl->best_round = st.best_round;
         ctl->best_size = st.best_size;
         ctl->bf_lo = (unsigned long long)st.bf;
@@ -957,9 +1132,10 @@ long long tail_cap_limit() {
     int dev = 0, smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // static shared memory of k_peel_tail is about 22 KB; 11 bytes per vertex
-    long long avail = (long long)smem - 24 * 1024;
-    long long cap = avail / 11;
+    // static shared memory of k_peel_tail is about 5 KB; 14 bytes per vertex
+    // plus padding to whole 64-vertex segments and 16 bytes per segment
+    long long avail = (long long)smem - 8 * 1024 - 8 * TAIL_SEG - 32;
+    long long cap = avail / (14 + 1);
     if (cap > 65535) cap = 65535;
     return cap < 0 ? 0 : cap;
 }
@@ -995,7 +1171,10 @@ static int set_tail_smem() {
     return DUPIN_OK;
 }
 
-static long long tail_smem_bytes(long long cap) { return ((9 * cap + 15) & ~15LL) + 2 * cap + 16; }
+static long long tail_smem_bytes(long long cap) {
+    const long long nseg = (cap + TAIL_SEG - 1) / TAIL_SEG;
+    return 8 * nseg * TAIL_SEG + 16 * nseg + 4 * (cap + 1) + 2 * cap + 16;
+}
 
 static int check_params(const dupin_graph *g, const dupin_params *p) {
     if (!p) return dupin_fail(DUPIN_ERR_INVALID_ARG, "params is NULL");
@@ -1018,6 +1197,8 @@ DevGraph dev_graph(const dupin_graph *g, int metric) {
     d.col = g->col;
     d.cw = metric == DUPIN_DG ? nullptr : g->cw;
     d.a = metric == DUPIN_DG ? nullptr : g->a;
+    d.hubs = g->hubs;
+    d.n_hubs = g->n_hubs;
     return d;
 }
 

@@ -221,6 +221,8 @@ class PeelOutput:
     trace_f: Optional[list] = None
     trace_size: Optional[object] = None
     trace_peeled: Optional[object] = None
+    n_bulk_rounds: int = 0
+    phase_ms: Optional[list] = None
 
 
 def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> Result:
@@ -235,7 +237,8 @@ def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> 
 
 def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
     out = PeelOutput(r.n_rounds, r.best_round, r.best_size, (int(r.best_f_hi) << 64) + int(r.best_f_lo),
-                     r.best_density, r.n_min_rule, peel_round, best_mask)
+                     r.best_density, r.n_min_rule, peel_round, best_mask, n_bulk_rounds=int(r.n_bulk_rounds),
+                     phase_ms=[float(x) for x in r.phase_ms])
     if trace is not None:
         R = r.n_rounds + 1
         fh, fl, sz, pe = trace
