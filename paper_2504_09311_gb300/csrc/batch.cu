@@ -1,21 +1,541 @@
-// batch.cu -- dupin_peel_batch: many independent graphs.
+// batch.cu -- dupin_peel_batch: many independent graphs, one CTA per graph.
+//
+// A persistent grid pulls graphs from an atomic queue; each CTA runs a whole
+// peel (Algorithm 2, Sec. 4.1) of its graph: initial weights (a warp per row,
+// the whole CTA for rows longer than CTA_BIGROW), then the rounds.  The
+// graph's weights stay in global memory (L2-resident for window-sized
+// graphs) with the vertex state in the sign (w >= 0 live, w = -i removed in
+// round i); 64-vertex segment minima, double-buffered by round parity, sit in
+// shared memory, so a round scans only segments that can hold selected
+// vertices and every warp closes the round itself (two barriers per round),
+// exactly as the single-graph tail does.  Graphs with more than CTA_MAX_N
+// vertices take the single-graph path.  Results are identical to dupin_peel:
+// the arithmetic is the same exact integer peel.
 #include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
 
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "dupin_internal.h"
+#include "peel_device.cuh"
+
+#define CTA_THREADS 256
+#define CTA_WARPS (CTA_THREADS / 32)
+#define CTA_MAX_SEG 4096
+#define CTA_MAX_N ((long long)CTA_MAX_SEG * TAIL_SEG)
+#define CTA_BIGROW 2048
+#define CTA_BIGLIST 64
+
+struct CtaJob {
+    long long n, arcs;
+    const long long *rp;
+    const int *col;
+    const long long *cw;  // nullptr: DG
+    const long long *a;   // nullptr: 0
+    const int *hubs;      // heads of hub-coded arcs
+    long long kD, D, max_rounds;
+    int use_min, gpo;
+    long long *w;      // [n] workspace
+    int *front;        // [n] workspace
+    int *pr;           // [n] output
+    long long *tr_f_hi;
+    unsigned long long *tr_f_lo;
+    long long *tr_size, *tr_peeled;
+    long long tr_cap;
+    long long *out;    // [8]: R, best round, best size, best f hi, best f lo, minimum-rule rounds, error, 0
+};
+
+__device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf, TailAcc *s_acc, long long *s_w,
+                                             long long *s_pref, long long *s_fs, long long *s_fl, int *s_big,
+                                             int *s_nbig, unsigned long long *s_lo, unsigned long long *s_hi) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long long n = J.n;
+    const bool dg = J.cw == nullptr;
+    long long *w = J.w;
+    const long long *rp = J.rp;
+    const int *col = J.col;
+    const long long *cw = J.cw;
+    const int *hubs = J.hubs;
+    const int nseg = (int)((n + TAIL_SEG - 1) / TAIL_SEG);
+
+    // ---- initial peeling weights w_u = a_u + sum_v c_uv (Sec. 2.2)
+    if (tid == 0) *s_nbig = 0;
+    for (long long u = tid; u < n; u += CTA_THREADS) {
+        const long long d = rp[u + 1] - rp[u];
+        w[u] = dg ? (d << 32) : (J.a ? J.a[u] : 0);
+    }
+    __syncthreads();
+    if (!dg) {
+        for (long long u = wid; u < n; u += CTA_WARPS) {
+            const long long b = rp[u], e = rp[u + 1];
+            if (e - b > CTA_BIGROW) {
+                int k = 0;
+                if (lane == 0) {
+                    k = atomicAdd(s_nbig, 1);
+                    if (k < CTA_BIGLIST) s_big[k] = (int)u;
+                }
+                k = __shfl_sync(0xffffffffu, k, 0);
+                if (k < CTA_BIGLIST) continue;  // the whole CTA sums it below
+                // list full: this warp sums the row itself
+            }
+            long long sum = 0;
+            for (long long p = b + lane; p < e; p += 32) sum += cw[p];
+            sum = warp_sum64(sum);
+            if (lane == 0) w[u] += sum;
+        }
+        __syncthreads();
+        const int nb = *s_nbig < CTA_BIGLIST ? *s_nbig : CTA_BIGLIST;
+        for (int k = 0; k < nb; k++) {
+            const long long u = s_big[k];
+            long long sum = 0;
+            for (long long p = rp[u] + tid; p < rp[u + 1]; p += CTA_THREADS) sum += cw[p];
+            sum = warp_sum64(sum);
+            if (lane == 0) s_w[wid] = sum;
+            __syncthreads();
+            if (tid == 0) {
+                long long t = 0;
+                for (int q = 0; q < CTA_WARPS; q++) t += s_w[q];
+                w[u] += t;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // f(V) = sum_u (w_u + a_u) / 2; segment minima of round 1
+    {
+        unsigned long long lo = 0, hi = 0;
+        for (long long u = tid; u < n; u += CTA_THREADS) {
+            add128(lo, hi, (unsigned long long)w[u], 0);
+            if (!dg && J.a) add128(lo, hi, (unsigned long long)J.a[u], 0);
+        }
+        warp_sum128(lo, hi);
+        if (lane == 0) {
+            s_lo[wid] = lo;
+            s_hi[wid] = hi;
+        }
+    }
+    long long *first = segbuf + (1 & 1) * nseg;
+    for (int q = wid; q < nseg; q += CTA_WARPS) {
+        const long long p = (long long)q * TAIL_SEG + 2 * lane;
+        const long long w0 = p < n ? w[p] : -1, w1 = p + 1 < n ? w[p + 1] : -1;
+        long long m = kMaxLL;
+        if (w0 >= 0) m = w0;
+        if (w1 >= 0 && w1 < m) m = w1;
+        m = warp_min64(m);
+        if (lane == 0) first[q] = m;
+    }
+    if (tid < 2) {
+        TailAcc z = {0, 0, 0, 0, 0, 0};
+        s_acc[tid] = z;
+    }
+    __syncthreads();
+    RoundState st;
+    {
+        unsigned long long lo = 0, hi = 0;
+        for (int q = 0; q < CTA_WARPS; q++) add128(lo, hi, s_lo[q], s_hi[q]);
+        st.f = mk128(lo, hi) >> 1;
+    }
+    st.round = 0;
+    st.size = n;
+    st.best_round = 0;
+    st.best_size = n;
+    st.bf = st.f;
+    st.gpo_le = 0;
+    st.n_min_rule = 0;
+    st.scan = 0;
+    if (tid == 0 && J.tr_cap > 0) {
+        J.tr_f_hi[0] = (long long)(unsigned long long)(st.f >> 64);
+        J.tr_f_lo[0] = (unsigned long long)st.f;
+        J.tr_size[0] = n;
+        J.tr_peeled[0] = 0;
+    }
+    TailRound R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, first, nseg);
+    int err = 0;
+    while (!R.done) {
+        if (R.i > J.max_rounds) {
+            err = DUPIN_ERR_NO_PROGRESS;
+            break;
+        }
+        const long long i = R.i;
+        const long long *cur = segbuf + (i & 1) * nseg;
+        long long *nxt = segbuf + ((i + 1) & 1) * nseg;
+        TailAcc &acc = s_acc[i & 1];
+        // ---- select
+        unsigned long long wlo = 0, whi = 0;
+        for (int q0 = wid * 32; q0 < nseg; q0 += CTA_THREADS) {
+            const int q = q0 + lane;
+            const long long sm = q < nseg ? cur[q] : kMaxLL;
+            if (q < nseg) nxt[q] = sm;
+            unsigned cm = __ballot_sync(0xffffffffu, seg_candidate(sm, R));
+            __syncwarp();
+            while (cm) {
+                const int qq = q0 + __ffs(cm) - 1;
+                cm &= cm - 1;
+                const long long p = (long long)qq * TAIL_SEG + 2 * lane;
+                const long long w0 = p < n ? w[p] : -1, w1 = p + 1 < n ? w[p + 1] : -1;
+                bool s0, s1;
+                if (R.minrule) {
+                    s0 = w0 >= 0 && w0 <= R.minw;
+                    s1 = w1 >= 0 && w1 <= R.minw;
+                } else {
+                    s0 = w0 >= 0 && (w0 <= R.gle || mul_le(w0, R.Y, R.Xhi, R.Xlo));
+                    s1 = w1 >= 0 && (w1 <= R.gle || mul_le(w1, R.Y, R.Xhi, R.Xlo));
+                }
+                long long m = kMaxLL;
+                if (w0 >= 0 && !s0) m = w0;
+                if (w1 >= 0 && !s1 && w1 < m) m = w1;
+                m = warp_min64(m);
+                if (lane == 0) nxt[qq] = m;
+                const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
+                if (b0 | b1) {
+                    unsigned base = 0;
+                    if (lane == 0) base = atomicAdd(&acc.F, (unsigned)(__popc(b0) + __popc(b1)));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const unsigned lt = (1u << lane) - 1u;
+                    unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
+                    if (s0) {
+                        w[p] = -i;
+                        add128(wlo, whi, (unsigned long long)w0, 0);
+                        J.front[slot] = (int)p;
+                        if (slot < TAIL_FAST) {
+                            s_fs[slot] = rp[p];
+                            s_fl[slot] = rp[p + 1] - rp[p];
+                        }
+                        slot++;
+                    }
+                    if (s1) {
+                        w[p + 1] = -i;
+                        add128(wlo, whi, (unsigned long long)w1, 0);
+                        J.front[slot] = (int)(p + 1);
+                        if (slot < TAIL_FAST) {
+                            s_fs[slot] = rp[p + 1];
+                            s_fl[slot] = rp[p + 2] - rp[p + 1];
+                        }
+                    }
+                }
+            }
+        }
+        warp_sum128(wlo, whi);
+        if (lane == 0) acc_add128(&acc.wlo, &acc.whi, wlo, whi);
+        __syncthreads();
+        if (tid == 0) {
+            TailAcc z = {0, 0, 0, 0, 0, 0};
+            s_acc[(i + 1) & 1] = z;
+        }
+        const int F = (int)acc.F;
+        // ---- expand: every arc of the frontier (heads read from global memory)
+        unsigned long long ilo = 0, ihi = 0;
+        auto arc = [&](long long pos) {
+            const int v = arc_head(col[pos], hubs);
+            const long long c = dg ? DUPIN_Q_ONE : cw[pos];
+            const long long wv = w[v];
+            if (wv >= 0) {
+                const long long old = (long long)atomicAdd((unsigned long long *)&w[v], (unsigned long long)(-c));
+                atomicMin(&nxt[v / TAIL_SEG], old - c);
+            } else if (wv == -i) {
+                add128(ilo, ihi, (unsigned long long)c, 0);
+            }
+        };
+        if (F <= TAIL_FAST) {
+            int q = 0;
+            long long qs = 0, ql = F > 0 ? s_fl[0] : 0;
+            for (long long x = tid;; x += CTA_THREADS) {
+                while (q < F && x >= qs + ql) {
+                    qs += ql;
+                    q++;
+                    if (q < F) ql = s_fl[q];
+                }
+                if (q >= F) break;
+                arc(s_fs[q] + (x - qs));
+            }
+        } else {
+            for (int c0 = 0; c0 < F; c0 += CTA_THREADS) {
+                const int qq = c0 + tid;
+                long long deg = 0;
+                if (qq < F) {
+                    const int p = J.front[qq];
+                    deg = rp[p + 1] - rp[p];
+                }
+                long long tot;
+                long long ex = block_excl_scan<CTA_WARPS>(deg, s_w, tot);
+                s_pref[tid] = ex;
+                const int nq = (F - c0) < CTA_THREADS ? (F - c0) : CTA_THREADS;
+                if (tid == 0) s_pref[nq] = tot;
+                __syncthreads();
+                for (long long x = tid; x < tot; x += CTA_THREADS) {
+                    const int e = smem_last_le(s_pref, nq, x);
+                    const int p = J.front[c0 + e];
+                    arc(rp[p] + (x - s_pref[e]));
+                }
+                __syncthreads();
+            }
+        }
+        warp_sum128(ilo, ihi);
+        if (lane == 0) acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
+        __syncthreads();
+        // ---- every warp: close round i, plan round i + 1
+        const u128 wsel = mk128(acc.wlo, acc.whi), internal = mk128(acc.ilo, acc.ihi);
+        st.f = st.f - (wsel - (internal >> 1));
+        st.size -= F;
+        st.round = i;
+        st.n_min_rule += R.minrule ? 1 : 0;
+        if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
+            st.bf = st.f;
+            st.best_size = st.size;
+            st.best_round = i;
+        }
+        if (tid == 0 && i < J.tr_cap) {
+            J.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
+            J.tr_f_lo[i] = (unsigned long long)st.f;
+            J.tr_size[i] = st.size;
+            J.tr_peeled[i] = F;
+        }
+        if (F == 0) {
+            err = DUPIN_ERR_NO_PROGRESS;
+            break;
+        }
+        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, nxt, nseg);
+    }
+    __syncthreads();
+    for (long long u = tid; u < n; u += CTA_THREADS) {
+        const long long wv = w[u];
+        J.pr[u] = wv < 0 ? (int)(-wv) : 0x7fffffff;
+    }
+    if (tid == 0) {
+        J.out[0] = st.round;
+        J.out[1] = st.best_round;
+        J.out[2] = st.best_size;
+        J.out[3] = (long long)(unsigned long long)(st.bf >> 64);
+        J.out[4] = (long long)(unsigned long long)st.bf;
+        J.out[5] = st.n_min_rule;
+        J.out[6] = err;
+        J.out[7] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(CTA_THREADS, 2) k_peel_cta(const CtaJob *jobs, int njobs, int *next) {
+    extern __shared__ __align__(16) long long s_seg[];  // 2 * CTA_MAX_SEG
+    __shared__ TailAcc s_acc[2];
+    __shared__ long long s_w[CTA_WARPS];
+    __shared__ long long s_pref[CTA_THREADS + 1];
+    __shared__ long long s_fs[TAIL_FAST], s_fl[TAIL_FAST];
+    __shared__ int s_big[CTA_BIGLIST];
+    __shared__ int s_nbig;
+    __shared__ unsigned long long s_lo[CTA_WARPS], s_hi[CTA_WARPS];
+    __shared__ int s_job;
+    for (;;) {
+        if (threadIdx.x == 0) s_job = atomicAdd(next, 1);
+        __syncthreads();
+        const int j = s_job;
+        __syncthreads();
+        if (j >= njobs) break;
+        const CtaJob J = jobs[j];
+        const int nseg = (int)((J.n + TAIL_SEG - 1) / TAIL_SEG);
+        (void)nseg;
+        cta_peel_one(J, s_seg, s_acc, s_w, s_pref, s_fs, s_fl, s_big, &s_nbig, s_lo, s_hi);
+        __syncthreads();
+    }
+}
+
+static int set_cta_smem() {
+    static bool done = false;
+    if (done) return DUPIN_OK;
+    cudaError_t e = cudaFuncSetAttribute(k_peel_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * CTA_MAX_SEG * sizeof(long long)));
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaFuncSetAttribute(k_peel_cta)");
+    done = true;
+    return DUPIN_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Run a set of graphs through k_peel_cta.  idx lists the batch positions;
+// results go to results[idx[k]] (host arrays, or device arrays with
+// DUPIN_RESULT_DEVICE).  Synchronises the stream.
+int run_cta_jobs(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
+                 const std::vector<int64_t> &idx, cudaStream_t s) {
+    if (idx.empty()) return DUPIN_OK;
+    int rc = set_cta_smem();
+    if (rc) return rc;
+    const size_t nj = idx.size();
+    // arena: jobs | next | per job: w, front, pr, trace x4, out
+    std::vector<size_t> off_w(nj), off_f(nj), off_pr(nj), off_tr(nj), off_out(nj);
+    std::vector<long long> trcap(nj);
+    size_t at = align256(sizeof(CtaJob) * nj) + 256;
+    const size_t outs_base = at;
+    at = align256(at + 64 * nj);
+    for (size_t k = 0; k < nj; k++) {
+        const dupin_graph *g = graphs[idx[k]];
+        const dupin_params &p = params[idx[k]];
+        const long long n = g->n;
+        long long mr = p.max_rounds > 0 ? p.max_rounds : n + 1;
+        trcap[k] = std::min<long long>(mr, n) + 1;
+        off_w[k] = at;
+        at = align256(at + 8 * (size_t)n);
+        off_f[k] = at;
+        at = align256(at + 4 * (size_t)n);
+        off_pr[k] = at;
+        at = align256(at + 4 * (size_t)n);
+        off_tr[k] = at;
+        at = align256(at + 32 * (size_t)trcap[k]);
+        off_out[k] = outs_base + 64 * k;
+    }
+    unsigned char *arena = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&arena, at, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return dupin_fail(e == cudaErrorMemoryAllocation ? DUPIN_ERR_OOM : DUPIN_ERR_CUDA,
+                          std::string("batch arena: ") + cudaGetErrorString(e));
+    }
+    std::vector<CtaJob> jobs(nj);
+    for (size_t k = 0; k < nj; k++) {
+        const dupin_graph *g = graphs[idx[k]];
+        const dupin_params &p = params[idx[k]];
+        const DevGraph dgr = dev_graph(g, p.metric);
+        CtaJob &J = jobs[k];
+        J.n = g->n;
+        J.arcs = g->arcs;
+        J.rp = dgr.rp;
+        J.col = dgr.col;
+        J.cw = dgr.cw;
+        J.a = dgr.a;
+        J.hubs = dgr.hubs;
+        J.kD = (long long)p.k_mult * (p.eps_den + p.eps_num);
+        J.D = p.eps_den;
+        J.max_rounds = p.max_rounds > 0 ? p.max_rounds : g->n + 1;
+        J.use_min = J.kD < 2 * J.D ? 1 : 0;
+        J.gpo = (p.flags & DUPIN_GPO) ? 1 : 0;
+        J.w = (long long *)(arena + off_w[k]);
+        J.front = (int *)(arena + off_f[k]);
+        const bool dev = (p.flags & DUPIN_RESULT_DEVICE) != 0;
+        dupin_result &r = results[idx[k]];
+        J.pr = (dev && r.peel_round) ? r.peel_round : (int *)(arena + off_pr[k]);
+        long long *tr = (long long *)(arena + off_tr[k]);
+        const bool user_tr = dev && r.trace_f_hi && r.trace_f_lo && r.trace_size && r.trace_peeled;
+        J.tr_f_hi = user_tr ? (long long *)r.trace_f_hi : tr;
+        J.tr_f_lo = user_tr ? (unsigned long long *)r.trace_f_lo : (unsigned long long *)(tr + trcap[k]);
+        J.tr_size = user_tr ? (long long *)r.trace_size : tr + 2 * trcap[k];
+        J.tr_peeled = user_tr ? (long long *)r.trace_peeled : tr + 3 * trcap[k];
+        J.tr_cap = user_tr ? std::min<long long>(trcap[k], r.trace_cap) : trcap[k];
+        J.out = (long long *)(arena + off_out[k]);
+    }
+    int *next = (int *)(arena + align256(sizeof(CtaJob) * nj));
+    int sms = 0, dev = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel_cta, CTA_THREADS, 2 * CTA_MAX_SEG * sizeof(long long));
+    if (occ < 1) occ = 1;
+    const int grid = (int)std::min<long long>((long long)nj, (long long)sms * occ);
+    e = cudaMemcpyAsync(arena, jobs.data(), sizeof(CtaJob) * nj, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_peel_cta<<<grid, CTA_THREADS, 2 * CTA_MAX_SEG * sizeof(long long), s>>>((const CtaJob *)arena, (int)nj, next);
+        e = cudaGetLastError();
+    }
+    // scalars of every job in one copy
+    std::vector<long long> outs(8 * nj);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(outs.data(), arena + outs_base, 64 * nj, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int status = DUPIN_OK;
+    std::string msg;
+    for (size_t k = 0; k < nj && e == cudaSuccess; k++) {
+        const dupin_graph *g = graphs[idx[k]];
+        const dupin_params &p = params[idx[k]];
+        dupin_result &r = results[idx[k]];
+        const long long *o = &outs[8 * k];
+        r.n_rounds = o[0];
+        r.n_min_rule = o[5];
+        r.n_bulk_rounds = 0;
+        for (int q = 0; q < 4; q++) r.phase_ms[q] = 0.f;
+        if (o[6]) {
+            if (!status) {
+                status = (int)o[6];
+                msg = "graph " + std::to_string((long long)idx[k]) + ": max_rounds reached before the set became empty";
+            }
+            continue;
+        }
+        r.best_round = o[1];
+        r.best_size = o[2];
+        r.best_f_hi = o[3];
+        r.best_f_lo = (unsigned long long)o[4];
+        const u128 bf = mk128((unsigned long long)o[4], (unsigned long long)o[3]);
+        r.best_density = o[2] > 0 ? (double)bf / 4294967296.0 / (double)o[2] : 0.0;
+        const bool dev = (p.flags & DUPIN_RESULT_DEVICE) != 0;
+        const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const long long n = g->n;
+        const int *pr_dev = dev && r.peel_round ? r.peel_round : (const int *)(arena + off_pr[k]);
+        if (r.peel_round && !dev && n > 0)
+            e = cudaMemcpyAsync(r.peel_round, pr_dev, 4 * (size_t)n, kind, s);
+        const long long nt = o[0] + 1;
+        const bool want_tr = r.trace_f_hi || r.trace_f_lo || r.trace_size || r.trace_peeled;
+        const bool user_tr = dev && r.trace_f_hi && r.trace_f_lo && r.trace_size && r.trace_peeled;
+        if (want_tr && !user_tr && e == cudaSuccess) {
+            const long long cnt = std::min<long long>(nt, (long long)r.trace_cap);
+            const long long *tr = (const long long *)(arena + off_tr[k]);
+            if (cnt > 0) {
+                if (r.trace_f_hi) e = cudaMemcpyAsync(r.trace_f_hi, tr, 8 * (size_t)cnt, kind, s);
+                if (r.trace_f_lo && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_f_lo, tr + trcap[k], 8 * (size_t)cnt, kind, s);
+                if (r.trace_size && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_size, tr + 2 * trcap[k], 8 * (size_t)cnt, kind, s);
+                if (r.trace_peeled && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_peeled, tr + 3 * trcap[k], 8 * (size_t)cnt, kind, s);
+            }
+        }
+        if (want_tr && r.trace_cap < nt && !status) {
+            status = DUPIN_ERR_BUFFER_TOO_SMALL;
+            msg = "graph " + std::to_string((long long)idx[k]) + ": trace_cap < n_rounds + 1";
+        }
+        if (r.best_mask && n > 0 && e == cudaSuccess) {
+            if (dev) {
+                launch_mask(pr_dev, n, o[1], r.best_mask, s);
+            } else {
+                e = cudaStreamSynchronize(s);
+                std::vector<int> tmp;
+                const int *prh = r.peel_round;
+                if (!prh) {
+                    tmp.resize((size_t)n);
+                    if (e == cudaSuccess) e = cudaMemcpy(tmp.data(), pr_dev, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+                    prh = tmp.data();
+                }
+                for (long long u = 0; u < n && e == cudaSuccess; u++) r.best_mask[u] = prh[u] > o[1] ? 1 : 0;
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(arena, s);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "batched peel");
+    if (status) return dupin_fail(status, msg);
+    return DUPIN_OK;
+}
 
 extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
                                 int64_t count, void *stream) {
     if (count < 0) return dupin_fail(DUPIN_ERR_INVALID_ARG, "count < 0");
     if (count > 0 && (!graphs || !params || !results))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "graphs, params and results must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> cta, big;
     for (int64_t j = 0; j < count; j++) {
-        int rc = dupin_peel(graphs[j], &params[j], &results[j], stream);
+        if (!graphs[j]) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph " + std::to_string((long long)j) + " is NULL");
+        long long a, b, c;
+        int rc = peel_resolve(graphs[j], &params[j], &a, &b, &c);
         if (rc) {
             char buf[512];
             dupin_last_error(buf, sizeof(buf));
-            return dupin_fail(rc, "graph " + std::to_string(j) + ": " + buf);
+            return dupin_fail(rc, "graph " + std::to_string((long long)j) + ": " + buf);
+        }
+        if (graphs[j]->n >= 1 && graphs[j]->n <= CTA_MAX_N) cta.push_back(j);
+        else big.push_back(j);
+    }
+    int rc = run_cta_jobs(graphs, params, results, cta, s);
+    if (rc) return rc;
+    for (int64_t j : big) {
+        rc = dupin_peel(graphs[j], &params[j], &results[j], stream);
+        if (rc) {
+            char buf[512];
+            dupin_last_error(buf, sizeof(buf));
+            return dupin_fail(rc, "graph " + std::to_string((long long)j) + ": " + buf);
         }
     }
     return DUPIN_OK;

@@ -80,6 +80,9 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
 int launch_init_weights(const DevGraph &dg, int metric, long long *w, int *pr, int *live0, PeelCtl *ctl,
                         bool check, cudaStream_t s);
 
+// best_mask[u] = (peel_round[u] > best_round) on the device
+void launch_mask(const int *pr, long long n, long long best_round, uint8_t *mask, cudaStream_t s);
+
 // a whole peel of a small graph with caller-supplied buffers (no allocation)
 int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStream_t s);
 

@@ -35,138 +35,9 @@
 #include <string>
 
 #include "dupin_internal.h"
+#include "peel_device.cuh"
 
-#define BULK_THREADS 512
-#define BULK_WARPS (BULK_THREADS / 32)
-#define WALK_WIN 1024
-#define INIT_THREADS 256
-#define INIT_WARPS (INIT_THREADS / 32)
-#ifndef TAIL_THREADS
-#define TAIL_THREADS 512
-#endif
-#define TAIL_WARPS (TAIL_THREADS / 32)
-#define SCAN_THREADS 1024
 
-// tail vertex states
-#define TS_LIVE 0
-#define TS_INU 1
-#define TS_DEAD 2
-
-static const long long kMaxLL = 0x7fffffffffffffffLL;
-
-// ------------------------------------------------------------ block helpers
-
-// Block-wide reduction of NV 64-bit sums, one u128 sum and one minimum.
-// All threads get the results.  Two __syncthreads.
-template <int NWARPS, int NV>
-struct BlockRed {
-    long long v[NV];
-    unsigned long long lo, hi;
-    long long mn;
-};
-
-template <int NWARPS, int NV>
-__device__ __forceinline__ void block_reduce(BlockRed<NWARPS, NV> &r, long long (*s_v)[NV], unsigned long long *s_lo,
-                                             unsigned long long *s_hi, long long *s_mn) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < NV; j++) r.v[j] = warp_sum64(r.v[j]);
-    warp_sum128(r.lo, r.hi);
-    r.mn = warp_min64(r.mn);
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < NV; j++) s_v[wid][j] = r.v[j];
-        s_lo[wid] = r.lo;
-        s_hi[wid] = r.hi;
-        s_mn[wid] = r.mn;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        bool in = lane < NWARPS;
-#pragma unroll
-        for (int j = 0; j < NV; j++) r.v[j] = in ? s_v[lane][j] : 0;
-        r.lo = in ? s_lo[lane] : 0;
-        r.hi = in ? s_hi[lane] : 0;
-        r.mn = in ? s_mn[lane] : kMaxLL;
-#pragma unroll
-        for (int j = 0; j < NV; j++) r.v[j] = warp_sum64(r.v[j]);
-        warp_sum128(r.lo, r.hi);
-        r.mn = warp_min64(r.mn);
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < NV; j++) s_v[0][j] = r.v[j];
-            s_lo[0] = r.lo;
-            s_hi[0] = r.hi;
-            s_mn[0] = r.mn;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NV; j++) r.v[j] = s_v[0][j];
-    r.lo = s_lo[0];
-    r.hi = s_hi[0];
-    r.mn = s_mn[0];
-    __syncthreads();
-}
-
-// Exclusive block scan of one 64-bit value per thread; 'total' gets the sum.
-template <int NWARPS>
-__device__ __forceinline__ long long block_excl_scan(long long x, long long *s_w, long long &total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    long long incl = warp_incl_scan64(x);
-    if (lane == 31) s_w[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        long long v = lane < NWARPS ? s_w[lane] : 0;
-        v = warp_incl_scan64(v);
-        if (lane < NWARPS) s_w[lane] = v;
-    }
-    __syncthreads();
-    long long before = wid ? s_w[wid - 1] : 0;
-    total = s_w[NWARPS - 1];
-    __syncthreads();
-    return before + incl - x;
-}
-
-// last t in [0, n) with s[t] <= x (s non-decreasing, s[0] <= x)
-__device__ __forceinline__ int smem_last_le(const long long *s, int n, long long x) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (s[mid] <= x) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Walk the arcs [e0, e1) of a segmented arc space.  Entry k (0 <= k < U)
-// covers [base(k), base(k+1)) and its arcs sit at col positions start(k) + (x -
-// base(k)); base(U) is the total.  k0 must satisfy base(k0) <= e0.  The
-// block loads WALK_WIN entries at a time into shared memory and calls
-// fn(k, pos) once per arc, consecutive threads on consecutive arcs.
-template <class BaseF, class StartF, class ArcF>
-__device__ __forceinline__ void walk_arcs(BaseF base, StartF start, long long U, long long e0, long long e1,
-                                          long long k0, long long *s_base, long long *s_start, ArcF fn) {
-    long long e = e0, k = k0;
-    while (e < e1) {
-        __syncthreads();
-        for (int t = threadIdx.x; t <= WALK_WIN; t += blockDim.x) {
-            long long idx = k + t;
-            s_base[t] = idx <= U ? base(idx) : kMaxLL;
-            s_start[t] = idx < U ? start(idx) : 0;
-        }
-        __syncthreads();
-        long long wend = s_base[WALK_WIN];
-        long long hi = e1 < wend ? e1 : wend;
-        for (long long x = e + threadIdx.x; x < hi; x += blockDim.x) {
-            int t = smem_last_le(s_base, WALK_WIN, x);
-            fn(k + t, s_start[t] + (x - s_base[t]));
-        }
-        int t2 = smem_last_le(s_base, WALK_WIN + 1, hi);
-        k += t2;
-        e = hi;
-    }
-}
 
 // ------------------------------------------------------------- (a) init
 
@@ -423,17 +294,6 @@ __global__ void k_init_finish(PeelArgs A, long long n) {
 }
 
 // ------------------------------------------------------ (b)-(c) bulk rounds
-
-struct RoundState {
-    long long round, size;
-    u128 f;
-    long long live_len;
-    int live_sel;
-    long long minw;
-    long long best_round, best_size;
-    u128 bf;
-    long long gpo_le, n_min_rule, scan;
-};
 
 __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
     __shared__ long long s_v[BULK_WARPS][6];
@@ -828,70 +688,6 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
               });
 }
 
-// Shared accumulator of one tail round (double-buffered by round parity).
-struct TailAcc {
-    unsigned long long wlo, whi;  // sum of the removed vertices' weights
-    unsigned long long ilo, ihi;  // sum of c over arcs inside U
-    unsigned int F;               // |U_i|
-    unsigned int pad;
-};
-
-// The parameters of one round, computed identically by every warp.
-struct TailRound {
-    long long i;                  // round number
-    unsigned long long Xhi, Xlo;  // X = k (D+N) f
-    unsigned long long Y;         // Y = D |S|
-    long long gle;                // Algorithm 3's floor(tau_max), -1 without GPO
-    long long minw;               // minimum live weight
-    int minrule;                  // threshold selects nobody: take the minimum
-    int done;                     // S is empty
-};
-
-__device__ __forceinline__ void acc_add128(unsigned long long *lo, unsigned long long *hi, unsigned long long xlo,
-                                           unsigned long long xhi) {
-    if (xlo) {
-        unsigned long long old = atomicAdd(lo, xlo);
-        if (old + xlo < old) xhi += 1;
-    }
-    if (xhi) atomicAdd(hi, xhi);
-}
-
-#define TAIL_FAST 32
-#define TAIL_SEG 64  // vertices per segment (one warp, two per lane)
-
-// can segment minimum sm hold a vertex that round R selects?
-__device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) {
-    if (sm == kMaxLL) return false;
-    return R.minrule ? sm == R.minw : (sm <= R.gle || mul_le(sm, R.Y, R.Xhi, R.Xlo));
-}
-
-// Every warp (all lanes, identical result): plan round st.round + 1 from the
-// state and the segment minima -- thresholds, minimum live weight, minimum rule.
-__device__ __forceinline__ TailRound tail_plan(const PeelArgs &A, RoundState &st, const long long *segmin,
-                                               int nseg) {
-    const int lane = threadIdx.x & 31;
-    long long m = kMaxLL;
-    for (int q = lane; q < nseg; q += 32) m = segmin[q] < m ? segmin[q] : m;
-    m = warp_min64(m);
-    m = __shfl_sync(0xffffffffu, m, 0);
-    const u128 X = (u128)(unsigned long long)A.kD * st.f;
-    TailRound R;
-    R.i = st.round + 1;
-    R.Xhi = (unsigned long long)(X >> 64);
-    R.Xlo = (unsigned long long)X;
-    R.Y = (unsigned long long)A.D * (unsigned long long)st.size;
-    R.gle = -1;
-    if (A.gpo && st.size > 0) {
-        long long le = floor_ratio((unsigned long long)A.D, st.f, (unsigned long long)A.kD, st.size);
-        st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
-        R.gle = st.gpo_le;
-    }
-    R.minw = m;
-    R.minrule = (A.use_min && st.size > 0 && !mul_le(m, R.Y, R.Xhi, R.Xlo) && m > R.gle) ? 1 : 0;
-    R.done = st.size == 0 ? 1 : 0;
-    return R;
-}
-
 // One CTA finishes the peel on the live sub-graph held in shared memory.
 // tw[p] is the peeling weight of local vertex p while it is live (>= 0) and
 // -i once it left in round i.  The live vertices are grouped in segments of
@@ -951,7 +747,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         if (lane == 0) first[q] = m;
     }
     __syncthreads();
-    TailRound R = tail_plan(A, st, first, nseg);
+    TailRound R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, first, nseg);
     int err = 0;
     while (!R.done) {
         if (R.i > A.max_rounds) {
@@ -1095,7 +891,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(A, st, nxt, nseg);
+        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, nxt, nseg);
     }
     __syncthreads();
     for (long long p = tid; p < L; p += TAIL_THREADS) {
@@ -1117,6 +913,17 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         ctl->scan_volume = st.scan;
         if (!err) ctl->status = ST_DONE;
     }
+}
+
+// best_mask[u] = (peel_round[u] > best_round) for a best round known on the host
+__global__ void k_mask_rounds(const int *pr, long long n, long long br, uint8_t *mask) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        mask[u] = (long long)pr[u] > br ? 1 : 0;
+}
+
+void launch_mask(const int *pr, long long n, long long best_round, uint8_t *mask, cudaStream_t s) {
+    const int grid = (int)std::min<long long>(1024, (n + 255) / 256);
+    k_mask_rounds<<<grid > 0 ? grid : 1, 256, 0, s>>>(pr, n, best_round, mask);
 }
 
 // best_mask[u] = (peel_round[u] > best_round)

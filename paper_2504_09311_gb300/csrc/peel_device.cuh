@@ -1,0 +1,210 @@
+// peel_device.cuh -- device building blocks shared by the peel kernels
+// (single graph: peel.cu; many graphs, one CTA each: batch.cu).
+#pragma once
+#include "dupin_common.cuh"
+
+#define BULK_THREADS 512
+#define BULK_WARPS (BULK_THREADS / 32)
+#define WALK_WIN 1024
+#define INIT_THREADS 256
+#define INIT_WARPS (INIT_THREADS / 32)
+#ifndef TAIL_THREADS
+#define TAIL_THREADS 512
+#endif
+#define TAIL_WARPS (TAIL_THREADS / 32)
+#define SCAN_THREADS 1024
+
+
+static const long long kMaxLL = 0x7fffffffffffffffLL;
+
+// ------------------------------------------------------------ block helpers
+
+// Block-wide reduction of NV 64-bit sums, one u128 sum and one minimum.
+// All threads get the results.  Two __syncthreads.
+template <int NWARPS, int NV>
+struct BlockRed {
+    long long v[NV];
+    unsigned long long lo, hi;
+    long long mn;
+};
+
+template <int NWARPS, int NV>
+__device__ __forceinline__ void block_reduce(BlockRed<NWARPS, NV> &r, long long (*s_v)[NV], unsigned long long *s_lo,
+                                             unsigned long long *s_hi, long long *s_mn) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; j++) r.v[j] = warp_sum64(r.v[j]);
+    warp_sum128(r.lo, r.hi);
+    r.mn = warp_min64(r.mn);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; j++) s_v[wid][j] = r.v[j];
+        s_lo[wid] = r.lo;
+        s_hi[wid] = r.hi;
+        s_mn[wid] = r.mn;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        bool in = lane < NWARPS;
+#pragma unroll
+        for (int j = 0; j < NV; j++) r.v[j] = in ? s_v[lane][j] : 0;
+        r.lo = in ? s_lo[lane] : 0;
+        r.hi = in ? s_hi[lane] : 0;
+        r.mn = in ? s_mn[lane] : kMaxLL;
+#pragma unroll
+        for (int j = 0; j < NV; j++) r.v[j] = warp_sum64(r.v[j]);
+        warp_sum128(r.lo, r.hi);
+        r.mn = warp_min64(r.mn);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NV; j++) s_v[0][j] = r.v[j];
+            s_lo[0] = r.lo;
+            s_hi[0] = r.hi;
+            s_mn[0] = r.mn;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; j++) r.v[j] = s_v[0][j];
+    r.lo = s_lo[0];
+    r.hi = s_hi[0];
+    r.mn = s_mn[0];
+    __syncthreads();
+}
+
+// Exclusive block scan of one 64-bit value per thread; 'total' gets the sum.
+template <int NWARPS>
+__device__ __forceinline__ long long block_excl_scan(long long x, long long *s_w, long long &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = warp_incl_scan64(x);
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long v = lane < NWARPS ? s_w[lane] : 0;
+        v = warp_incl_scan64(v);
+        if (lane < NWARPS) s_w[lane] = v;
+    }
+    __syncthreads();
+    long long before = wid ? s_w[wid - 1] : 0;
+    total = s_w[NWARPS - 1];
+    __syncthreads();
+    return before + incl - x;
+}
+
+// last t in [0, n) with s[t] <= x (s non-decreasing, s[0] <= x)
+__device__ __forceinline__ int smem_last_le(const long long *s, int n, long long x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Walk the arcs [e0, e1) of a segmented arc space.  Entry k (0 <= k < U)
+// covers [base(k), base(k+1)) and its arcs sit at col positions start(k) + (x -
+// base(k)); base(U) is the total.  k0 must satisfy base(k0) <= e0.  The
+// block loads WALK_WIN entries at a time into shared memory and calls
+// fn(k, pos) once per arc, consecutive threads on consecutive arcs.
+template <class BaseF, class StartF, class ArcF>
+__device__ __forceinline__ void walk_arcs(BaseF base, StartF start, long long U, long long e0, long long e1,
+                                          long long k0, long long *s_base, long long *s_start, ArcF fn) {
+    long long e = e0, k = k0;
+    while (e < e1) {
+        __syncthreads();
+        for (int t = threadIdx.x; t <= WALK_WIN; t += blockDim.x) {
+            long long idx = k + t;
+            s_base[t] = idx <= U ? base(idx) : kMaxLL;
+            s_start[t] = idx < U ? start(idx) : 0;
+        }
+        __syncthreads();
+        long long wend = s_base[WALK_WIN];
+        long long hi = e1 < wend ? e1 : wend;
+        for (long long x = e + threadIdx.x; x < hi; x += blockDim.x) {
+            int t = smem_last_le(s_base, WALK_WIN, x);
+            fn(k + t, s_start[t] + (x - s_base[t]));
+        }
+        int t2 = smem_last_le(s_base, WALK_WIN + 1, hi);
+        k += t2;
+        e = hi;
+    }
+}
+
+
+struct RoundState {
+    long long round, size;
+    u128 f;
+    long long live_len;
+    int live_sel;
+    long long minw;
+    long long best_round, best_size;
+    u128 bf;
+    long long gpo_le, n_min_rule, scan;
+};
+
+
+// Shared accumulator of one tail round (double-buffered by round parity).
+struct TailAcc {
+    unsigned long long wlo, whi;  // sum of the removed vertices' weights
+    unsigned long long ilo, ihi;  // sum of c over arcs inside U
+    unsigned int F;               // |U_i|
+    unsigned int pad;
+};
+
+// The parameters of one round, computed identically by every warp.
+struct TailRound {
+    long long i;                  // round number
+    unsigned long long Xhi, Xlo;  // X = k (D+N) f
+    unsigned long long Y;         // Y = D |S|
+    long long gle;                // Algorithm 3's floor(tau_max), -1 without GPO
+    long long minw;               // minimum live weight
+    int minrule;                  // threshold selects nobody: take the minimum
+    int done;                     // S is empty
+};
+
+__device__ __forceinline__ void acc_add128(unsigned long long *lo, unsigned long long *hi, unsigned long long xlo,
+                                           unsigned long long xhi) {
+    if (xlo) {
+        unsigned long long old = atomicAdd(lo, xlo);
+        if (old + xlo < old) xhi += 1;
+    }
+    if (xhi) atomicAdd(hi, xhi);
+}
+
+#define TAIL_FAST 32
+#define TAIL_SEG 64  // vertices per segment (one warp, two per lane)
+
+// can segment minimum sm hold a vertex that round R selects?
+__device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) {
+    if (sm == kMaxLL) return false;
+    return R.minrule ? sm == R.minw : (sm <= R.gle || mul_le(sm, R.Y, R.Xhi, R.Xlo));
+}
+
+// Every warp (all lanes, identical result): plan round st.round + 1 from the
+// state and the segment minima -- thresholds, minimum live weight, minimum rule.
+__device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int use_min, int gpo, RoundState &st,
+                                               const long long *segmin, int nseg) {
+    const int lane = threadIdx.x & 31;
+    long long m = kMaxLL;
+    for (int q = lane; q < nseg; q += 32) m = segmin[q] < m ? segmin[q] : m;
+    m = warp_min64(m);
+    m = __shfl_sync(0xffffffffu, m, 0);
+    const u128 X = (u128)(unsigned long long)kD * st.f;
+    TailRound R;
+    R.i = st.round + 1;
+    R.Xhi = (unsigned long long)(X >> 64);
+    R.Xlo = (unsigned long long)X;
+    R.Y = (unsigned long long)D * (unsigned long long)st.size;
+    R.gle = -1;
+    if (gpo && st.size > 0) {
+        long long le = floor_ratio((unsigned long long)D, st.f, (unsigned long long)kD, st.size);
+        st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
+        R.gle = st.gpo_le;
+    }
+    R.minw = m;
+    R.minrule = (use_min && st.size > 0 && !mul_le(m, R.Y, R.Xhi, R.Xlo) && m > R.gle) ? 1 : 0;
+    R.done = st.size == 0 ? 1 : 0;
+    return R;
+}
+

@@ -1,0 +1,144 @@
+"""Batched and served peels equal single-graph peels exactly (GPU).
+
+dupin_peel_batch runs window-sized graphs one CTA each in one persistent
+launch and larger graphs through the single-graph path; the serving layer
+admits requests into slots under a device-memory budget and runs them
+concurrently.  The arithmetic is the same exact integer peel, so every
+result (peel rounds, density trace, best prefix) must be bit-identical to
+dupin_peel on the same graph, alone or in a mix.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_09311_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dupin():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2504_09311_gb300 import dupin as d
+
+    d.lib()
+    return d
+
+
+def same(a, b, ctx=""):
+    assert a.n_rounds == b.n_rounds, ctx
+    assert np.array_equal(a.peel_round, b.peel_round), ctx
+    assert (a.best_round, a.best_size, a.best_f) == (b.best_round, b.best_size, b.best_f), ctx
+    assert a.n_min_rule == b.n_min_rule, ctx
+    if a.trace_f is not None and b.trace_f is not None:
+        assert a.trace_f == b.trace_f, ctx
+        assert np.array_equal(np.asarray(a.trace_size), np.asarray(b.trace_size)), ctx
+
+
+def window_graphs(count, seed, lo=1000, hi=60000):
+    sizes = synth.window_sizes(count, lo, hi, seed=seed)
+    return [synth.transaction_window(int(m), seed=seed * 1000 + j) for j, m in enumerate(sizes)]
+
+
+def test_batch_equals_single(dupin):
+    gs = window_graphs(24, seed=3)
+    # one graph beyond the one-CTA limit takes the single-graph path
+    big = synth.bipartite_zipf(200_000, 100_000, 900_000, 1.8, 1, 50, 50, 0.4, 10, seed=9)
+    big.c = synth.fd_weights(big)
+    gs.insert(5, big)
+    # and a DW graph with vertex weights, and a DG graph
+    dw = synth.random_general(5000, 40000, seed=2)
+    synth.with_weights(dw, "dw", seed=2, a_range=(0, 4))
+    gs.append(dw)
+    gs.append(synth.dg_planted_block(seed=2, nU=3000, nI=1500, draws=20000, block=60, p=0.5))
+    metrics = ["fd"] * 25 + ["dw", "dg"]
+    dgs = [dupin.Graph.from_synth(g) for g in gs]
+    params = []
+    for j, g in enumerate(gs):
+        k = 1 + (j % 2)
+        eps = [(1, 10), (0, 1), (1, 5)][j % 3]
+        flags = dupin.GPO if j % 5 == 4 else 0
+        params.append(dupin.make_params(metrics[j], k, eps, flags=flags))
+    outs = dupin.peel_batch(dgs, params, want_rounds=True, want_trace=True)
+    for j, (g, dg, p) in enumerate(zip(gs, dgs, params)):
+        ref = dupin.peel(dg, p.metric, p.k_mult, (p.eps_num, p.eps_den), flags=p.flags)
+        same(outs[j], ref, j)
+    # the small case against the oracle as well
+    og = oracle.Graph.from_synth(gs[0], "fd")
+    r = oracle.peel_batch(og, params[0].k_mult, (params[0].eps_num, params[0].eps_den))
+    assert np.array_equal(outs[0].peel_round, r.peel_round) and outs[0].trace_f == r.trace_f
+    for dg in dgs:
+        dg.free()
+
+
+def test_batch_repeated_graph_and_device_results(dupin):
+    import torch
+
+    g = synth.transaction_window(20000, seed=77)
+    dg = dupin.Graph.from_synth(g)
+    ps = [dupin.make_params("fd", 1, e) for e in ((1, 10), (1, 20), (0, 1))] * 2
+    outs = dupin.peel_batch([dg] * len(ps), ps, want_rounds=True, want_trace=True)
+    for o, p in zip(outs, ps):
+        same(o, dupin.peel(dg, "fd", 1, (p.eps_num, p.eps_den)))
+    # device-resident results
+    k = 3
+    prs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(k)]
+    mks = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for _ in range(k)]
+    P = (dupin.Params * k)()
+    R = (dupin.Result * k)()
+    G = (ctypes.c_void_p * k)(*[dg.handle.value] * k)
+    for j in range(k):
+        P[j] = dupin.make_params("fd", 1, ((1, 10), (1, 20), (0, 1))[j], flags=dupin.RESULT_DEVICE)
+        R[j].peel_round = prs[j].data_ptr()
+        R[j].best_mask = mks[j].data_ptr()
+    dupin.check(dupin.lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
+                                             ctypes.cast(R, ctypes.c_void_p), k, None))
+    torch.cuda.synchronize()
+    for j in range(k):
+        ref = dupin.peel(dg, "fd", 1, ((1, 10), (1, 20), (0, 1))[j])
+        assert np.array_equal(prs[j].cpu().numpy(), ref.peel_round)
+        assert np.array_equal(mks[j].cpu().numpy(), ref.best_mask)
+        assert R[j].best_round == ref.best_round
+    dg.free()
+
+
+def test_serving_alone_and_in_a_mix(dupin):
+    gs = window_graphs(16, seed=5, lo=1000, hi=40000)
+    big = synth.bipartite_zipf(40_000, 20_000, 200_000, 1.8, 1, 40, 40, 0.4, 10, seed=4)
+    big.c = synth.fd_weights(big)
+    gs.append(big)
+    dgs = [dupin.Graph.from_synth(g) for g in gs]
+    refs = [dupin.peel(dg, "fd", 1, (1, 10)) for dg in dgs]
+    srv = dupin.Server(memory_budget=2 << 30, max_slots=8)
+    p = dupin.make_params("fd", 1, (1, 10))
+    # alone: one request at a time
+    for j in (0, len(dgs) - 1):
+        t = srv.submit(dgs[j], p, want_trace=True)
+        same(srv.wait(t), refs[j], ("alone", j))
+    # in a mix: everything at once, several times over, waited in reverse order
+    tickets = [(j, srv.submit(dgs[j], p, want_trace=True)) for _ in range(3) for j in range(len(dgs))]
+    for j, t in reversed(tickets):
+        same(srv.wait(t), refs[j], ("mix", j))
+    st = srv.stats()
+    assert st["completed"] == st["submitted"] == 2 + 3 * len(dgs)
+    assert st["p99_ms"] >= st["p50_ms"] > 0 and st["graphs_per_s"] > 0
+    srv.close()
+    for dg in dgs:
+        dg.free()
+
+
+def test_serving_budget(dupin):
+    g = synth.transaction_window(50000, seed=8)
+    dg = dupin.Graph.from_synth(g)
+    srv = dupin.Server(memory_budget=1 << 16, max_slots=2)  # far below one request's state
+    with pytest.raises(dupin.DupinError) as e:
+        srv.submit(dg, dupin.make_params("fd", 1, (1, 10)))
+    assert e.value.code == dupin.ERR_OOM
+    assert srv.stats()["rejected"] == 1
+    srv.close()
+    dg.free()
