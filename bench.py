@@ -149,6 +149,88 @@ def algorithmic_bytes(g, pr, trace_size, n_bulk, metric):
             "bulk_arcs": bulk_arcs, "tail_live_arcs": tail_live_arcs}
 
 
+def bench_batched(dupin, stream, args):
+    """4,096 transaction windows (edges log-uniform in 1k..500k, FD, eps=1/10, k=1) peeled by one
+    dupin_peel_batch call vs one dupin_peel per graph; results must be identical."""
+    import torch
+
+    from paper_2504_09311_gb300 import synth
+
+    t0 = time.perf_counter()
+    gs = synth.transaction_windows(args.windows, seed=1)
+    tgen = time.perf_counter() - t0
+    dgs = [dupin.Graph.from_synth(g) for g in gs]
+    ps = [dupin.make_params("fd", 1, (1, 10)) for _ in gs]
+    for _ in range(2):
+        dupin.peel_batch(dgs, ps, want_rounds=False, stream=stream)
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        outs = dupin.peel_batch(dgs, ps, want_rounds=True, stream=stream)
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    singles = [dupin.peel(dg, "fd", 1, (1, 10), want_mask=False, want_trace=False, stream=stream) for dg in dgs]
+    torch.cuda.synchronize()
+    tl = time.perf_counter() - t0
+    same = all(np.array_equal(a.peel_round, b.peel_round) and a.best_round == b.best_round and a.best_f == b.best_f
+               for a, b in zip(outs, singles))
+    edges = int(sum(g.m for g in gs))
+    for dg in dgs:
+        dg.free()
+    return {"workload": f"{args.windows} bipartite windows, edges log-uniform 1k..500k (total {edges}), FD, "
+                        "eps=1/10, k=1", "graphs_per_s": args.windows / tb, "edges_per_s": edges / tb,
+            "ms": tb * 1e3, "one_launch_per_graph_graphs_per_s": args.windows / tl, "speedup": tl / tb,
+            "identical_to_single": bool(same), "generation_s": round(tgen, 1)}
+
+
+def bench_serving(dupin, args, requests=2000, rate=2000.0):
+    """Poisson stream (mean 2,000 req/s) of FD peels over resident graphs: the window mix plus
+    1% of requests on a few R-MAT scale-21 graphs (edge factor 10); p50/p99 from the server."""
+    import threading
+
+    from paper_2504_09311_gb300 import synth
+
+    pool = synth.transaction_windows(256, seed=7)
+    big = [synth.rmat_weighted(21, 10, "fd", seed=s) for s in (1, 2)]
+    gpool = [dupin.Graph.from_synth(g) for g in pool]
+    gbig = [dupin.Graph.from_synth(g) for g in big]
+    p = dupin.make_params("fd", 1, (1, 10))
+    arrivals = synth.poisson_arrivals(requests, rate, seed=3)
+    pick = synth.uniform_ints(requests, 1_000_000, seed=4)
+    srv = dupin.Server(memory_budget=16 << 30, max_slots=8)
+    tickets = []
+    t0 = time.perf_counter()
+    for j in range(requests):
+        dt = arrivals[j] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        if pick[j] % 100 == 0:
+            g = gbig[int(pick[j] // 100) % len(gbig)]
+        else:
+            g = gpool[int(pick[j]) % len(gpool)]
+        tickets.append((g, srv.submit(g, p, want_rounds=True)))
+    outs = [(g, srv.wait(t)) for g, t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # every result equals the graph's own peel alone
+    ref = {}
+    mismatch = 0
+    for g, o in outs:
+        key = id(g)
+        if key not in ref:
+            ref[key] = dupin.peel(g, "fd", 1, (1, 10), want_mask=False, want_trace=False)
+        r = ref[key]
+        mismatch += 0 if (np.array_equal(o.peel_round, r.peel_round) and o.best_f == r.best_f) else 1
+    for g in gpool + gbig:
+        g.free()
+    return {"workload": f"{requests} requests, Poisson {rate:.0f}/s, 256 windows + 1% on 2 R-MAT-21 (ef 10) graphs",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "graphs_per_s": requests / wall,
+            "completed": st["completed"], "mismatches_vs_alone": mismatch}
+
+
 def cpu_baseline(g, metric, eps, k):
     import oracle
 
@@ -200,6 +282,9 @@ def main():
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--windows", type=int, default=4096)
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.k is not None:
@@ -330,12 +415,15 @@ def main():
                "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
                "includes": "graph load from pinned host memory + validation + 3 peels + result copies + free"}
 
+    batched = None if args.no_batch else bench_batched(dupin, stream, args)
+    serving = None if args.no_serve else bench_serving(dupin, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, metric, epss[1] if len(epss) > 1 else epss[0], k)
         cpu["unit"] = "edges/s"
 
-    launches_per_peel = 14
+    launches_per_peel = 13  # reset, init x4, bulk, tail build x5, tail, mask
     line = {
         "metric": "edges peeled/s", "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -351,6 +439,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches_per_peel * len(params) * args.steps,
         "clocks": clocks.summary(),
+        "batched": batched,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

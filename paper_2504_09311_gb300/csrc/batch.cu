@@ -352,44 +352,74 @@ static int set_cta_smem() {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Run a set of graphs through k_peel_cta.  idx lists the batch positions;
-// results go to results[idx[k]] (host arrays, or device arrays with
-// DUPIN_RESULT_DEVICE).  Synchronises the stream.
-int run_cta_jobs(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
-                 const std::vector<int64_t> &idx, cudaStream_t s) {
+static long long trace_cap_of(const dupin_graph *g, const dupin_params &p) {
+    const long long mr = p.max_rounds > 0 ? p.max_rounds : g->n + 1;
+    return std::min<long long>(mr, g->n) + 1;
+}
+
+long long cta_graph_limit() { return CTA_MAX_N; }
+
+// device bytes one graph takes in a batch arena
+long long cta_job_bytes(const dupin_graph *g, const dupin_params *p) {
+    const long long n = g->n;
+    return (long long)(align256(8 * (size_t)n) + align256(4 * (size_t)n) + align256(4 * (size_t)n) +
+                       align256(32 * (size_t)trace_cap_of(g, *p)) + 64 + sizeof(CtaJob) + 256);
+}
+
+struct CtaBatch {
+    unsigned char *arena = nullptr;
+    size_t nj = 0, outs_base = 0;
+    std::vector<size_t> off_pr, off_tr;
+    std::vector<long long> trcap;
+    std::vector<int64_t> idx;
+    dupin_graph *const *graphs = nullptr;
+    const dupin_params *params = nullptr;
+    dupin_result *results = nullptr;
+};
+
+// Enqueue one persistent launch for graphs[idx[k]] on stream s (no host
+// synchronisation).  Results stay in the arena until cta_batch_finish.
+int cta_batch_enqueue(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
+                      const std::vector<int64_t> &idx, cudaStream_t s, CtaBatch **out) {
+    *out = nullptr;
     if (idx.empty()) return DUPIN_OK;
     int rc = set_cta_smem();
     if (rc) return rc;
+    CtaBatch *B = new CtaBatch();
+    B->graphs = graphs;
+    B->params = params;
+    B->results = results;
+    B->idx = idx;
     const size_t nj = idx.size();
-    // arena: jobs | next | per job: w, front, pr, trace x4, out
-    std::vector<size_t> off_w(nj), off_f(nj), off_pr(nj), off_tr(nj), off_out(nj);
-    std::vector<long long> trcap(nj);
+    B->nj = nj;
+    std::vector<size_t> off_w(nj), off_f(nj);
+    B->off_pr.resize(nj);
+    B->off_tr.resize(nj);
+    B->trcap.resize(nj);
     size_t at = align256(sizeof(CtaJob) * nj) + 256;
-    const size_t outs_base = at;
+    B->outs_base = at;
     at = align256(at + 64 * nj);
     for (size_t k = 0; k < nj; k++) {
         const dupin_graph *g = graphs[idx[k]];
-        const dupin_params &p = params[idx[k]];
         const long long n = g->n;
-        long long mr = p.max_rounds > 0 ? p.max_rounds : n + 1;
-        trcap[k] = std::min<long long>(mr, n) + 1;
+        B->trcap[k] = trace_cap_of(g, params[idx[k]]);
         off_w[k] = at;
         at = align256(at + 8 * (size_t)n);
         off_f[k] = at;
         at = align256(at + 4 * (size_t)n);
-        off_pr[k] = at;
+        B->off_pr[k] = at;
         at = align256(at + 4 * (size_t)n);
-        off_tr[k] = at;
-        at = align256(at + 32 * (size_t)trcap[k]);
-        off_out[k] = outs_base + 64 * k;
+        B->off_tr[k] = at;
+        at = align256(at + 32 * (size_t)B->trcap[k]);
     }
-    unsigned char *arena = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&arena, at, s);
+    cudaError_t e = cudaMallocAsync((void **)&B->arena, at, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        delete B;
         return dupin_fail(e == cudaErrorMemoryAllocation ? DUPIN_ERR_OOM : DUPIN_ERR_CUDA,
                           std::string("batch arena: ") + cudaGetErrorString(e));
     }
+    unsigned char *arena = B->arena;
     std::vector<CtaJob> jobs(nj);
     for (size_t k = 0; k < nj; k++) {
         const dupin_graph *g = graphs[idx[k]];
@@ -412,15 +442,16 @@ int run_cta_jobs(dupin_graph *const *graphs, const dupin_params *params, dupin_r
         J.front = (int *)(arena + off_f[k]);
         const bool dev = (p.flags & DUPIN_RESULT_DEVICE) != 0;
         dupin_result &r = results[idx[k]];
-        J.pr = (dev && r.peel_round) ? r.peel_round : (int *)(arena + off_pr[k]);
-        long long *tr = (long long *)(arena + off_tr[k]);
+        J.pr = (dev && r.peel_round) ? r.peel_round : (int *)(arena + B->off_pr[k]);
+        long long *tr = (long long *)(arena + B->off_tr[k]);
+        const long long tc = B->trcap[k];
         const bool user_tr = dev && r.trace_f_hi && r.trace_f_lo && r.trace_size && r.trace_peeled;
         J.tr_f_hi = user_tr ? (long long *)r.trace_f_hi : tr;
-        J.tr_f_lo = user_tr ? (unsigned long long *)r.trace_f_lo : (unsigned long long *)(tr + trcap[k]);
-        J.tr_size = user_tr ? (long long *)r.trace_size : tr + 2 * trcap[k];
-        J.tr_peeled = user_tr ? (long long *)r.trace_peeled : tr + 3 * trcap[k];
-        J.tr_cap = user_tr ? std::min<long long>(trcap[k], r.trace_cap) : trcap[k];
-        J.out = (long long *)(arena + off_out[k]);
+        J.tr_f_lo = user_tr ? (unsigned long long *)r.trace_f_lo : (unsigned long long *)(tr + tc);
+        J.tr_size = user_tr ? (long long *)r.trace_size : tr + 2 * tc;
+        J.tr_peeled = user_tr ? (long long *)r.trace_peeled : tr + 3 * tc;
+        J.tr_cap = user_tr ? std::min<long long>(tc, r.trace_cap) : tc;
+        J.out = (long long *)(arena + B->outs_base + 64 * k);
     }
     int *next = (int *)(arena + align256(sizeof(CtaJob) * nj));
     int sms = 0, dev = 0, occ = 0;
@@ -435,25 +466,42 @@ int run_cta_jobs(dupin_graph *const *graphs, const dupin_params *params, dupin_r
         k_peel_cta<<<grid, CTA_THREADS, 2 * CTA_MAX_SEG * sizeof(long long), s>>>((const CtaJob *)arena, (int)nj, next);
         e = cudaGetLastError();
     }
-    // scalars of every job in one copy
+    if (e != cudaSuccess) {
+        cudaFreeAsync(B->arena, s);
+        delete B;
+        return dupin_cuda_fail(e, "batched peel launch");
+    }
+    *out = B;
+    return DUPIN_OK;
+}
+
+// Copy a finished batch's results into the callers' result structs and free
+// its arena.  'status' gets the first failing graph's code (0 if none).
+int cta_batch_finish(CtaBatch *B, cudaStream_t s, std::vector<int> *per_job_status) {
+    if (!B) return DUPIN_OK;
+    const size_t nj = B->nj;
+    unsigned char *arena = B->arena;
     std::vector<long long> outs(8 * nj);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(outs.data(), arena + outs_base, 64 * nj, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(outs.data(), arena + B->outs_base, 64 * nj, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int status = DUPIN_OK;
     std::string msg;
+    if (per_job_status) per_job_status->assign(nj, DUPIN_OK);
     for (size_t k = 0; k < nj && e == cudaSuccess; k++) {
-        const dupin_graph *g = graphs[idx[k]];
-        const dupin_params &p = params[idx[k]];
-        dupin_result &r = results[idx[k]];
+        const int64_t j = B->idx[k];
+        const dupin_graph *g = B->graphs[j];
+        const dupin_params &p = B->params[j];
+        dupin_result &r = B->results[j];
         const long long *o = &outs[8 * k];
         r.n_rounds = o[0];
         r.n_min_rule = o[5];
         r.n_bulk_rounds = 0;
         for (int q = 0; q < 4; q++) r.phase_ms[q] = 0.f;
         if (o[6]) {
+            if (per_job_status) (*per_job_status)[k] = (int)o[6];
             if (!status) {
                 status = (int)o[6];
-                msg = "graph " + std::to_string((long long)idx[k]) + ": max_rounds reached before the set became empty";
+                msg = "graph " + std::to_string((long long)j) + ": max_rounds reached before the set became empty";
             }
             continue;
         }
@@ -466,25 +514,28 @@ int run_cta_jobs(dupin_graph *const *graphs, const dupin_params *params, dupin_r
         const bool dev = (p.flags & DUPIN_RESULT_DEVICE) != 0;
         const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         const long long n = g->n;
-        const int *pr_dev = dev && r.peel_round ? r.peel_round : (const int *)(arena + off_pr[k]);
-        if (r.peel_round && !dev && n > 0)
-            e = cudaMemcpyAsync(r.peel_round, pr_dev, 4 * (size_t)n, kind, s);
+        const int *pr_dev = dev && r.peel_round ? r.peel_round : (const int *)(arena + B->off_pr[k]);
+        if (r.peel_round && !dev && n > 0) e = cudaMemcpyAsync(r.peel_round, pr_dev, 4 * (size_t)n, kind, s);
         const long long nt = o[0] + 1;
         const bool want_tr = r.trace_f_hi || r.trace_f_lo || r.trace_size || r.trace_peeled;
         const bool user_tr = dev && r.trace_f_hi && r.trace_f_lo && r.trace_size && r.trace_peeled;
         if (want_tr && !user_tr && e == cudaSuccess) {
             const long long cnt = std::min<long long>(nt, (long long)r.trace_cap);
-            const long long *tr = (const long long *)(arena + off_tr[k]);
+            const long long *tr = (const long long *)(arena + B->off_tr[k]);
+            const long long tc = B->trcap[k];
             if (cnt > 0) {
                 if (r.trace_f_hi) e = cudaMemcpyAsync(r.trace_f_hi, tr, 8 * (size_t)cnt, kind, s);
-                if (r.trace_f_lo && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_f_lo, tr + trcap[k], 8 * (size_t)cnt, kind, s);
-                if (r.trace_size && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_size, tr + 2 * trcap[k], 8 * (size_t)cnt, kind, s);
-                if (r.trace_peeled && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_peeled, tr + 3 * trcap[k], 8 * (size_t)cnt, kind, s);
+                if (r.trace_f_lo && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_f_lo, tr + tc, 8 * (size_t)cnt, kind, s);
+                if (r.trace_size && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_size, tr + 2 * tc, 8 * (size_t)cnt, kind, s);
+                if (r.trace_peeled && e == cudaSuccess) e = cudaMemcpyAsync(r.trace_peeled, tr + 3 * tc, 8 * (size_t)cnt, kind, s);
             }
         }
-        if (want_tr && r.trace_cap < nt && !status) {
-            status = DUPIN_ERR_BUFFER_TOO_SMALL;
-            msg = "graph " + std::to_string((long long)idx[k]) + ": trace_cap < n_rounds + 1";
+        if (want_tr && r.trace_cap < nt) {
+            if (per_job_status) (*per_job_status)[k] = DUPIN_ERR_BUFFER_TOO_SMALL;
+            if (!status) {
+                status = DUPIN_ERR_BUFFER_TOO_SMALL;
+                msg = "graph " + std::to_string((long long)j) + ": trace_cap < n_rounds + 1";
+            }
         }
         if (r.best_mask && n > 0 && e == cudaSuccess) {
             if (dev) {
@@ -504,6 +555,7 @@ int run_cta_jobs(dupin_graph *const *graphs, const dupin_params *params, dupin_r
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(arena, s);
+    delete B;
     if (e != cudaSuccess) return dupin_cuda_fail(e, "batched peel");
     if (status) return dupin_fail(status, msg);
     return DUPIN_OK;
@@ -528,7 +580,10 @@ extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *
         if (graphs[j]->n >= 1 && graphs[j]->n <= CTA_MAX_N) cta.push_back(j);
         else big.push_back(j);
     }
-    int rc = run_cta_jobs(graphs, params, results, cta, s);
+    CtaBatch *B = nullptr;
+    int rc = cta_batch_enqueue(graphs, params, results, cta, s, &B);
+    if (rc) return rc;
+    rc = cta_batch_finish(B, s, nullptr);
     if (rc) return rc;
     for (int64_t j : big) {
         rc = dupin_peel(graphs[j], &params[j], &results[j], stream);

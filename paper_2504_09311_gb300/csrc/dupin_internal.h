@@ -80,6 +80,15 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
 int launch_init_weights(const DevGraph &dg, int metric, long long *w, int *pr, int *live0, PeelCtl *ctl,
                         bool check, cudaStream_t s);
 
+// batched one-CTA-per-graph peels (batch.cu)
+#include <vector>
+struct CtaBatch;
+long long cta_graph_limit();
+long long cta_job_bytes(const dupin_graph *g, const dupin_params *p);
+int cta_batch_enqueue(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
+                      const std::vector<int64_t> &idx, cudaStream_t s, CtaBatch **out);
+int cta_batch_finish(CtaBatch *B, cudaStream_t s, std::vector<int> *per_job_status);
+
 // best_mask[u] = (peel_round[u] > best_round) on the device
 void launch_mask(const int *pr, long long n, long long best_round, uint8_t *mask, cudaStream_t s);
 

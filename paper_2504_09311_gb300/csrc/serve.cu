@@ -1,17 +1,18 @@
 // serve.cu -- continuous batching of peel requests over resident graphs.
 //
 // A worker thread owns 'max_slots' non-blocking CUDA streams.  Requests wait
-// in a FIFO queue and are admitted into a free slot as soon as the
-// device-memory budget has room for their per-request state (a peeling
-// workspace allocated stream-ordered on the slot's stream); graphs
-// themselves stay resident and are shared.  Admitted requests run
-// concurrently -- a graph small enough for the one-CTA peel occupies one SM,
-// so many of them overlap -- while new requests keep being admitted as
-// earlier ones finish.  A graph that needs the grid-wide persistent kernel
-// runs alone (it is admitted only when no other slot is busy and nothing is
-// admitted beside it), so co-residency of its cooperative grid is never in
-// question.  Every request's arithmetic is the same exact integer peel, so a
-// result is identical whether it ran alone or in a mix.
+// in a FIFO queue.  Whenever a slot is free, the worker takes the queued
+// requests for graphs small enough for one CTA (as many as the device-memory
+// budget admits, in arrival order) and launches them together as one
+// persistent one-CTA-per-graph peel on that slot's stream; it does not wait
+// for it, so requests arriving meanwhile go into the next launch on another
+// slot and the launches run side by side on the GPU.  A graph that needs the
+// grid-wide persistent kernel runs alone (admitted only when no slot is busy,
+// nothing admitted beside it), so its cooperative grid never competes for
+// SMs.  Graphs stay resident and shared; only per-request state is allocated
+// (stream-ordered, counted against the budget).  Every request's arithmetic
+// is the same exact integer peel, so a result is identical whether it ran
+// alone or in a mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,8 +43,20 @@ struct Request {
     double t_submit = 0, t_done = 0;
     int status = DUPIN_OK;
     bool done = false;
-    PeelWorkspace *ws = nullptr;
-    int slot = -1;
+};
+
+// what one slot is running: a batch of small requests, or one large request
+struct Slot {
+    std::vector<Request *> reqs;
+    CtaBatch *batch = nullptr;
+    PeelWorkspace *ws = nullptr;  // large request
+    long long bytes = 0;
+    bool busy = false;
+    bool large = false;
+    // the batch entry point wants arrays indexed by position
+    std::vector<dupin_graph *> gs;
+    std::vector<dupin_params> ps;
+    std::vector<dupin_result> rs;
 };
 
 }  // namespace
@@ -58,20 +71,128 @@ struct dupin_server {
     std::unordered_map<uint64_t, Request *> all;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
-    std::vector<Request *> running;
+    std::vector<Slot> slots;
     long long used_bytes = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
     bool exclusive = false;
-    long long submitted = 0, completed = 0, rejected = 0;
+    long long submitted = 0, completed = 0, rejected = 0, launches = 0;
     std::vector<double> lat_ms;
     double first_submit = -1, last_done = 0;
 };
 
-static int n_running(const dupin_server *s) {
+static int n_busy(const dupin_server *s) {
     int k = 0;
-    for (auto *q : s->running) k += q != nullptr;
+    for (const auto &sl : s->slots) k += sl.busy ? 1 : 0;
     return k;
+}
+
+static const size_t kMaxBatch = 4096;
+
+// Fill free slots from the queue (lock held on entry and exit).
+static bool admit(dupin_server *s, std::unique_lock<std::mutex> &lk) {
+    bool progress = false;
+    for (;;) {
+        if (s->queue.empty() || s->exclusive) return progress;
+        int slot = -1;
+        for (int i = 0; i < (int)s->slots.size(); i++)
+            if (!s->slots[i].busy) {
+                slot = i;
+                break;
+            }
+        if (slot < 0) return progress;
+        Slot &sl = s->slots[slot];
+        Request *front = s->queue.front();
+        sl.reqs.clear();
+        sl.bytes = 0;
+        if (front->large) {
+            if (n_busy(s) > 0) return progress;  // waits for an idle GPU
+            if (s->used_bytes + front->bytes > s->cfg.memory_budget) return progress;
+            s->queue.pop_front();
+            sl.reqs.push_back(front);
+            sl.bytes = front->bytes;
+            sl.large = true;
+            s->exclusive = true;
+        } else {
+            // consecutive small requests from the front, within the budget
+            while (!s->queue.empty() && sl.reqs.size() < kMaxBatch) {
+                Request *q = s->queue.front();
+                if (q->large) break;
+                if (s->used_bytes + sl.bytes + q->bytes > s->cfg.memory_budget) break;
+                s->queue.pop_front();
+                sl.reqs.push_back(q);
+                sl.bytes += q->bytes;
+            }
+            if (sl.reqs.empty()) return progress;
+            sl.large = false;
+        }
+        s->used_bytes += sl.bytes;
+        sl.busy = true;
+        s->launches++;
+        lk.unlock();
+        cudaStream_t st = s->streams[slot];
+        int rc = DUPIN_OK;
+        if (sl.large) {
+            Request *q = sl.reqs[0];
+            sl.ws = workspace_create(q->g->n, q->g->arcs, q->g->cw != nullptr, q->tail_cap, q->tr_cap, true, st, &rc);
+            if (rc == DUPIN_OK) rc = enqueue_peel(q->g, sl.ws, &q->p, q->tail_cap, q->max_rounds, st);
+        } else {
+            const size_t k = sl.reqs.size();
+            sl.gs.resize(k);
+            sl.ps.resize(k);
+            sl.rs.resize(k);
+            std::vector<int64_t> idx(k);
+            for (size_t j = 0; j < k; j++) {
+                sl.gs[j] = sl.reqs[j]->g;
+                sl.ps[j] = sl.reqs[j]->p;
+                sl.rs[j] = *sl.reqs[j]->r;
+                idx[j] = (int64_t)j;
+            }
+            rc = cta_batch_enqueue(sl.gs.data(), sl.ps.data(), sl.rs.data(), idx, st, &sl.batch);
+        }
+        if (rc == DUPIN_OK) {
+            cudaError_t e = cudaEventRecord(s->events[slot], st);
+            if (e != cudaSuccess) rc = dupin_cuda_fail(e, "cudaEventRecord");
+        }
+        lk.lock();
+        if (rc != DUPIN_OK)
+            for (Request *q : sl.reqs) q->status = rc;
+        progress = true;
+    }
+}
+
+static void finish_slot(dupin_server *s, int i) {
+    Slot &sl = s->slots[i];
+    cudaStream_t st = s->streams[i];
+    const bool launched_ok = sl.reqs.empty() || sl.reqs[0]->status == DUPIN_OK;
+    if (sl.large) {
+        Request *q = sl.reqs[0];
+        if (launched_ok) q->status = peel_finish(q->g, sl.ws, &q->p, q->r, st);
+        workspace_free(sl.ws, st);
+        sl.ws = nullptr;
+    } else if (sl.batch) {
+        std::vector<int> st_each;
+        cta_batch_finish(sl.batch, st, &st_each);
+        sl.batch = nullptr;
+        for (size_t j = 0; j < sl.reqs.size(); j++) {
+            *sl.reqs[j]->r = sl.rs[j];
+            if (j < st_each.size() && st_each[j] != DUPIN_OK) sl.reqs[j]->status = st_each[j];
+        }
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    const double t = now_s();
+    for (Request *q : sl.reqs) {
+        q->t_done = t;
+        q->done = true;
+        s->completed++;
+        if (q->status == DUPIN_OK) s->lat_ms.push_back((q->t_done - q->t_submit) * 1e3);
+    }
+    s->last_done = t;
+    s->used_bytes -= sl.bytes;
+    if (sl.large) s->exclusive = false;
+    sl.busy = false;
+    sl.reqs.clear();
+    s->done_cv.notify_all();
 }
 
 static void serve_loop(dupin_server *s) {
@@ -80,79 +201,35 @@ static void serve_loop(dupin_server *s) {
         bool progress = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->stop && s->queue.empty() && n_running(s) == 0) break;
-            // admission, first come first served
-            while (!s->queue.empty()) {
-                Request *q = s->queue.front();
-                const int busy = n_running(s);
-                if (s->exclusive) break;
-                if (q->large && busy > 0) break;
-                int slot = -1;
-                for (int i = 0; i < (int)s->running.size(); i++)
-                    if (!s->running[i]) {
-                        slot = i;
-                        break;
-                    }
-                if (slot < 0) break;
-                if (s->used_bytes + q->bytes > s->cfg.memory_budget) break;
-                s->queue.pop_front();
-                s->used_bytes += q->bytes;
-                q->slot = slot;
-                s->running[slot] = q;
-                if (q->large) s->exclusive = true;
-                lk.unlock();
-                cudaStream_t st = s->streams[slot];
-                int rc = DUPIN_OK;
-                q->ws = workspace_create(q->g->n, q->g->arcs, q->g->cw != nullptr, q->tail_cap, q->tr_cap, true, st, &rc);
-                if (rc == DUPIN_OK) rc = enqueue_peel(q->g, q->ws, &q->p, q->tail_cap, q->max_rounds, st);
-                if (rc == DUPIN_OK) {
-                    cudaError_t e = cudaEventRecord(s->events[slot], st);
-                    if (e != cudaSuccess) rc = dupin_cuda_fail(e, "cudaEventRecord");
-                }
-                lk.lock();
-                if (rc != DUPIN_OK) {
-                    q->status = rc;
-                    q->ws = q->ws;  // freed below with the others
-                }
-                progress = true;
-            }
+            if (s->stop && s->queue.empty() && n_busy(s) == 0) break;
+            progress = admit(s, lk);
         }
-        // completions
-        for (int i = 0; i < (int)s->running.size(); i++) {
-            Request *q;
+        for (int i = 0; i < (int)s->slots.size(); i++) {
+            bool busy;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
-                q = s->running[i];
+                busy = s->slots[i].busy;
             }
-            if (!q) continue;
-            if (q->status == DUPIN_OK) {
+            if (!busy) continue;
+            const bool failed = !s->slots[i].reqs.empty() && s->slots[i].reqs[0]->status != DUPIN_OK;
+            if (!failed) {
                 cudaError_t e = cudaEventQuery(s->events[i]);
                 if (e == cudaErrorNotReady) continue;
-                if (e != cudaSuccess) q->status = dupin_cuda_fail(e, "request kernels");
-                else q->status = peel_finish(q->g, q->ws, &q->p, q->r, s->streams[i]);
+                if (e != cudaSuccess) {
+                    const int rc = dupin_cuda_fail(e, "request kernels");
+                    for (Request *q : s->slots[i].reqs) q->status = rc;
+                }
             }
-            workspace_free(q->ws, s->streams[i]);
-            q->ws = nullptr;
-            std::lock_guard<std::mutex> lk(s->mu);
-            q->t_done = now_s();
-            q->done = true;
-            s->running[i] = nullptr;
-            s->used_bytes -= q->bytes;
-            if (q->large) s->exclusive = false;
-            s->completed++;
-            if (q->status == DUPIN_OK) s->lat_ms.push_back((q->t_done - q->t_submit) * 1e3);
-            s->last_done = q->t_done;
-            s->done_cv.notify_all();
+            finish_slot(s, i);
             progress = true;
         }
         if (!progress) {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (n_running(s) > 0) {
+            if (n_busy(s) > 0) {
                 lk.unlock();
                 std::this_thread::yield();
             } else {
-                s->cv.wait_for(lk, std::chrono::milliseconds(2),
-                               [&] { return s->stop || !s->queue.empty(); });
+                s->cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return s->stop || !s->queue.empty(); });
             }
         }
     }
@@ -167,7 +244,7 @@ extern "C" int dupin_serve_create(const dupin_serve_config *cfg, dupin_server **
     s->cfg = *cfg;
     s->streams.resize(cfg->max_slots);
     s->events.resize(cfg->max_slots);
-    s->running.assign(cfg->max_slots, nullptr);
+    s->slots.resize(cfg->max_slots);
     for (int i = 0; i < cfg->max_slots; i++) {
         cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
@@ -201,8 +278,9 @@ extern "C" int dupin_serve_submit(dupin_server *s, dupin_graph *g, const dupin_p
         delete q;
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "serving writes host results; DUPIN_RESULT_DEVICE is not accepted");
     }
-    q->large = g->n > q->tail_cap;
-    q->bytes = workspace_bytes(g->n, g->arcs, g->cw != nullptr, q->tail_cap, q->tr_cap, peel_grid_size());
+    q->large = g->n < 1 || g->n > cta_graph_limit();
+    q->bytes = q->large ? workspace_bytes(g->n, g->arcs, g->cw != nullptr, q->tail_cap, q->tr_cap, peel_grid_size())
+                        : cta_job_bytes(g, p);
     q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
     q->ticket = s->next_ticket++;
@@ -252,7 +330,8 @@ extern "C" int dupin_serve_stats(dupin_server *s, dupin_serve_stats_t *out) {
     out->submitted = s->submitted;
     out->completed = s->completed;
     out->rejected = s->rejected;
-    out->in_flight = n_running(s);
+    out->in_flight = 0;
+    for (const auto &sl : s->slots) out->in_flight += sl.busy ? (int64_t)sl.reqs.size() : 0;
     out->queued = (int64_t)s->queue.size();
     std::vector<double> v = s->lat_ms;
     std::sort(v.begin(), v.end());

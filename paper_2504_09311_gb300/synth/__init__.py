@@ -285,6 +285,23 @@ def transaction_window(m: int, seed: int) -> SynthGraph:
     return g
 
 
+def transaction_windows(count: int, seed: int = 1, lo: float = 1_000, hi: float = 500_000, workers: int = 0):
+    """The batched workload: 'count' windows with log-uniform edge counts, built in parallel
+    (the C generator releases the GIL; each window is single-threaded, so the output does not
+    depend on the worker count)."""
+    import concurrent.futures as cf
+
+    sizes = window_sizes(count, lo, hi, seed=seed)
+    workers = workers or (os.cpu_count() or 4)
+    lib().sg_set_threads(1)
+    try:
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            return list(ex.map(lambda jm: transaction_window(int(jm[1]), seed=seed * 1_000_003 + jm[0]),
+                               enumerate(sizes)))
+    finally:
+        lib().sg_set_threads(0)
+
+
 def poisson_arrivals(k: int, rate: float, seed: int) -> np.ndarray:
     t = np.empty(k, np.float64)
     lib().sg_poisson_arrivals(k, rate, seed, _ptr(t))
