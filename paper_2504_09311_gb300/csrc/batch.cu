@@ -128,7 +128,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         if (lane == 0) first[q] = m;
     }
     if (tid < 2) {
-        TailAcc z = {0, 0, 0, 0, 0, 0};
+        TailAcc z = TAIL_ACC_ZERO;
         s_acc[tid] = z;
     }
     __syncthreads();
@@ -152,7 +152,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         J.tr_size[0] = n;
         J.tr_peeled[0] = 0;
     }
-    TailRound R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, first, nseg);
+    TailRound R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, seg_global_min(first, nseg));
     int err = 0;
     while (!R.done) {
         if (R.i > J.max_rounds) {
@@ -165,11 +165,14 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         TailAcc &acc = s_acc[i & 1];
         // ---- select
         unsigned long long wlo = 0, whi = 0;
+        long long mins = kMaxLL;  // new minimum over the segments this lane looked at
         for (int q0 = wid * 32; q0 < nseg; q0 += CTA_THREADS) {
             const int q = q0 + lane;
             const long long sm = q < nseg ? cur[q] : kMaxLL;
             if (q < nseg) nxt[q] = sm;
-            unsigned cm = __ballot_sync(0xffffffffu, seg_candidate(sm, R));
+            const bool cand = seg_candidate(sm, R);
+            if (!cand) mins = sm < mins ? sm : mins;  // untouched by the select
+            unsigned cm = __ballot_sync(0xffffffffu, cand);
             __syncwarp();
             while (cm) {
                 const int qq = q0 + __ffs(cm) - 1;
@@ -188,7 +191,10 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
                 if (w0 >= 0 && !s0) m = w0;
                 if (w1 >= 0 && !s1 && w1 < m) m = w1;
                 m = warp_min64(m);
-                if (lane == 0) nxt[qq] = m;
+                if (lane == 0) {
+                    nxt[qq] = m;
+                    mins = m < mins ? m : mins;
+                }
                 const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
                 if (b0 | b1) {
                     unsigned base = 0;
@@ -219,15 +225,20 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
             }
         }
         warp_sum128(wlo, whi);
-        if (lane == 0) acc_add128(&acc.wlo, &acc.whi, wlo, whi);
+        mins = warp_min64(mins);
+        if (lane == 0) {
+            acc_add128(&acc.wlo, &acc.whi, wlo, whi);
+            if (mins != kMaxLL) atomicMin(&acc.mins, mins);
+        }
         __syncthreads();
         if (tid == 0) {
-            TailAcc z = {0, 0, 0, 0, 0, 0};
+            TailAcc z = TAIL_ACC_ZERO;
             s_acc[(i + 1) & 1] = z;
         }
         const int F = (int)acc.F;
         // ---- expand: every arc of the frontier (heads read from global memory)
         unsigned long long ilo = 0, ihi = 0;
+        long long mind = kMaxLL;
         auto arc = [&](long long pos) {
             const int v = arc_head(col[pos], hubs);
             const long long c = dg ? DUPIN_Q_ONE : cw[pos];
@@ -235,6 +246,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
             if (wv >= 0) {
                 const long long old = (long long)atomicAdd((unsigned long long *)&w[v], (unsigned long long)(-c));
                 atomicMin(&nxt[v / TAIL_SEG], old - c);
+                mind = old - c < mind ? old - c : mind;
             } else if (wv == -i) {
                 add128(ilo, ihi, (unsigned long long)c, 0);
             }
@@ -274,7 +286,11 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
             }
         }
         warp_sum128(ilo, ihi);
-        if (lane == 0) acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
+        mind = warp_min64(mind);
+        if (lane == 0) {
+            acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
+            if (mind != kMaxLL) atomicMin(&acc.mins, mind);
+        }
         __syncthreads();
         // ---- every warp: close round i, plan round i + 1
         const u128 wsel = mk128(acc.wlo, acc.whi), internal = mk128(acc.ilo, acc.ihi);
@@ -297,7 +313,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, nxt, nseg);
+        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, acc.mins);
     }
     __syncthreads();
     for (long long u = tid; u < n; u += CTA_THREADS) {
@@ -452,6 +468,18 @@ int cta_batch_enqueue(dupin_graph *const *graphs, const dupin_params *params, du
         J.tr_peeled = user_tr ? (long long *)r.trace_peeled : tr + 3 * tc;
         J.tr_cap = user_tr ? std::min<long long>(tc, r.trace_cap) : tc;
         J.out = (long long *)(arena + B->outs_base + 64 * k);
+    }
+    // largest graphs first: the queue hands them out before the small ones,
+    // so the launch does not end waiting for a big graph started last
+    {
+        std::vector<size_t> order(nj);
+        for (size_t k = 0; k < nj; k++) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+            return jobs[x].arcs + jobs[x].n > jobs[y].arcs + jobs[y].n;
+        });
+        std::vector<CtaJob> sorted(nj);
+        for (size_t k = 0; k < nj; k++) sorted[k] = jobs[order[k]];
+        jobs.swap(sorted);
     }
     int *next = (int *)(arena + align256(sizeof(CtaJob) * nj));
     int sms = 0, dev = 0, occ = 0;

@@ -163,9 +163,18 @@ __device__ __forceinline__ bool mul_le(long long w, unsigned long long Y, unsign
     return hi < Xhi || (hi == Xhi && lo <= Xlo);
 }
 
-// a/b > c/d for the best-prefix rule (strict: earliest round wins ties)
+// a * b mod 2^128 for a 64-bit b (three multiplies instead of a 128x128 product)
+__device__ __forceinline__ u128 mul_u128_u64(u128 a, unsigned long long b) {
+    const unsigned long long alo = (unsigned long long)a, ahi = (unsigned long long)(a >> 64);
+    const unsigned long long lo = alo * b;
+    const unsigned long long hi = __umul64hi(alo, b) + ahi * b;
+    return ((u128)hi << 64) | (u128)lo;
+}
+
+// a/b > c/d for the best-prefix rule (strict: earliest round wins ties);
+// a, c < 2^96 and b, d < 2^31, so both products fit in 128 bits
 __device__ __forceinline__ bool frac_gt(u128 a, long long b, u128 c, long long d) {
-    return a * (u128)(unsigned long long)d > c * (u128)(unsigned long long)b;
+    return mul_u128_u64(a, (unsigned long long)d) > mul_u128_u64(c, (unsigned long long)b);
 }
 
 __device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long xlo,

@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
     for (long long p = tid; p <= L; p += TAIL_THREADS) toff[p] = (int)A.tlrp[p];
     for (long long p = tid; p < LP; p += TAIL_THREADS) tw[p] = p < L ? A.w[live[p]] : -1;  // pads: gone
     if (tid < 2) {
-        TailAcc z = {0, 0, 0, 0, 0, 0};
+        TailAcc z = TAIL_ACC_ZERO;
         s_acc[tid] = z;
     }
     __syncthreads();
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         if (lane == 0) first[q] = m;
     }
     __syncthreads();
-    TailRound R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, first, nseg);
+    TailRound R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, seg_global_min(first, nseg));
     int err = 0;
     while (!R.done) {
         if (R.i > A.max_rounds) {
@@ -761,11 +761,14 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         // ---- select: lanes test segments in parallel; a candidate segment
         // is then scanned by its warp (two vertices per lane)
         unsigned long long wlo = 0, whi = 0;
+        long long mins = kMaxLL;  // new minimum over the segments this lane looked at
         for (int q0 = wid * 32; q0 < nseg; q0 += TAIL_THREADS) {
             const int q = q0 + lane;
             const long long sm = q < nseg ? cur[q] : kMaxLL;
             if (q < nseg) nxt[q] = sm;
-            unsigned cm = __ballot_sync(0xffffffffu, seg_candidate(sm, R));
+            const bool cand = seg_candidate(sm, R);
+            if (!cand) mins = sm < mins ? sm : mins;  // untouched by the select
+            unsigned cm = __ballot_sync(0xffffffffu, cand);
             __syncwarp();
             while (cm) {
                 const int qq = q0 + __ffs(cm) - 1;
@@ -784,7 +787,10 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                 if (v.x >= 0 && !s0) m = v.x;
                 if (v.y >= 0 && !s1 && v.y < m) m = v.y;
                 m = warp_min64(m);
-                if (lane == 0) nxt[qq] = m;
+                if (lane == 0) {
+                    nxt[qq] = m;
+                    mins = m < mins ? m : mins;
+                }
                 const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
                 if (b0 | b1) {
                     unsigned base = 0;
@@ -806,16 +812,21 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             }
         }
         warp_sum128(wlo, whi);
-        if (lane == 0) acc_add128(&acc.wlo, &acc.whi, wlo, whi);
+        mins = warp_min64(mins);
+        if (lane == 0) {
+            acc_add128(&acc.wlo, &acc.whi, wlo, whi);
+            if (mins != kMaxLL) atomicMin(&acc.mins, mins);
+        }
         __syncthreads();
         // round i+1's accumulator was last read in round i-1: reset it now
         if (tid == 0) {
-            TailAcc z = {0, 0, 0, 0, 0, 0};
+            TailAcc z = TAIL_ACC_ZERO;
             s_acc[(i + 1) & 1] = z;
         }
         const int F = (int)acc.F;
         // ---- expand
         unsigned long long ilo = 0, ihi = 0;
+        long long mind = kMaxLL;
         auto arc = [&](long long pos) {
             const int v = tcol[pos];
             const long long c = dg ? DUPIN_Q_ONE : tcw[pos];
@@ -823,6 +834,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             if (wv >= 0) {
                 const long long old = (long long)atomicAdd((unsigned long long *)&tw[v], (unsigned long long)(-c));
                 atomicMin(&nxt[v / TAIL_SEG], old - c);
+                mind = old - c < mind ? old - c : mind;
             } else if (wv == -i) {
                 add128(ilo, ihi, (unsigned long long)c, 0);
             }
@@ -867,7 +879,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             }
         }
         warp_sum128(ilo, ihi);
-        if (lane == 0) acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
+        mind = warp_min64(mind);
+        if (lane == 0) {
+            acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
+            if (mind != kMaxLL) atomicMin(&acc.mins, mind);
+        }
         __syncthreads();
         // ---- every warp: close round i and plan round i + 1 (same values everywhere)
         const u128 wsel = mk128(acc.wlo, acc.whi), internal = mk128(acc.ilo, acc.ihi);
@@ -891,7 +907,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, nxt, nseg);
+        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, acc.mins);
     }
     __syncthreads();
     for (long long p = tid; p < L; p += TAIL_THREADS) {

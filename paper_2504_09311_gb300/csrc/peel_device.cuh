@@ -9,7 +9,7 @@
 #define INIT_THREADS 256
 #define INIT_WARPS (INIT_THREADS / 32)
 #ifndef TAIL_THREADS
-#define TAIL_THREADS 512
+#define TAIL_THREADS 256
 #endif
 #define TAIL_WARPS (TAIL_THREADS / 32)
 #define SCAN_THREADS 1024
@@ -148,9 +148,12 @@ struct RoundState {
 struct TailAcc {
     unsigned long long wlo, whi;  // sum of the removed vertices' weights
     unsigned long long ilo, ihi;  // sum of c over arcs inside U
+    long long mins;               // minimum live weight after the round
     unsigned int F;               // |U_i|
     unsigned int pad;
 };
+
+#define TAIL_ACC_ZERO {0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0}
 
 // The parameters of one round, computed identically by every warp.
 struct TailRound {
@@ -182,15 +185,10 @@ __device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) 
 }
 
 // Every warp (all lanes, identical result): plan round st.round + 1 from the
-// state and the segment minima -- thresholds, minimum live weight, minimum rule.
+// state and the minimum live weight m -- thresholds and the minimum rule.
 __device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int use_min, int gpo, RoundState &st,
-                                               const long long *segmin, int nseg) {
-    const int lane = threadIdx.x & 31;
-    long long m = kMaxLL;
-    for (int q = lane; q < nseg; q += 32) m = segmin[q] < m ? segmin[q] : m;
-    m = warp_min64(m);
-    m = __shfl_sync(0xffffffffu, m, 0);
-    const u128 X = (u128)(unsigned long long)kD * st.f;
+                                               long long m) {
+    const u128 X = mul_u128_u64(st.f, (unsigned long long)kD);
     TailRound R;
     R.i = st.round + 1;
     R.Xhi = (unsigned long long)(X >> 64);
@@ -208,3 +206,11 @@ __device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int us
     return R;
 }
 
+// minimum of segment minima (one warp; all lanes get the result)
+__device__ __forceinline__ long long seg_global_min(const long long *segmin, int nseg) {
+    const int lane = threadIdx.x & 31;
+    long long m = kMaxLL;
+    for (int q = lane; q < nseg; q += 32) m = segmin[q] < m ? segmin[q] : m;
+    m = warp_min64(m);
+    return __shfl_sync(0xffffffffu, m, 0);
+}

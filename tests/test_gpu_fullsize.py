@@ -1,0 +1,82 @@
+"""Full-size workloads on the GPU, checked against the oracle.
+
+* FD transaction graph, 2M users x 1M items, 40.7M edges (the benchmark
+  workload): bit-exact against the oracle's full replay of Algorithm 2 for
+  eps = 1/20, and through the oracle's verifier for eps = 0 and 1/5.
+* R-MAT scale 18 (DW): bit-exact against the full replay, k = 1 and k = 2.
+* R-MAT scale 22 and scale 24 (DW, c in 1..100, a in 0..10; 64M and ~260M
+  edges): the replay would take too long single-threaded, so the verifier
+  checks every vertex's round against the definitions (its peeling weight at
+  the start of its round is at most the threshold recomputed from the trace,
+  or equals the minimum), recomputes the whole density trace from the peel
+  rounds, checks the best round, and checks every survivor at sampled rounds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_09311_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dupin():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2504_09311_gb300 import dupin as d
+
+    d.lib()
+    return d
+
+
+def verify(og, out, k, eps, nsample=3):
+    fh = np.array([x >> 64 for x in out.trace_f], np.int64)
+    fl = np.array([x & ((1 << 64) - 1) for x in out.trace_f], np.uint64)
+    return oracle.verify(og, k, eps, out.peel_round, out.n_rounds, fh, fl, out.trace_size, out.trace_peeled,
+                         out.best_round, nsample=nsample)
+
+
+def test_fd_config_full_size(dupin):
+    g = synth.fd_camouflage(seed=1)
+    dg = dupin.Graph.from_synth(g)
+    og = oracle.Graph.from_synth(g, "fd")
+    out = dupin.peel(dg, "fd", 1, (1, 20))
+    ref = oracle.peel_batch(og, 1, (1, 20))
+    assert np.array_equal(out.peel_round, ref.peel_round)
+    assert out.trace_f == ref.trace_f
+    assert (out.best_round, out.best_size, out.best_f) == (ref.best_round, ref.best_size, ref.best_f)
+    for eps in ((0, 1), (1, 5)):
+        o = dupin.peel(dg, "fd", 1, eps)
+        assert verify(og, o, 1, eps) == (0, "")
+    dg.free()
+    og.close()
+
+
+def test_rmat18_exact(dupin):
+    g = synth.rmat_weighted(18, 16, "dw", seed=2)
+    dg = dupin.Graph.from_synth(g)
+    og = oracle.Graph.from_synth(g, "dw")
+    for k in (1, 2):
+        out = dupin.peel(dg, "dw", k, (1, 10))
+        ref = oracle.peel_batch(og, k, (1, 10))
+        assert np.array_equal(out.peel_round, ref.peel_round)
+        assert out.trace_f == ref.trace_f
+        assert (out.best_round, out.best_size, out.best_f) == (ref.best_round, ref.best_size, ref.best_f)
+    dg.free()
+    og.close()
+
+
+@pytest.mark.parametrize("scale", [22, 24])
+def test_rmat_large_verified(dupin, scale):
+    g = synth.rmat_weighted(scale, 16, "dw", seed=1)
+    dg = dupin.Graph.from_synth(g)
+    og = oracle.Graph.from_synth(g, "dw")
+    for k in ((1, 2) if scale == 22 else (1,)):
+        out = dupin.peel(dg, "dw", k, (1, 10))
+        assert verify(og, out, k, (1, 10), nsample=2 if scale == 24 else 3) == (0, "")
+        assert out.trace_size[-1] == 0 and out.trace_f[-1] == 0
+    dg.free()
+    og.close()
