@@ -103,8 +103,8 @@ typedef struct {
  * Copy a graph to the current CUDA device as one symmetric adjacency
  * (int64 row offsets, int32 neighbour ids, int64 Q32.32 arc weights) and
  * validate it (offsets monotone, ids in range, weights >= 0, every initial
- * peeling weight a_u + sum_v c_uv < 2^63).  On success *out owns the device
- * copy until dupin_graph_free.  Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
+ * peeling weight a_u + sum_v c_uv < 2^63, fewer than 2^40 arcs).  On
+ * success *out owns the device copy until dupin_graph_free.  Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
  * Synchronises 'stream'.
  */
 int dupin_graph_load(const dupin_graph_desc *desc, void *stream, dupin_graph **out);
@@ -130,6 +130,8 @@ typedef struct {
     int64_t max_rounds; /* <= 0: n + 1 */
     uint32_t flags;
     int32_t tail_cap;   /* <= 0: automatic; else live-set size below which one CTA finishes */
+    int64_t tail_arc_cap; /* <= 0: automatic (2^21); else the one CTA also waits until
+                             the live sub-graph has at most this many arcs (2 |E(S)|) */
 } dupin_params;
 
 /*
@@ -142,7 +144,8 @@ typedef struct {
  * Scalars (always host): n_rounds R, best_round b (S_b = {u : peel_round[u]
  * > b}), |S_b|, f(S_b) as (hi, lo), g(S_b) as a double (value, not Q32.32),
  * how many rounds used the minimum-weight rule, how many rounds ran in the
- * grid-wide kernel (the rest ran in the one-CTA tail), and with DUPIN_TIMING
+ * grid-wide kernel (the rest ran in the one-CTA tail), the tail's arc
+ * count (0 when the grid-wide rounds emptied S), and with DUPIN_TIMING
  * the device time of each phase: [0] initial weights, [1] grid-wide rounds,
  * [2] tail sub-graph build, [3] one-CTA rounds.
  */
@@ -162,6 +165,7 @@ typedef struct {
     double best_density;
     int64_t n_min_rule;
     int64_t n_bulk_rounds;
+    int64_t tail_arcs;  /* arcs of the live sub-graph the one-CTA tail started on */
     float phase_ms[4];
 } dupin_result;
 
@@ -254,6 +258,14 @@ int dupin_last_error(char *buf, size_t cap);
 
 /* Library version as "major.minor.patch". */
 const char *dupin_version(void);
+
+/*
+ * sizeof() of a public struct as this library was compiled, by type name
+ * ("dupin_graph_desc", "dupin_params", "dupin_result", "dupin_serve_config",
+ * "dupin_serve_stats_t"), so that a binding can check its layouts; -1 for an
+ * unknown name or NULL.  Touches no device.
+ */
+int64_t dupin_struct_size(const char *name);
 
 #ifdef __cplusplus
 }

@@ -29,4 +29,15 @@ extern "C" int dupin_last_error(char *buf, size_t cap) {
     return DUPIN_OK;
 }
 
-extern "C" const char *dupin_version(void) { return "0.1.0"; }
+extern "C" const char *dupin_version(void) { return "0.2.0"; }
+
+extern "C" int64_t dupin_struct_size(const char *name) {
+    if (!name) return -1;
+    const std::string n(name);
+    if (n == "dupin_graph_desc") return (int64_t)sizeof(dupin_graph_desc);
+    if (n == "dupin_params") return (int64_t)sizeof(dupin_params);
+    if (n == "dupin_result") return (int64_t)sizeof(dupin_result);
+    if (n == "dupin_serve_config") return (int64_t)sizeof(dupin_serve_config);
+    if (n == "dupin_serve_stats_t") return (int64_t)sizeof(dupin_serve_stats_t);
+    return -1;
+}

@@ -598,8 +598,8 @@ extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *
     std::vector<int64_t> cta, big;
     for (int64_t j = 0; j < count; j++) {
         if (!graphs[j]) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph " + std::to_string((long long)j) + " is NULL");
-        long long a, b, c;
-        int rc = peel_resolve(graphs[j], &params[j], &a, &b, &c);
+        PeelPlan plan;
+        int rc = peel_resolve(graphs[j], &params[j], &plan);
         if (rc) {
             char buf[512];
             dupin_last_error(buf, sizeof(buf));

@@ -21,7 +21,7 @@ typedef unsigned __int128 u128;
 
 // In-kernel waits give up after this many polls (about a second with the
 // back-off below) and report DUPIN_ERR_TIMEOUT instead of hanging.
-#define DUPIN_SPIN_LIMIT (1ll << 22)
+#define DUPIN_SPIN_LIMIT (1ll << 21)
 
 // Peeling phases recorded in PeelCtl::status
 #define ST_RUNNING 0
@@ -48,6 +48,8 @@ struct PeelCtl {
     long long n_min_rule;
     long long scan_volume;
     long long bulk_rounds;
+    long long elive;      // |E(S)|: undirected edges with both ends live
+    long long tail_arcs;  // arcs of the tail sub-graph (0 if the tail did not run)
     unsigned long long init_lo, init_hi;  // sum over u of (w_u + a_u) = 2 f(V)
     long long init_min;
     int init_overflow;
@@ -64,7 +66,8 @@ struct BlockPart {
     long long min_surv;   // minimum survivor weight
     unsigned long long in_lo, in_hi;  // expand: sum of c over arcs inside U
     long long min_dec;    // expand: minimum weight after a decrement
-    long long pad[6];
+    long long rem_cnt;    // expand: 2 per arc from U to S \ U, 1 per arc inside U
+    long long pad[5];
 };
 
 // Hubs: up to DUPIN_HUB_MAX highest-degree vertices (degree >= DUPIN_HUB_MIN_DEG).
@@ -107,7 +110,8 @@ struct PeelArgs {
     int use_min;        // k (1 + eps) < 2: the minimum rule can fire
     int gpo;            // Algorithm 3
     long long max_rounds;
-    long long tail_cap;
+    long long tail_cap;     // the tail takes over once |S| <= tail_cap ...
+    long long tail_arcs;    // ... and 2 |E(S)| <= tail_arcs
     // tail sub-graph
     int *loc;           // global id -> local id (valid for live vertices)
     long long *tdeg;    // tail: full degree prefix [L+1]
@@ -120,6 +124,12 @@ struct PeelArgs {
 };
 
 // ---------------------------------------------------------------- helpers
+
+// Arc counts stay below 2^40 (checked when a graph is loaded), so the even
+// split of an arc or vertex range over at most 2^16 parts has a 64-bit product.
+__host__ __device__ __forceinline__ long long split_at(long long T, long long c, long long G) {
+    return (long long)(((unsigned long long)T * (unsigned long long)c) / (unsigned long long)G);
+}
 
 __host__ __device__ __forceinline__ u128 mk128(unsigned long long lo, unsigned long long hi) {
     return ((u128)hi << 64) | (u128)lo;
@@ -228,35 +238,49 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p) {
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
 
 // Grid-wide barrier for a cooperative launch (every block resident).
-// Sense is a generation counter read before arriving; the last block to
-// arrive resets the count and advances the generation.  Waiting is bounded:
-// after DUPIN_SPIN_LIMIT polls the block records DUPIN_ERR_TIMEOUT and every
-// block leaves at its next barrier.  Returns false when the peel must stop.
-__device__ __forceinline__ bool grid_barrier(PeelCtl *ctl, unsigned nblocks) {
+// ctl->bar_count counts the arrivals since the control block was reset, so
+// barrier number e (e = 1, 2, ... in every block) is complete once it reaches
+// e * nblocks: one release-add to arrive and acquire loads to wait, with no
+// reset step between barriers.  The error flag is read alongside.  Waiting
+// is bounded: after DUPIN_SPIN_LIMIT polls the block records
+// DUPIN_ERR_TIMEOUT and every block leaves at its next barrier.  Returns
+// false when the peel must stop.  'epoch' is the caller's count of barriers
+// passed (used by thread 0 only).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_release_u32(unsigned *p, unsigned x) {
+    unsigned v;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "r"(x) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(PeelCtl *ctl, unsigned nblocks, unsigned &epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned gen = ld_volatile_u32(&ctl->bar_gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        epoch++;
+        const unsigned target = epoch * nblocks;  // wraps consistently with the counter
+        __threadfence();  // the block's writes (ordered by the block barrier) before the arrival
+        unsigned v = atom_add_release_u32(&ctl->bar_count, 1u) + 1u;
+        int err = ld_volatile_i32(&ctl->error);
         int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            long long it = 0;
-            while (ld_volatile_u32(&ctl->bar_gen) == gen) {
-                if (++it > DUPIN_SPIN_LIMIT) {
-                    set_error(ctl, DUPIN_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (it > 64) __nanosleep(it > 4096 ? 256 : 32);
+        long long it = 0;
+        while ((int)(v - target) < 0 && err == 0) {
+            if (++it > DUPIN_SPIN_LIMIT) {
+                set_error(ctl, DUPIN_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            if (it > 256) __nanosleep(it > 8192 ? 256 : 20);
+            v = ld_acquire_u32(&ctl->bar_count);
+            err = ld_volatile_i32(&ctl->error);
         }
         __threadfence();
-        s_ok = ok && ld_volatile_i32(&ctl->error) == 0;
+        s_ok = ok && err == 0;
     }
     __syncthreads();
     return s_ok != 0;
@@ -271,7 +295,7 @@ __device__ __forceinline__ long long warp_search_last_le(const long long *base, 
         long long span = hi - lo;  // candidates lo+1 .. hi
         long long p;
         if (span <= 32) p = lo + 1 + lane;
-        else p = lo + 1 + (long long)(((u128)(span - 1) * (unsigned)lane) / 31u);
+        else p = lo + 1 + (long long)(((unsigned long long)(span - 1) * (unsigned)lane) / 31u);
         bool valid = p <= hi;
         bool le = valid && base[p] <= x;
         unsigned m = __ballot_sync(0xffffffffu, le);

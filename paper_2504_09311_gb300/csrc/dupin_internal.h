@@ -61,19 +61,24 @@ struct dupin_graph {
     PeelWorkspace *ws = nullptr;
 };
 
+// The caps of one peel, resolved from its params and the graph: the tail
+// takes over once |S| <= tail_cap and 2 |E(S)| <= tail_arcs.
+struct PeelPlan {
+    long long tail_cap = 0, tail_arcs = 0, max_rounds = 0, tr_cap = 0;
+};
+
 DevGraph dev_graph(const dupin_graph *g, int metric);
-long long workspace_bytes(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap, int grid);
-PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap,
-                                bool async, cudaStream_t s, int *rc);
+long long workspace_bytes(long long n, long long arcs, bool has_cw, const PeelPlan &plan, int grid);
+PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const PeelPlan &plan, bool async,
+                                cudaStream_t s, int *rc);
 void workspace_free(PeelWorkspace *ws);
 void workspace_free(PeelWorkspace *ws, cudaStream_t s);
-int workspace_ensure(dupin_graph *g, long long tail_cap, long long tr_cap);
+int workspace_ensure(dupin_graph *g, const PeelPlan &plan);
 
 // the three steps of dupin_peel: caps from params, kernels on a stream, results
-int peel_resolve(const dupin_graph *g, const dupin_params *p, long long *tail_cap, long long *max_rounds,
-                 long long *tr_cap);
-int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, long long tail_cap,
-                 long long max_rounds, cudaStream_t s);
+int peel_resolve(const dupin_graph *g, const dupin_params *p, PeelPlan *plan);
+int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
+                 cudaStream_t s);
 int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, dupin_result *r, cudaStream_t s);
 
 // kernels shared by loading and peeling
@@ -95,7 +100,8 @@ void launch_mask(const int *pr, long long n, long long best_round, uint8_t *mask
 // a whole peel of a small graph with caller-supplied buffers (no allocation)
 int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStream_t s);
 
-// the largest live set the single-CTA tail accepts, and the default cap
+// the largest live set the single-CTA tail accepts, and the default caps
 long long tail_cap_limit();
 long long tail_cap_default();
+#define DUPIN_TAIL_ARCS_DEFAULT (1LL << 21)
 int peel_grid_size();

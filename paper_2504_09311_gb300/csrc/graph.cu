@@ -182,6 +182,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
     const long long n = nL + nR;
     const long long arcs = bip ? 2 * m_csr : m_csr;
     if (!bip && (arcs & 1)) return dupin_fail(DUPIN_ERR_INVALID_ARG, "a symmetric CSR has an even number of arcs");
+    if (arcs >= (1LL << 40)) return dupin_fail(DUPIN_ERR_INVALID_ARG, "a graph holds fewer than 2^40 arcs");
 
     dupin_graph *g = new dupin_graph();
     cudaGetDevice(&g->device);

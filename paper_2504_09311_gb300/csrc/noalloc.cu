@@ -169,6 +169,7 @@ extern "C" int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32
     A.gpo = (p.flags & DUPIN_GPO) ? 1 : 0;
     A.max_rounds = p.max_rounds > 0 ? p.max_rounds : n + 1;
     A.tail_cap = DUPIN_NOALLOC_MAX_N;
+    A.tail_arcs = arcs;
     // the graph itself is the one-CTA kernel's sub-graph (local ids = ids)
     A.tlrp = (long long *)rp;
     A.tcol = (int *)col;
@@ -182,6 +183,7 @@ extern "C" int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32
     result->n_rounds = c.round;
     result->n_min_rule = c.n_min_rule;
     result->n_bulk_rounds = 0;
+    result->tail_arcs = arcs;
     for (int j = 0; j < 4; j++) result->phase_ms[j] = 0.f;
     if (c.error) {
         return dupin_fail(c.error, c.error == DUPIN_ERR_NO_PROGRESS ? "max_rounds reached before the set became empty"

@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
     const long long NW = (long long)gridDim.x * INIT_WARPS;
     const long long W = blockIdx.x * (long long)INIT_WARPS + (threadIdx.x >> 5);
     const long long A = g.arcs, n = g.n;
-    const long long we0 = (long long)(((u128)A * (unsigned long long)W) / (unsigned long long)NW);
-    const long long we1 = (long long)(((u128)A * (unsigned long long)(W + 1)) / (unsigned long long)NW);
+    const long long we0 = split_at(A, W, NW);
+    const long long we1 = split_at(A, W + 1, NW);
     if (we0 >= we1) return;
     long long r = warp_search_last_le(g.rp, n, we0);  // row of the first arc
     long long carry_own = -1, carry_val = 0;
@@ -283,8 +283,10 @@ __global__ void k_init_finish(PeelArgs A, long long n) {
     c->scan_volume = 0;
     c->bar_count = 0;
     c->bar_gen = 0;
+    c->elive = A.g.arcs / 2;
+    c->tail_arcs = 0;
     if (c->init_overflow) c->error = DUPIN_ERR_OVERFLOW;
-    c->status = n == 0 ? ST_DONE : (n <= A.tail_cap ? ST_TAIL : ST_RUNNING);
+    c->status = n == 0 ? ST_DONE : (n <= A.tail_cap && A.g.arcs <= A.tail_arcs ? ST_TAIL : ST_RUNNING);
     if (A.tr_cap > 0) {
         A.tr_f_hi[0] = (long long)c->f_hi;
         A.tr_f_lo[0] = c->f_lo;
@@ -305,6 +307,16 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
     __shared__ long long s_start[WALK_WIN + 1];
     __shared__ int s_hub[DUPIN_HUB_MAX];
     __shared__ unsigned long long s_hacc[DUPIN_HUB_MAX];
+    // The state after the last completed round lives in shared memory, not in
+    // registers: thread 0 updates it at the end of a round (phase D) and a
+    // block barrier publishes it.  s_rd carries phase B's totals to phase D.
+    __shared__ RoundState s_st;
+    __shared__ long long s_elive;  // |E(S)|
+    __shared__ struct {
+        unsigned long long wlo, whi;  // sum of the selected vertices' weights
+        long long U_sel, newSize;
+        int minrule, compact;
+    } s_rd;
 
     const unsigned G = gridDim.x;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -316,47 +328,57 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         s_hub[h] = g.hubs[h];
         s_hacc[h] = 0;
     }
+    unsigned epoch = 0;  // grid barriers passed
+    if (tid == 0) {
+        RoundState &st = s_st;
+        st.round = ctl->round;
+        st.size = ctl->size;
+        st.f = mk128(ctl->f_lo, ctl->f_hi);
+        st.live_len = ctl->live_len;
+        st.live_sel = ctl->live_sel;
+        st.minw = ctl->minw;
+        st.best_round = ctl->best_round;
+        st.best_size = ctl->best_size;
+        st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
+        st.gpo_le = ctl->gpo_le;
+        st.n_min_rule = ctl->n_min_rule;
+        st.scan = ctl->scan_volume;
+        s_elive = ctl->elive;
+    }
     __syncthreads();
-
-    RoundState st;
-    st.round = ctl->round;
-    st.size = ctl->size;
-    st.f = mk128(ctl->f_lo, ctl->f_hi);
-    st.live_len = ctl->live_len;
-    st.live_sel = ctl->live_sel;
-    st.minw = ctl->minw;
-    st.best_round = ctl->best_round;
-    st.best_size = ctl->best_size;
-    st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
-    st.gpo_le = ctl->gpo_le;
-    st.n_min_rule = ctl->n_min_rule;
-    st.scan = ctl->scan_volume;
     if (ctl->status != ST_RUNNING || ctl->error) return;
 
     for (;;) {
-        if (st.size == 0 || st.size <= A.tail_cap) break;
-        if (st.round >= A.max_rounds) {
+        const long long size = s_st.size;
+        if (size == 0 || (size <= A.tail_cap && 2 * s_elive <= A.tail_arcs)) break;
+        if (s_st.round >= A.max_rounds) {
             if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
             break;
         }
-        const long long i = st.round + 1;
-        long long T = floor_ratio((unsigned long long)A.kD, st.f, (unsigned long long)A.D, st.size);
-        if (A.gpo) {
-            long long le = floor_ratio((unsigned long long)A.D, st.f, (unsigned long long)A.kD, st.size);
-            st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
-            T = st.gpo_le > T ? st.gpo_le : T;
+        const long long i = s_st.round + 1;
+        long long T;
+        {
+            const u128 f = s_st.f;
+            T = floor_ratio((unsigned long long)A.kD, f, (unsigned long long)A.D, size);
+            if (A.gpo) {
+                const long long le = floor_ratio((unsigned long long)A.D, f, (unsigned long long)A.kD, size);
+                const long long gl = le > s_st.gpo_le ? le : s_st.gpo_le;
+                T = gl > T ? gl : T;
+                __syncthreads();  // every thread has read s_st.gpo_le
+                if (tid == 0) s_st.gpo_le = gl;
+            }
         }
-        int *live = st.live_sel ? A.live1 : A.live0;
-        int *nlive = st.live_sel ? A.live0 : A.live1;
-        const long long L = st.live_len;
-        const long long j0 = (long long)(((u128)L * b) / G), j1 = (long long)(((u128)L * (b + 1)) / G);
+        const int live_sel = s_st.live_sel;
+        int *live = live_sel ? A.live1 : A.live0;
+        int *nlive = live_sel ? A.live0 : A.live1;
+        const long long L = s_st.live_len;
+        const long long j0 = split_at(L, b, G), j1 = split_at(L, b + 1, G);
         // Phase A selects w <= T.  If no block selected anything (possible only
         // when k(1+eps) < 2), the round takes the minimum rule: phase A runs a
         // second time with the minimum live weight, which the first pass found.
         long long thr = T;
         bool minrule = false;
         long long U_sel = 0, U_stage = 0, totArcs = 0, slotBase = 0, arcBase = 0, survBase = 0;
-        unsigned long long Wlo = 0, Whi = 0;
         for (int pass = 0;; pass++) {
             // ---------------- phase A: select
             if (tid == 0) s_pack = 0;
@@ -415,7 +437,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                     p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
                 }
             }
-            if (!grid_barrier(ctl, G)) return;
+            if (!grid_barrier(ctl, G, epoch)) return;
             // ---------------- phase B (part 1): totals and this block's offsets
             long long minSurvAll;
             {
@@ -440,13 +462,17 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
                 U_sel = r.v[0]; U_stage = r.v[1]; totArcs = r.v[2];
                 survBase = r.v[3]; slotBase = r.v[4]; arcBase = r.v[5];
-                Wlo = r.lo; Whi = r.hi; minSurvAll = r.mn;
+                minSurvAll = r.mn;
+                if (tid == 0) {
+                    s_rd.wlo = r.lo;
+                    s_rd.whi = r.hi;
+                }
             }
             if (U_sel > 0 || pass > 0 || !A.use_min || minSurvAll == kMaxLL) break;
             thr = minSurvAll;  // every live vertex survived the threshold: minimum rule
             minrule = true;
             // every block has read the partials before the second pass rewrites them
-            if (!grid_barrier(ctl, G)) return;
+            if (!grid_barrier(ctl, G, epoch)) return;
         }
         if (U_sel == 0) {  // cannot happen (Lemma 4.2 / minimum rule): stop rather than spin
             if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
@@ -457,8 +483,31 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
             myStage = A.part[b].stage_cnt;
             myDeg = A.part[b].sel_deg;
         }
-        const long long newSize = st.size - U_sel;
+        const long long newSize = size - U_sel;
         const bool compact = newSize > 0 && (2 * newSize <= L || newSize <= A.tail_cap);
+        if (tid == 0) {
+            s_rd.U_sel = U_sel;
+            s_rd.newSize = newSize;
+            s_rd.minrule = minrule ? 1 : 0;
+            s_rd.compact = compact ? 1 : 0;
+        }
+        // Consumer block c expands the arcs [split_at(totArcs, c, G), split_at(totArcs, c + 1, G))
+        // and starts its walk at the frontier entry holding its first arc.  The
+        // consumers whose first arc lies in this block's entries, global arcs
+        // [arcBase, arcBase + myDeg), are c_lo .. c_lo + nc - 1; their first
+        // arcs go to shared memory (s_base is free until phase C), and every
+        // entry finds its consumers there by binary search.
+        long long *s_cs = s_base;
+        long long c_lo = 0, nc = 0;
+        if (myDeg > 0) {
+            const unsigned long long T = (unsigned long long)totArcs;
+            c_lo = (long long)(((unsigned long long)arcBase * G + T - 1) / T);
+            long long c_hi = (long long)(((unsigned long long)(arcBase + myDeg) * G + T - 1) / T);
+            if (c_hi > (long long)G) c_hi = G;
+            nc = c_hi - c_lo;
+        }
+        for (long long t = tid; t < nc; t += BULK_THREADS) s_cs[t] = split_at(totArcs, c_lo + t, G);
+        __syncthreads();
         for (long long q = tid; q < myStage; q += BULK_THREADS) {
             const long long gs = slotBase + q;
             const long long off = A.stage_off[j0 + q];
@@ -467,13 +516,13 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
             A.fbase[gs] = goff;
             const long long nxt = (q + 1 < myStage) ? A.stage_off[j0 + q + 1] : myDeg;
             const long long gend = arcBase + nxt;
-            // consumer blocks whose share starts inside [goff, gend)
-            long long c = (long long)(((u128)goff * G + (unsigned long long)totArcs - 1) / (unsigned long long)totArcs);
-            for (; c < (long long)G; c++) {
-                long long e0c = (long long)(((u128)totArcs * (unsigned long long)c) / G);
-                if (e0c >= gend) break;
-                A.cstart[c] = gs;
+            int lo = 0, hi = (int)nc;  // first consumer whose first arc is >= goff
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cs[mid] < goff) lo = mid + 1;
+                else hi = mid;
             }
+            for (int t = lo; t < (int)nc && s_cs[t] < gend; t++) A.cstart[c_lo + t] = gs;
         }
         if (b == 0 && tid == 0) A.fbase[U_stage] = totArcs;
         if (compact) {
@@ -492,14 +541,15 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 }
             }
         }
-        if (!grid_barrier(ctl, G)) return;
+        if (!grid_barrier(ctl, G, epoch)) return;
 
         // ---------------- phase C: expand
         long long mindec = kMaxLL;
         unsigned long long ilo = 0, ihi = 0;
+        long long nrem = 0;  // 2 per arc from U to S \ U, 1 per arc inside U
         if (totArcs > 0) {
-            const long long E0 = (long long)(((u128)totArcs * (unsigned long long)b) / G);
-            const long long E1 = (long long)(((u128)totArcs * (unsigned long long)(b + 1)) / G);
+            const long long E0 = split_at(totArcs, b, G);
+            const long long E1 = split_at(totArcs, b + 1, G);
             if (E0 < E1) {
                 const long long k0 = A.cstart[b];
                 const long long *fb = A.fbase;
@@ -519,14 +569,21 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                                   if (p > (int)i) {
                                       // result unused: a fire-and-forget reduction
                                       atomicAdd((unsigned long long *)&w[cv], (unsigned long long)(-c));
+                                      nrem += 2;
                                   } else if (p == (int)i) {
                                       add128(ilo, ihi, (unsigned long long)c, 0);
+                                      nrem++;
                                   }
                               } else {  // hub head: aggregate in shared memory
                                   const int h = -cv - 1;
                                   const int p = pr[s_hub[h]];
-                                  if (p > (int)i) atomicAdd(&s_hacc[h], (unsigned long long)c);
-                                  else if (p == (int)i) add128(ilo, ihi, (unsigned long long)c, 0);
+                                  if (p > (int)i) {
+                                      atomicAdd(&s_hacc[h], (unsigned long long)c);
+                                      nrem += 2;
+                                  } else if (p == (int)i) {
+                                      add128(ilo, ihi, (unsigned long long)c, 0);
+                                      nrem++;
+                                  }
                               }
                           });
             }
@@ -544,15 +601,17 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         {
             BlockRed<BULK_WARPS, 6> r;
             for (int j = 0; j < 6; j++) r.v[j] = 0;
+            r.v[0] = nrem;
             r.lo = ilo; r.hi = ihi; r.mn = mindec;
             block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
             if (tid == 0) {
                 A.part[b].in_lo = r.lo;
                 A.part[b].in_hi = r.hi;
                 A.part[b].min_dec = r.mn;
+                A.part[b].rem_cnt = r.v[0];
             }
         }
-        if (!grid_barrier(ctl, G)) return;
+        if (!grid_barrier(ctl, G, epoch)) return;
 
         // ---------------- phase D: close the round (every block)
         {
@@ -562,35 +621,42 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
             for (int t = tid; t < (int)G; t += BULK_THREADS) {
                 add128(r.lo, r.hi, A.part[t].in_lo, A.part[t].in_hi);
                 r.mn = A.part[t].min_dec < r.mn ? A.part[t].min_dec : r.mn;
+                r.v[0] += A.part[t].rem_cnt;
             }
             block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
-            const u128 internal = mk128(r.lo, r.hi);
-            const u128 wsel = mk128(Wlo, Whi);
-            st.f = st.f - (wsel - (internal >> 1));
-            st.scan += L;
-            st.size = newSize;
-            st.round = i;
-            st.n_min_rule += minrule ? 1 : 0;
-            if (compact) {
-                st.live_sel ^= 1;
-                st.live_len = newSize;
-            }
-            if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
-                st.bf = st.f;
-                st.best_size = st.size;
-                st.best_round = i;
-            }
-            if (b == 0 && tid == 0) {
-                if (i < A.tr_cap) {
+            if (tid == 0) {
+                RoundState &st = s_st;
+                // an edge leaves E(S) with its first removed end: counted 2 on
+                // its one arc from U to S \ U, 1 on each of its two arcs inside U
+                s_elive -= r.v[0] / 2;
+                const u128 internal = mk128(r.lo, r.hi);
+                const u128 wsel = mk128(s_rd.wlo, s_rd.whi);
+                st.f = st.f - (wsel - (internal >> 1));
+                st.scan += L;
+                st.size = s_rd.newSize;
+                st.round = i;
+                st.n_min_rule += s_rd.minrule;
+                if (s_rd.compact) {
+                    st.live_sel ^= 1;
+                    st.live_len = s_rd.newSize;
+                }
+                if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
+                    st.bf = st.f;
+                    st.best_size = st.size;
+                    st.best_round = i;
+                }
+                if (b == 0 && i < A.tr_cap) {
                     A.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
                     A.tr_f_lo[i] = (unsigned long long)st.f;
                     A.tr_size[i] = st.size;
-                    A.tr_peeled[i] = U_sel;
+                    A.tr_peeled[i] = s_rd.U_sel;
                 }
             }
+            __syncthreads();
         }
     }
     if (b == 0 && tid == 0) {
+        const RoundState &st = s_st;
         ctl->round = st.round;
         ctl->size = st.size;
         ctl->f_lo = (unsigned long long)st.f;
@@ -606,6 +672,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         ctl->n_min_rule = st.n_min_rule;
         ctl->scan_volume = st.scan;
         ctl->bulk_rounds = st.round;
+        ctl->elive = s_elive;
         if (ctl->error == 0) ctl->status = st.size == 0 ? ST_DONE : ST_TAIL;
     }
 }
@@ -642,7 +709,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tail_scan(PeelArgs A, long lon
     }
     if (threadIdx.x == 0) {
         x[L] = carry;
-        if (cnt && carry > A.tarc_cap) set_error(A.ctl, DUPIN_ERR_OOM);
+        if (cnt) {
+            A.ctl->tail_arcs = carry;
+            if (carry > A.tarc_cap) set_error(A.ctl, DUPIN_ERR_OOM);
+        }
     }
 }
 
@@ -658,8 +728,8 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
     const int *live = c->live_sel ? A.live1 : A.live0;
     const long long tot = A.tdeg[L];
     const unsigned G = gridDim.x;
-    const long long e0 = (long long)(((u128)tot * blockIdx.x) / G);
-    const long long e1 = (long long)(((u128)tot * (blockIdx.x + 1)) / G);
+    const long long e0 = split_at(tot, blockIdx.x, G);
+    const long long e1 = split_at(tot, blockIdx.x + 1, G);
     if (e0 >= e1) return;
     const long long *tdeg = A.tdeg;
     const long long *rp = A.g.rp;
@@ -827,9 +897,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         // ---- expand
         unsigned long long ilo = 0, ihi = 0;
         long long mind = kMaxLL;
-        auto arc = [&](long long pos) {
-            const int v = tcol[pos];
-            const long long c = dg ? DUPIN_Q_ONE : tcw[pos];
+        auto apply = [&](int v, long long c) {
             const long long wv = tw[v];
             if (wv >= 0) {
                 const long long old = (long long)atomicAdd((unsigned long long *)&tw[v], (unsigned long long)(-c));
@@ -839,22 +907,49 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                 add128(ilo, ihi, (unsigned long long)c, 0);
             }
         };
+        // TAIL_ILP arcs per thread at a time: their loads from L2 are issued
+        // together before any of them is applied
+        auto arcs = [&](const long long (&pos)[TAIL_ILP]) {
+            int cv[TAIL_ILP];
+            long long cc[TAIL_ILP];
+#pragma unroll
+            for (int u = 0; u < TAIL_ILP; u++) {
+                if (pos[u] >= 0) {
+                    cv[u] = tcol[pos[u]];
+                    cc[u] = dg ? DUPIN_Q_ONE : tcw[pos[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TAIL_ILP; u++)
+                if (pos[u] >= 0) apply(cv[u], cc[u]);
+        };
         if (F <= TAIL_FAST) {
             // every thread walks the concatenation of the F arc ranges
             // (offsets in shared memory), advancing a running offset
             int q = 0, qp = F > 0 ? tf[0] : 0;
             long long qs = 0, ql = F > 0 ? toff[qp + 1] - toff[qp] : 0;
-            for (long long x = tid;; x += TAIL_THREADS) {
-                while (q < F && x >= qs + ql) {
-                    qs += ql;
-                    q++;
+            for (long long x0 = tid;; x0 += TAIL_ILP * TAIL_THREADS) {
+                long long pos[TAIL_ILP];
+                int got = 0;
+#pragma unroll
+                for (int u = 0; u < TAIL_ILP; u++) {
+                    const long long x = x0 + (long long)u * TAIL_THREADS;
+                    while (q < F && x >= qs + ql) {
+                        qs += ql;
+                        q++;
+                        if (q < F) {
+                            qp = tf[q];
+                            ql = toff[qp + 1] - toff[qp];
+                        }
+                    }
+                    pos[u] = -1;
                     if (q < F) {
-                        qp = tf[q];
-                        ql = toff[qp + 1] - toff[qp];
+                        pos[u] = toff[qp] + (x - qs);
+                        got++;
                     }
                 }
-                if (q >= F) break;
-                arc(toff[qp] + (x - qs));
+                arcs(pos);
+                if (got < TAIL_ILP) break;
             }
         } else {
             for (int c0 = 0; c0 < F; c0 += TAIL_THREADS) {
@@ -870,10 +965,19 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                 const int nq = (F - c0) < TAIL_THREADS ? (F - c0) : TAIL_THREADS;
                 if (tid == 0) s_pref[nq] = tot;
                 __syncthreads();
-                for (long long x = tid; x < tot; x += TAIL_THREADS) {
-                    const int e = smem_last_le(s_pref, nq, x);
-                    const int p = tf[c0 + e];
-                    arc(toff[p] + (x - s_pref[e]));
+                for (long long x0 = tid; x0 < tot; x0 += TAIL_ILP * TAIL_THREADS) {
+                    long long pos[TAIL_ILP];
+#pragma unroll
+                    for (int u = 0; u < TAIL_ILP; u++) {
+                        const long long x = x0 + (long long)u * TAIL_THREADS;
+                        pos[u] = -1;
+                        if (x < tot) {
+                            const int e = smem_last_le(s_pref, nq, x);
+                            const int p = tf[c0 + e];
+                            pos[u] = toff[p] + (x - s_pref[e]);
+                        }
+                    }
+                    arcs(pos);
                 }
                 __syncthreads();
             }
@@ -975,7 +1079,8 @@ int peel_grid_size() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel_bulk, BULK_THREADS, 0);
     if (occ < 1) occ = 1;
     if (occ > 2) occ = 2;
-    return sms * occ;
+    // the consumer starts of one round are staged in s_base (WALK_WIN + 1 entries)
+    return std::min(sms * occ, WALK_WIN);
 }
 
 static int set_tail_smem() {
@@ -1025,8 +1130,16 @@ DevGraph dev_graph(const dupin_graph *g, int metric) {
     return d;
 }
 
-long long workspace_bytes(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap, int grid) {
-    const long long tarc = std::min<long long>(arcs, tail_cap * (tail_cap > 0 ? tail_cap - 1 : 0));
+// arcs the tail buffer must hold: the live sub-graph has at most
+// min(all arcs, |S| (|S| - 1), the plan's arc cap)
+static long long tail_arc_buffer(long long arcs, const PeelPlan &plan) {
+    const long long tc = plan.tail_cap;
+    return std::min<long long>(std::min<long long>(arcs, tc * (tc > 0 ? tc - 1 : 0)), plan.tail_arcs);
+}
+
+long long workspace_bytes(long long n, long long arcs, bool has_cw, const PeelPlan &plan, int grid) {
+    const long long tail_cap = plan.tail_cap, tr_cap = plan.tr_cap;
+    const long long tarc = tail_arc_buffer(arcs, plan);
     long long b = 0;
     b += n * (8 + 4 + 4 + 4 + 4 + 8 + 8 + 8 + 4 + 1) + 8 * (n + 1);
     b += 8 * (grid + 1) + (long long)sizeof(BlockPart) * grid + (long long)sizeof(PeelCtl);
@@ -1054,14 +1167,15 @@ void workspace_free(PeelWorkspace *ws, cudaStream_t s) {
 
 void workspace_free(PeelWorkspace *ws) { workspace_free(ws, 0); }
 
-PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, long long tail_cap, long long tr_cap,
-                                bool async, cudaStream_t s, int *rc) {
+PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const PeelPlan &plan, bool async,
+                                cudaStream_t s, int *rc) {
+    const long long tail_cap = plan.tail_cap, tr_cap = plan.tr_cap;
     PeelWorkspace *ws = new PeelWorkspace();
     ws->n = n;
     ws->arcs = arcs;
     ws->tail_cap = tail_cap;
     ws->tr_cap = tr_cap;
-    ws->tarc_cap = std::min<long long>(arcs, tail_cap * (tail_cap > 0 ? tail_cap - 1 : 0));
+    ws->tarc_cap = tail_arc_buffer(arcs, plan);
     ws->grid = peel_grid_size();
     ws->async = async;
     cudaError_t e = cudaSuccess;
@@ -1106,22 +1220,25 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, long l
     return ws;
 }
 
-int workspace_ensure(dupin_graph *g, long long tail_cap, long long tr_cap) {
+int workspace_ensure(dupin_graph *g, const PeelPlan &plan) {
     PeelWorkspace *ws = g->ws;
-    if (ws && ws->tail_cap >= tail_cap && ws->tr_cap >= tr_cap) return DUPIN_OK;
-    if (ws) {
-        tail_cap = std::max(tail_cap, ws->tail_cap);
-        tr_cap = std::max(tr_cap, ws->tr_cap);
+    const long long tarc = tail_arc_buffer(g->arcs, plan);
+    if (ws && ws->tail_cap >= plan.tail_cap && ws->tr_cap >= plan.tr_cap && ws->tarc_cap >= tarc) return DUPIN_OK;
+    PeelPlan big = plan;
+    if (ws) {  // grow to cover both the old and the new caps
+        big.tail_cap = std::max(plan.tail_cap, ws->tail_cap);
+        big.tr_cap = std::max(plan.tr_cap, ws->tr_cap);
+        big.tail_arcs = std::max(tarc, ws->tarc_cap);
         workspace_free(ws);
         g->ws = nullptr;
     }
     int rc;
-    g->ws = workspace_create(g->n, g->arcs, g->cw != nullptr, tail_cap, tr_cap, false, 0, &rc);
+    g->ws = workspace_create(g->n, g->arcs, g->cw != nullptr, big, false, 0, &rc);
     return rc;
 }
 
-static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const dupin_params *p, long long tail_cap,
-                          long long max_rounds) {
+static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const dupin_params *p,
+                          const PeelPlan &plan) {
     PeelArgs A;
     A.g = dev_graph(g, p->metric);
     A.w = ws->w;
@@ -1145,8 +1262,9 @@ static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const d
     A.D = p->eps_den;
     A.use_min = A.kD < 2 * A.D ? 1 : 0;
     A.gpo = (p->flags & DUPIN_GPO) ? 1 : 0;
-    A.max_rounds = max_rounds;
-    A.tail_cap = tail_cap;
+    A.max_rounds = plan.max_rounds;
+    A.tail_cap = plan.tail_cap;
+    A.tail_arcs = std::min<long long>(plan.tail_arcs, ws->tarc_cap);
     A.loc = ws->loc;
     A.tdeg = ws->tdeg;
     A.tlrp = ws->tlrp;
@@ -1166,9 +1284,10 @@ __global__ void k_ctl_reset(PeelCtl *c) {
     *c = z;
 }
 
-int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, long long tail_cap,
-                 long long max_rounds, cudaStream_t s) {
-    PeelArgs A = make_args(g, ws, p, tail_cap, max_rounds);
+int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
+                 cudaStream_t s) {
+    PeelArgs A = make_args(g, ws, p, plan);
+    const long long tail_cap = plan.tail_cap;
     const bool timing = (p->flags & DUPIN_TIMING) != 0;
     if (timing && !ws->ev[0]) {
         for (int j = 0; j < 5; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
@@ -1179,7 +1298,7 @@ int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p,
     if (rc) return rc;
     k_init_finish<<<1, 1, 0, s>>>(A, g->n);
     if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[1], s));
-    if (g->n > tail_cap) {
+    if (g->n > tail_cap || g->arcs > A.tail_arcs) {
         void *args[] = {&A};
         cudaError_t e = cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(ws->grid), dim3(BULK_THREADS), args, 0, s);
         if (e != cudaSuccess) return dupin_cuda_fail(e, "cooperative launch of k_peel_bulk");
@@ -1207,14 +1326,14 @@ int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p,
     return DUPIN_OK;
 }
 
-int peel_resolve(const dupin_graph *g, const dupin_params *p, long long *tail_cap, long long *max_rounds,
-                 long long *tr_cap) {
+int peel_resolve(const dupin_graph *g, const dupin_params *p, PeelPlan *plan) {
     int rc = check_params(g, p);
     if (rc) return rc;
     long long lim = tail_cap_limit();
-    *tail_cap = p->tail_cap > 0 ? std::min<long long>(p->tail_cap, lim) : tail_cap_default();
-    *max_rounds = p->max_rounds > 0 ? p->max_rounds : g->n + 1;
-    *tr_cap = std::min<long long>(*max_rounds, g->n) + 1;
+    plan->tail_cap = p->tail_cap > 0 ? std::min<long long>(p->tail_cap, lim) : tail_cap_default();
+    plan->tail_arcs = p->tail_arc_cap > 0 ? p->tail_arc_cap : DUPIN_TAIL_ARCS_DEFAULT;
+    plan->max_rounds = p->max_rounds > 0 ? p->max_rounds : g->n + 1;
+    plan->tr_cap = std::min<long long>(plan->max_rounds, g->n) + 1;
     return DUPIN_OK;
 }
 
@@ -1225,6 +1344,7 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
     r->n_rounds = c.round;
     r->n_min_rule = c.n_min_rule;
     r->n_bulk_rounds = c.bulk_rounds;
+    r->tail_arcs = c.tail_arcs;
     for (int j = 0; j < 4; j++) r->phase_ms[j] = 0.f;
     if ((p->flags & DUPIN_TIMING) && ws->ev[0]) {
         for (int j = 0; j < 4; j++) cudaEventElapsedTime(&r->phase_ms[j], ws->ev[j], ws->ev[j + 1]);
@@ -1296,14 +1416,14 @@ int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStrea
 extern "C" int dupin_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, void *stream) {
     if (!g) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph is NULL");
     if (!r) return dupin_fail(DUPIN_ERR_INVALID_ARG, "result is NULL");
-    long long tail_cap, max_rounds, tr_cap;
-    int rc = peel_resolve(g, p, &tail_cap, &max_rounds, &tr_cap);
+    PeelPlan plan;
+    int rc = peel_resolve(g, p, &plan);
     if (rc) return rc;
     DUPIN_CUDA_TRY(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
-    rc = workspace_ensure(g, tail_cap, tr_cap);
+    rc = workspace_ensure(g, plan);
     if (rc) return rc;
-    rc = enqueue_peel(g, g->ws, p, tail_cap, max_rounds, s);
+    rc = enqueue_peel(g, g->ws, p, plan, s);
     if (rc) return rc;
     return peel_finish(g, g->ws, p, r, s);
 }

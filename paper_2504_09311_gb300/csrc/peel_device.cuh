@@ -177,6 +177,7 @@ __device__ __forceinline__ void acc_add128(unsigned long long *lo, unsigned long
 
 #define TAIL_FAST 32
 #define TAIL_SEG 64  // vertices per segment (one warp, two per lane)
+#define TAIL_ILP 4   // arcs in flight per thread in the tail's expand
 
 // can segment minimum sm hold a vertex that round R selects?
 __device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) {

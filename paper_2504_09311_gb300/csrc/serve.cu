@@ -38,7 +38,8 @@ struct Request {
     dupin_graph *g = nullptr;
     dupin_params p{};
     dupin_result *r = nullptr;
-    long long tail_cap = 0, max_rounds = 0, tr_cap = 0, bytes = 0;
+    PeelPlan plan;
+    long long bytes = 0;
     bool large = false;
     double t_submit = 0, t_done = 0;
     int status = DUPIN_OK;
@@ -134,8 +135,8 @@ static bool admit(dupin_server *s, std::unique_lock<std::mutex> &lk) {
         int rc = DUPIN_OK;
         if (sl.large) {
             Request *q = sl.reqs[0];
-            sl.ws = workspace_create(q->g->n, q->g->arcs, q->g->cw != nullptr, q->tail_cap, q->tr_cap, true, st, &rc);
-            if (rc == DUPIN_OK) rc = enqueue_peel(q->g, sl.ws, &q->p, q->tail_cap, q->max_rounds, st);
+            sl.ws = workspace_create(q->g->n, q->g->arcs, q->g->cw != nullptr, q->plan, true, st, &rc);
+            if (rc == DUPIN_OK) rc = enqueue_peel(q->g, sl.ws, &q->p, q->plan, st);
         } else {
             const size_t k = sl.reqs.size();
             sl.gs.resize(k);
@@ -269,7 +270,7 @@ extern "C" int dupin_serve_submit(dupin_server *s, dupin_graph *g, const dupin_p
     q->g = g;
     q->p = *p;
     q->r = r;
-    int rc = peel_resolve(g, p, &q->tail_cap, &q->max_rounds, &q->tr_cap);
+    int rc = peel_resolve(g, p, &q->plan);
     if (rc) {
         delete q;
         return rc;
@@ -279,7 +280,7 @@ extern "C" int dupin_serve_submit(dupin_server *s, dupin_graph *g, const dupin_p
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "serving writes host results; DUPIN_RESULT_DEVICE is not accepted");
     }
     q->large = g->n < 1 || g->n > cta_graph_limit();
-    q->bytes = q->large ? workspace_bytes(g->n, g->arcs, g->cw != nullptr, q->tail_cap, q->tr_cap, peel_grid_size())
+    q->bytes = q->large ? workspace_bytes(g->n, g->arcs, g->cw != nullptr, q->plan, peel_grid_size())
                         : cta_job_bytes(g, p);
     q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s->mu);

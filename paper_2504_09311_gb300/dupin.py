@@ -45,7 +45,7 @@ class GraphDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("metric", ctypes.c_int32), ("k_mult", ctypes.c_int32), ("eps_num", ctypes.c_int64),
                 ("eps_den", ctypes.c_int64), ("max_rounds", ctypes.c_int64), ("flags", ctypes.c_uint32),
-                ("tail_cap", ctypes.c_int32)]
+                ("tail_cap", ctypes.c_int32), ("tail_arc_cap", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):
@@ -54,7 +54,7 @@ class Result(ctypes.Structure):
                 ("trace_peeled", ctypes.c_void_p), ("trace_cap", ctypes.c_int64), ("n_rounds", ctypes.c_int64),
                 ("best_round", ctypes.c_int64), ("best_size", ctypes.c_int64), ("best_f_hi", ctypes.c_int64),
                 ("best_f_lo", ctypes.c_uint64), ("best_density", ctypes.c_double), ("n_min_rule", ctypes.c_int64),
-                ("n_bulk_rounds", ctypes.c_int64), ("phase_ms", ctypes.c_float * 4)]
+                ("n_bulk_rounds", ctypes.c_int64), ("tail_arcs", ctypes.c_int64), ("phase_ms", ctypes.c_float * 4)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -70,7 +70,7 @@ class ServeStats(ctypes.Structure):
 # every symbol include/dupin.h declares
 EXPORTS = ["dupin_graph_load", "dupin_graph_free", "dupin_graph_info", "dupin_peel", "dupin_peel_batch",
            "dupin_serve_create", "dupin_serve_submit", "dupin_serve_poll", "dupin_serve_wait", "dupin_serve_stats",
-           "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc"]
+           "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc", "dupin_struct_size"]
 
 NOALLOC_MAX_N = 8192
 
@@ -100,9 +100,15 @@ def lib():
         L.dupin_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.dupin_peel_noalloc.argtypes = [i64, P, P, P, P, ctypes.POINTER(Params), P, ctypes.POINTER(Result), P]
         L.dupin_version.restype = ctypes.c_char_p
+        L.dupin_struct_size.argtypes = [ctypes.c_char_p]
         for nm in EXPORTS:
-            if nm != "dupin_version":
+            if nm not in ("dupin_version", "dupin_struct_size"):
                 getattr(L, nm).restype = ctypes.c_int
+        L.dupin_struct_size.restype = ctypes.c_int64
+        for st, nm in ((GraphDesc, b"dupin_graph_desc"), (Params, b"dupin_params"), (Result, b"dupin_result"),
+                       (ServeConfig, b"dupin_serve_config"), (ServeStats, b"dupin_serve_stats_t")):
+            if L.dupin_struct_size(nm) != ctypes.sizeof(st):
+                raise RuntimeError(f"libdupin.so was built with another layout of {nm.decode()}: rebuild it")
         _lib = L
     return _lib
 
@@ -203,9 +209,9 @@ class Graph:
             pass
 
 
-def make_params(metric="dg", k_mult=1, eps=(1, 10), max_rounds=0, flags=0, tail_cap=0) -> Params:
+def make_params(metric="dg", k_mult=1, eps=(1, 10), max_rounds=0, flags=0, tail_cap=0, tail_arc_cap=0) -> Params:
     m = METRICS[metric] if isinstance(metric, str) else int(metric)
-    return Params(m, k_mult, eps[0], eps[1], max_rounds, flags, tail_cap)
+    return Params(m, k_mult, eps[0], eps[1], max_rounds, flags, tail_cap, tail_arc_cap)
 
 
 @dataclass
@@ -223,6 +229,7 @@ class PeelOutput:
     trace_peeled: Optional[object] = None
     n_bulk_rounds: int = 0
     phase_ms: Optional[list] = None
+    tail_arcs: int = 0
 
 
 def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> Result:
@@ -238,7 +245,7 @@ def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> 
 def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
     out = PeelOutput(r.n_rounds, r.best_round, r.best_size, (int(r.best_f_hi) << 64) + int(r.best_f_lo),
                      r.best_density, r.n_min_rule, peel_round, best_mask, n_bulk_rounds=int(r.n_bulk_rounds),
-                     phase_ms=[float(x) for x in r.phase_ms])
+                     phase_ms=[float(x) for x in r.phase_ms], tail_arcs=int(r.tail_arcs))
     if trace is not None:
         R = r.n_rounds + 1
         fh, fl, sz, pe = trace
@@ -249,9 +256,9 @@ def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
 
 
 def peel(g: Graph, metric="dg", k_mult=1, eps=(1, 10), flags=0, max_rounds=0, tail_cap=0, want_rounds=True,
-         want_mask=True, want_trace=True, stream=None) -> PeelOutput:
+         want_mask=True, want_trace=True, stream=None, tail_arc_cap=0) -> PeelOutput:
     """dupin_peel with host result buffers (numpy)."""
-    p = make_params(metric, k_mult, eps, max_rounds, flags, tail_cap)
+    p = make_params(metric, k_mult, eps, max_rounds, flags, tail_cap, tail_arc_cap)
     pr = np.empty(g.n, np.int32) if want_rounds else None
     mk = np.empty(g.n, np.uint8) if want_mask else None
     trace = None

@@ -58,8 +58,15 @@ def test_struct_layouts_match_header():
 
     # 2 int64 + 7 pointers + uint32 (+ padding)
     assert ctypes.sizeof(dupin.GraphDesc) == 2 * 8 + 7 * 8 + 8
-    assert ctypes.sizeof(dupin.Params) == 4 + 4 + 8 + 8 + 8 + 4 + 4
-    assert ctypes.sizeof(dupin.Result) == 6 * 8 + 9 * 8 + 4 * 4
+    assert ctypes.sizeof(dupin.Params) == 4 + 4 + 8 + 8 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(dupin.Result) == 6 * 8 + 10 * 8 + 4 * 4
+    # and the library's own sizeof() of every public struct agrees
+    L = dupin.lib()
+    for st, nm in ((dupin.GraphDesc, b"dupin_graph_desc"), (dupin.Params, b"dupin_params"),
+                   (dupin.Result, b"dupin_result"), (dupin.ServeConfig, b"dupin_serve_config"),
+                   (dupin.ServeStats, b"dupin_serve_stats_t")):
+        assert L.dupin_struct_size(nm) == ctypes.sizeof(st), nm
+    assert L.dupin_struct_size(b"no_such_struct") == -1
 
 
 def test_product_path_does_not_import_oracle():

@@ -46,11 +46,11 @@ def assert_same(out, ref, ctx=""):
     assert np.array_equal(out.best_mask, ref.best_mask), ctx
 
 
-def run_both(dupin, g, metric, k, eps, flags=0, tail_cap=0):
+def run_both(dupin, g, metric, k, eps, flags=0, tail_cap=0, tail_arc_cap=0):
     og = oracle.Graph.from_synth(g, metric)
     dg = dupin.Graph.from_synth(g)
     ref = oracle.peel_batch(og, k, eps, flags=flags & oracle.FLAG_GPO)
-    out = dupin.peel(dg, metric, k, eps, flags=flags, tail_cap=tail_cap)
+    out = dupin.peel(dg, metric, k, eps, flags=flags, tail_cap=tail_cap, tail_arc_cap=tail_arc_cap)
     dg.free()
     og.close()
     return out, ref
@@ -106,6 +106,36 @@ def test_rmat_dw_gpo(dupin, tail_cap):
         for flags in (0, 1):
             out, ref = run_both(dupin, g, "dw", k, (1, 10), flags=flags, tail_cap=tail_cap)
             assert_same(out, ref, (k, flags, tail_cap))
+
+
+def live_arcs_after(g, peel_round, r):
+    """2 |E(S_r)|: arcs whose both ends are still live after round r."""
+    u, v = g.global_edges()
+    return 2 * int(np.count_nonzero(np.minimum(peel_round[u], peel_round[v]) > r))
+
+
+@pytest.mark.parametrize("tail_arc_cap", [1, 700, 20000])
+def test_tail_waits_for_few_arcs(dupin, tail_arc_cap):
+    """The tail starts only once 2|E(S)| <= tail_arc_cap; the grid-wide rounds
+    track |E(S)| exactly (the arcs the tail was built from match the oracle's
+    rounds), and the peel is unchanged."""
+    graphs = [(synth.rmat_weighted(14, 16, "dw", seed=3), "dw"),
+              (synth.bipartite_zipf(3000, 1500, 20000, 1.6, 1, 30, 30, 0.5, 12, seed=4), "fd")]
+    graphs[1][0].c = synth.fd_weights(graphs[1][0])
+    for g, metric in graphs:
+        for k in (1, 2):
+            for tail_cap in (2000, 300):
+                out, ref = run_both(dupin, g, metric, k, (1, 10), tail_cap=tail_cap, tail_arc_cap=tail_arc_cap)
+                ctx = (metric, k, tail_cap, tail_arc_cap)
+                assert_same(out, ref, ctx)
+                exact = live_arcs_after(g, ref.peel_round, out.n_bulk_rounds)
+                assert out.tail_arcs == exact, ctx
+                assert out.tail_arcs <= tail_arc_cap, ctx
+                # the tail started as soon as both caps allowed it
+                if out.n_bulk_rounds > 0:
+                    r = out.n_bulk_rounds - 1
+                    size_before = int(ref.trace_size[r])
+                    assert size_before > tail_cap or live_arcs_after(g, ref.peel_round, r) > tail_arc_cap, ctx
 
 
 def test_planted_block_config(dupin):
