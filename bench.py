@@ -40,6 +40,8 @@ WORKLOADS = {
     "fd_2Mx1M_40M": dict(metric="fd", eps=[(0, 1), (1, 20), (1, 5)], k=1),
     "rmat24_dw": dict(metric="dw", eps=[(1, 10)], k=1),
     "dg_block_10kx5k": dict(metric="dg", eps=[(1, 10)], k=1),
+    # the FD generator at a quarter of the size: the profiling case (arcs still exceed L2)
+    "fd_500kx250k_8M": dict(metric="fd", eps=[(0, 1), (1, 20), (1, 5)], k=1),
 }
 
 
@@ -52,6 +54,8 @@ def make_graph(name: str):
         return synth.rmat_weighted(24, 16, "dw", seed=1)
     if name == "dg_block_10kx5k":
         return synth.dg_planted_block(seed=1)
+    if name == "fd_500kx250k_8M":
+        return synth.fd_camouflage(seed=1, nU=500_000, nI=250_000, m_bg=8_000_000)
     raise ValueError(name)
 
 

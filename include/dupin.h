@@ -130,8 +130,10 @@ typedef struct {
     int64_t max_rounds; /* <= 0: n + 1 */
     uint32_t flags;
     int32_t tail_cap;   /* <= 0: automatic; else live-set size below which one CTA finishes */
-    int64_t tail_arc_cap; /* <= 0: automatic (2^21); else the one CTA also waits until
-                             the live sub-graph has at most this many arcs (2 |E(S)|) */
+    int64_t tail_arc_cap; /* <= 0: automatic (2^16); else, once |S| <= tail_cap, the
+                             one CTA takes over when the live sub-graph has at most
+                             this many arcs (2 |E(S)|) or after a round that removed
+                             at most 64 vertices, whichever comes first */
 } dupin_params;
 
 /*

@@ -23,6 +23,11 @@ typedef unsigned __int128 u128;
 // back-off below) and report DUPIN_ERR_TIMEOUT instead of hanging.
 #define DUPIN_SPIN_LIMIT (1ll << 21)
 
+// A grid-wide round that removed at most this many vertices is "small":
+// once S fits the one-CTA tail, the tail takes over after such a round
+// whatever the live arc count.
+#define DUPIN_TAIL_SMALL_ROUND 64
+
 // Peeling phases recorded in PeelCtl::status
 #define ST_RUNNING 0
 #define ST_DONE 1
@@ -67,7 +72,10 @@ struct BlockPart {
     unsigned long long in_lo, in_hi;  // expand: sum of c over arcs inside U
     long long min_dec;    // expand: minimum weight after a decrement
     long long rem_cnt;    // expand: 2 per arc from U to S \ U, 1 per arc inside U
-    long long pad[5];
+    long long mc_cnt;     // minimum-rule candidates (live vertices of weight min_surv)
+    long long mc_stage;   // ... with at least one arc
+    long long mc_deg;     // ... and their arcs
+    long long pad[2];
 };
 
 // Hubs: up to DUPIN_HUB_MAX highest-degree vertices (degree >= DUPIN_HUB_MIN_DEG).
@@ -95,7 +103,7 @@ struct PeelArgs {
     long long *w;
     int *pr;
     int *live0, *live1;
-    int *stage_id;
+    int *stage_id;      // minimum-rule candidates: live-list positions
     long long *stage_start, *stage_off;
     long long *fstart, *fbase;
     long long *cstart;

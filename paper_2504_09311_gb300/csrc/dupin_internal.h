@@ -103,5 +103,5 @@ int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStrea
 // the largest live set the single-CTA tail accepts, and the default caps
 long long tail_cap_limit();
 long long tail_cap_default();
-#define DUPIN_TAIL_ARCS_DEFAULT (1LL << 21)
+#define DUPIN_TAIL_ARCS_DEFAULT (1LL << 16)
 int peel_grid_size();

@@ -297,6 +297,27 @@ __global__ void k_init_finish(PeelArgs A, long long n) {
 
 // ------------------------------------------------------ (b)-(c) bulk rounds
 
+// Stage one warp's frontier entries (lanes with 'stage' set): slots and arc
+// offsets within the block come from one shared counter packing
+// (entries << 40 | arcs).
+__device__ __forceinline__ void stage_entry(const PeelArgs &A, long long j0, bool stage, long long start,
+                                            long long deg, unsigned long long *s_pack) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, stage);
+    if (!bal) return;
+    const long long incl = warp_incl_scan64(stage ? deg : 0);
+    const long long tot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(s_pack, ((unsigned long long)__popc(bal) << 40) | (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (stage) {
+        const long long slot = (long long)(base >> 40) + __popc(bal & ((1u << lane) - 1u));
+        const long long off = (long long)(base & ((1ull << 40) - 1)) + incl - deg;
+        A.stage_start[j0 + slot] = start;
+        A.stage_off[j0 + slot] = off;
+    }
+}
+
 __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
     __shared__ long long s_v[BULK_WARPS][6];
     __shared__ unsigned long long s_lo[BULK_WARPS], s_hi[BULK_WARPS];
@@ -344,13 +365,19 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         st.n_min_rule = ctl->n_min_rule;
         st.scan = ctl->scan_volume;
         s_elive = ctl->elive;
+        s_rd.U_sel = kMaxLL;  // no round yet
     }
     __syncthreads();
     if (ctl->status != ST_RUNNING || ctl->error) return;
 
     for (;;) {
         const long long size = s_st.size;
-        if (size == 0 || (size <= A.tail_cap && 2 * s_elive <= A.tail_arcs)) break;
+        // the one-CTA tail takes over once S fits it and either its arcs are
+        // few or the rounds have become small (a round of few vertices costs
+        // the tail microseconds and the grid-wide kernel its barriers)
+        if (size == 0 ||
+            (size <= A.tail_cap && (2 * s_elive <= A.tail_arcs || s_rd.U_sel <= DUPIN_TAIL_SMALL_ROUND)))
+            break;
         if (s_st.round >= A.max_rounds) {
             if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
             break;
@@ -373,16 +400,19 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         int *nlive = live_sel ? A.live0 : A.live1;
         const long long L = s_st.live_len;
         const long long j0 = split_at(L, b, G), j1 = split_at(L, b + 1, G);
-        // Phase A selects w <= T.  If no block selected anything (possible only
-        // when k(1+eps) < 2), the round takes the minimum rule: phase A runs a
-        // second time with the minimum live weight, which the first pass found.
-        long long thr = T;
+        // Phase A selects w <= T.  When k(1+eps) < 2 the threshold can select
+        // nobody, and the round then takes the minimum rule (U_i = the live
+        // vertices of minimum weight).  So that this needs no second pass, a
+        // block that selected nothing also stages its own minimum-weight
+        // vertices as candidates; after the barrier, if no block selected
+        // anything, the blocks whose minimum is the global one commit theirs.
+        const long long thr = T;
         bool minrule = false;
         long long U_sel = 0, U_stage = 0, totArcs = 0, slotBase = 0, arcBase = 0, survBase = 0;
-        for (int pass = 0;; pass++) {
-            // ---------------- phase A: select
-            if (tid == 0) s_pack = 0;
-            __syncthreads();
+        // ---------------- phase A: select
+        if (tid == 0) s_pack = 0;
+        __syncthreads();
+        {
             long long cnt = 0, surv = 0, minsurv = kMaxLL;
             unsigned long long wlo = 0, whi = 0;
             for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
@@ -404,84 +434,142 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                     start = g.rp[id];
                     deg = g.rp[id + 1] - start;
                 }
-                const bool stage = sel && deg > 0;
-                const unsigned bal = __ballot_sync(0xffffffffu, stage);
-                if (bal) {
-                    long long incl = warp_incl_scan64(stage ? deg : 0);
-                    long long tot = __shfl_sync(0xffffffffu, incl, 31);
-                    unsigned long long base = 0;
-                    if (lane == 0)
-                        base = atomicAdd(&s_pack, ((unsigned long long)__popc(bal) << 40) | (unsigned long long)tot);
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (stage) {
-                        long long slot = (long long)(base >> 40) + __popc(bal & ((1u << lane) - 1u));
-                        long long off = (long long)(base & ((1ull << 40) - 1)) + incl - deg;
-                        A.stage_start[j0 + slot] = start;
-                        A.stage_off[j0 + slot] = off;
-                    }
-                }
+                stage_entry(A, j0, sel && deg > 0, start, deg, &s_pack);
             }
-            {
-                BlockRed<BULK_WARPS, 6> r;
-                r.v[0] = cnt; r.v[1] = surv; r.v[2] = 0; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
-                r.lo = wlo; r.hi = whi; r.mn = minsurv;
-                block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            BlockRed<BULK_WARPS, 6> r;
+            r.v[0] = cnt; r.v[1] = surv; r.v[2] = 0; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
+            r.lo = wlo; r.hi = whi; r.mn = minsurv;
+            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            BlockPart &p = A.part[b];
+            if (tid == 0) {
+                p.sel_cnt = r.v[0];
+                p.surv_cnt = r.v[1];
+                p.ws_lo = r.lo;
+                p.ws_hi = r.hi;
+                p.min_surv = r.mn;
+                p.stage_cnt = (long long)(s_pack >> 40);
+                p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
+            }
+            const long long m = r.mn;
+            if (A.use_min && r.v[0] == 0 && m != kMaxLL) {
+                // minimum-rule candidates: the live vertices of weight m (their
+                // list positions in stage_id, the ones with arcs staged as usual)
+                __syncthreads();  // thread 0 has read s_pack
                 if (tid == 0) {
-                    BlockPart &p = A.part[b];
-                    p.sel_cnt = r.v[0];
-                    p.surv_cnt = r.v[1];
-                    p.ws_lo = r.lo;
-                    p.ws_hi = r.hi;
-                    p.min_surv = r.mn;
-                    p.stage_cnt = (long long)(s_pack >> 40);
-                    p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
+                    s_pack = 0;
+                    s_surv = 0;
                 }
+                __syncthreads();
+                for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
+                    const long long j = jb + lane;
+                    const int id = j < j1 ? live[j] : -1;
+                    const bool c = id >= 0 && A.w[id] == m;
+                    const unsigned cb = __ballot_sync(0xffffffffu, c);
+                    long long start = 0, deg = 0;
+                    if (cb) {
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(&s_surv, (unsigned long long)__popc(cb));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (c) {
+                            A.stage_id[j0 + (long long)base + __popc(cb & ((1u << lane) - 1u))] = (int)j;
+                            start = g.rp[id];
+                            deg = g.rp[id + 1] - start;
+                        }
+                    }
+                    stage_entry(A, j0, c && deg > 0, start, deg, &s_pack);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    p.mc_cnt = (long long)s_surv;
+                    p.mc_stage = (long long)(s_pack >> 40);
+                    p.mc_deg = (long long)(s_pack & ((1ull << 40) - 1));
+                }
+            } else if (tid == 0) {
+                p.mc_cnt = 0;
+                p.mc_stage = 0;
+                p.mc_deg = 0;
             }
-            if (!grid_barrier(ctl, G, epoch)) return;
-            // ---------------- phase B (part 1): totals and this block's offsets
-            long long minSurvAll;
-            {
-                BlockRed<BULK_WARPS, 6> r;
+        }
+        if (!grid_barrier(ctl, G, epoch)) return;
+        // ---------------- phase B (part 1): totals and this block's offsets
+        long long myStage, myDeg, myCand = 0;
+        {
+            BlockRed<BULK_WARPS, 6> r;
+            for (int j = 0; j < 6; j++) r.v[j] = 0;
+            r.lo = 0; r.hi = 0; r.mn = kMaxLL;
+            // v: 0 sel_cnt, 1 stage_cnt, 2 sel_deg, 3 survivors before b,
+            //    4 stage entries before b, 5 arcs before b
+            for (int t = tid; t < (int)G; t += BULK_THREADS) {
+                const BlockPart &p = A.part[t];
+                r.v[0] += p.sel_cnt;
+                r.v[1] += p.stage_cnt;
+                r.v[2] += p.sel_deg;
+                if (t < b) {
+                    r.v[3] += p.surv_cnt;
+                    r.v[4] += p.stage_cnt;
+                    r.v[5] += p.sel_deg;
+                }
+                add128(r.lo, r.hi, p.ws_lo, p.ws_hi);
+                r.mn = p.min_surv < r.mn ? p.min_surv : r.mn;
+            }
+            block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
+            U_sel = r.v[0]; U_stage = r.v[1]; totArcs = r.v[2];
+            survBase = r.v[3]; slotBase = r.v[4]; arcBase = r.v[5];
+            if (tid == 0) {
+                s_rd.wlo = r.lo;
+                s_rd.whi = r.hi;
+            }
+            myStage = A.part[b].stage_cnt;
+            myDeg = A.part[b].sel_deg;
+            const long long minAll = r.mn;
+            if (U_sel == 0 && A.use_min && minAll != kMaxLL) {
+                // minimum rule: U_i = the candidates of the blocks whose
+                // minimum is the global minimum
+                minrule = true;
                 for (int j = 0; j < 6; j++) r.v[j] = 0;
                 r.lo = 0; r.hi = 0; r.mn = kMaxLL;
-                // v: 0 sel_cnt, 1 stage_cnt, 2 sel_deg, 3 survivors before b,
-                //    4 stage entries before b, 5 arcs before b
                 for (int t = tid; t < (int)G; t += BULK_THREADS) {
                     const BlockPart &p = A.part[t];
-                    r.v[0] += p.sel_cnt;
-                    r.v[1] += p.stage_cnt;
-                    r.v[2] += p.sel_deg;
-                    if (t < b) {
-                        r.v[3] += p.surv_cnt;
-                        r.v[4] += p.stage_cnt;
-                        r.v[5] += p.sel_deg;
+                    const bool q = p.min_surv == minAll;
+                    if (q) {
+                        r.v[0] += p.mc_cnt;
+                        r.v[1] += p.mc_stage;
+                        r.v[2] += p.mc_deg;
                     }
-                    add128(r.lo, r.hi, p.ws_lo, p.ws_hi);
-                    r.mn = p.min_surv < r.mn ? p.min_surv : r.mn;
+                    if (t < b) {
+                        r.v[3] += p.surv_cnt - (q ? p.mc_cnt : 0);
+                        if (q) {
+                            r.v[4] += p.mc_stage;
+                            r.v[5] += p.mc_deg;
+                        }
+                    }
                 }
                 block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
                 U_sel = r.v[0]; U_stage = r.v[1]; totArcs = r.v[2];
                 survBase = r.v[3]; slotBase = r.v[4]; arcBase = r.v[5];
-                minSurvAll = r.mn;
+                const BlockPart &pb = A.part[b];
+                const bool mine = pb.min_surv == minAll;
+                myStage = mine ? pb.mc_stage : 0;
+                myDeg = mine ? pb.mc_deg : 0;
+                myCand = mine ? pb.mc_cnt : 0;
                 if (tid == 0) {
-                    s_rd.wlo = r.lo;
-                    s_rd.whi = r.hi;
+                    const u128 ws = (u128)(unsigned long long)U_sel * (unsigned long long)minAll;
+                    s_rd.wlo = (unsigned long long)ws;
+                    s_rd.whi = (unsigned long long)(ws >> 64);
                 }
             }
-            if (U_sel > 0 || pass > 0 || !A.use_min || minSurvAll == kMaxLL) break;
-            thr = minSurvAll;  // every live vertex survived the threshold: minimum rule
-            minrule = true;
-            // every block has read the partials before the second pass rewrites them
-            if (!grid_barrier(ctl, G, epoch)) return;
         }
         if (U_sel == 0) {  // cannot happen (Lemma 4.2 / minimum rule): stop rather than spin
             if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
             return;
         }
-        long long myStage, myDeg;
-        {
-            myStage = A.part[b].stage_cnt;
-            myDeg = A.part[b].sel_deg;
+        if (myCand > 0) {  // commit this block's minimum-rule candidates
+            for (long long c = tid; c < myCand; c += BULK_THREADS) {
+                const long long j = A.stage_id[j0 + c];
+                A.pr[live[j]] = (int)i;
+                live[j] = -1;
+            }
+            __syncthreads();
         }
         const long long newSize = size - U_sel;
         const bool compact = newSize > 0 && (2 * newSize <= L || newSize <= A.tail_cap);
@@ -1131,16 +1219,18 @@ DevGraph dev_graph(const dupin_graph *g, int metric) {
 }
 
 // arcs the tail buffer must hold: the live sub-graph has at most
-// min(all arcs, |S| (|S| - 1), the plan's arc cap)
+// min(all arcs, |S| (|S| - 1)) (the tail may start after a small round
+// whatever its arc count)
 static long long tail_arc_buffer(long long arcs, const PeelPlan &plan) {
     const long long tc = plan.tail_cap;
-    return std::min<long long>(std::min<long long>(arcs, tc * (tc > 0 ? tc - 1 : 0)), plan.tail_arcs);
+    return std::min<long long>(arcs, tc * (tc > 0 ? tc - 1 : 0));
 }
 
 long long workspace_bytes(long long n, long long arcs, bool has_cw, const PeelPlan &plan, int grid) {
     const long long tail_cap = plan.tail_cap, tr_cap = plan.tr_cap;
     const long long tarc = tail_arc_buffer(arcs, plan);
     long long b = 0;
+    // w, pr, live0, live1, stage_id, stage_start, stage_off, fstart, loc, mask; fbase
     b += n * (8 + 4 + 4 + 4 + 4 + 8 + 8 + 8 + 4 + 1) + 8 * (n + 1);
     b += 8 * (grid + 1) + (long long)sizeof(BlockPart) * grid + (long long)sizeof(PeelCtl);
     b += 32 * tr_cap;
@@ -1189,7 +1279,7 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
     A(&ws->pr, n);
     A(&ws->live0, n);
     A(&ws->live1, n);
-    A(&ws->stage_id, 1);
+    A(&ws->stage_id, n);
     A(&ws->stage_start, n);
     A(&ws->stage_off, n);
     A(&ws->fstart, n);

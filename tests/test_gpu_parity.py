@@ -116,7 +116,8 @@ def live_arcs_after(g, peel_round, r):
 
 @pytest.mark.parametrize("tail_arc_cap", [1, 700, 20000])
 def test_tail_waits_for_few_arcs(dupin, tail_arc_cap):
-    """The tail starts only once 2|E(S)| <= tail_arc_cap; the grid-wide rounds
+    """The tail starts once S fits it and either 2|E(S)| <= tail_arc_cap or the
+    last grid-wide round removed at most 64 vertices; the grid-wide rounds
     track |E(S)| exactly (the arcs the tail was built from match the oracle's
     rounds), and the peel is unchanged."""
     graphs = [(synth.rmat_weighted(14, 16, "dw", seed=3), "dw"),
@@ -128,14 +129,20 @@ def test_tail_waits_for_few_arcs(dupin, tail_arc_cap):
                 out, ref = run_both(dupin, g, metric, k, (1, 10), tail_cap=tail_cap, tail_arc_cap=tail_arc_cap)
                 ctx = (metric, k, tail_cap, tail_arc_cap)
                 assert_same(out, ref, ctx)
-                exact = live_arcs_after(g, ref.peel_round, out.n_bulk_rounds)
+                nb = out.n_bulk_rounds
+                exact = live_arcs_after(g, ref.peel_round, nb)
                 assert out.tail_arcs == exact, ctx
-                assert out.tail_arcs <= tail_arc_cap, ctx
-                # the tail started as soon as both caps allowed it
-                if out.n_bulk_rounds > 0:
-                    r = out.n_bulk_rounds - 1
-                    size_before = int(ref.trace_size[r])
-                    assert size_before > tail_cap or live_arcs_after(g, ref.peel_round, r) > tail_arc_cap, ctx
+                # the tail starts once S fits and either its arcs are few or the
+                # last grid-wide round was small (<= 64 vertices) ...
+                if out.tail_arcs > 0:
+                    assert ref.trace_size[nb] <= tail_cap, ctx
+                    assert out.tail_arcs <= tail_arc_cap or (nb > 0 and ref.trace_peeled[nb] <= 64), ctx
+                # ... and not later
+                if nb > 0:
+                    r = nb - 1
+                    small = r > 0 and ref.trace_peeled[r] <= 64
+                    assert ref.trace_size[r] > tail_cap or (live_arcs_after(g, ref.peel_round, r) > tail_arc_cap
+                                                            and not small), ctx
 
 
 def test_planted_block_config(dupin):
