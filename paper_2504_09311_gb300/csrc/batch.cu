@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <mutex>
 #include "dupin_internal.h"
 #include "peel_device.cuh"
 
@@ -48,7 +50,7 @@ struct CtaJob {
     long long *out;    // [8]: R, best round, best size, best f hi, best f lo, minimum-rule rounds, error, 0
 };
 
-__device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf, TailAcc *s_acc, long long *s_w,
+__device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf, TailAcc<CTA_WARPS> *s_acc, long long *s_w,
                                              long long *s_pref, long long *s_fs, long long *s_fl, int *s_big,
                                              int *s_nbig, unsigned long long *s_lo, unsigned long long *s_hi) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -127,10 +129,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         m = warp_min64(m);
         if (lane == 0) first[q] = m;
     }
-    if (tid < 2) {
-        TailAcc z = TAIL_ACC_ZERO;
-        s_acc[tid] = z;
-    }
+    if (tid < 2) s_acc[tid].F = 0;
     __syncthreads();
     RoundState st;
     {
@@ -162,7 +161,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         const long long i = R.i;
         const long long *cur = segbuf + (i & 1) * nseg;
         long long *nxt = segbuf + ((i + 1) & 1) * nseg;
-        TailAcc &acc = s_acc[i & 1];
+        TailAcc<CTA_WARPS> &acc = s_acc[i & 1];
         // ---- select
         unsigned long long wlo = 0, whi = 0;
         long long mins = kMaxLL;  // new minimum over the segments this lane looked at
@@ -227,14 +226,12 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         warp_sum128(wlo, whi);
         mins = warp_min64(mins);
         if (lane == 0) {
-            acc_add128(&acc.wlo, &acc.whi, wlo, whi);
-            if (mins != kMaxLL) atomicMin(&acc.mins, mins);
+            acc.wlo[wid] = wlo;
+            acc.whi[wid] = whi;
+            acc.mins[wid] = mins;
         }
         __syncthreads();
-        if (tid == 0) {
-            TailAcc z = TAIL_ACC_ZERO;
-            s_acc[(i + 1) & 1] = z;
-        }
+        if (tid == 0) s_acc[(i + 1) & 1].F = 0;
         const int F = (int)acc.F;
         // ---- expand: every arc of the frontier (heads read from global memory)
         unsigned long long ilo = 0, ihi = 0;
@@ -288,12 +285,15 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         warp_sum128(ilo, ihi);
         mind = warp_min64(mind);
         if (lane == 0) {
-            acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
-            if (mind != kMaxLL) atomicMin(&acc.mins, mind);
+            acc.ilo[wid] = ilo;
+            acc.ihi[wid] = ihi;
+            if (mind < acc.mins[wid]) acc.mins[wid] = mind;
         }
         __syncthreads();
         // ---- every warp: close round i, plan round i + 1
-        const u128 wsel = mk128(acc.wlo, acc.whi), internal = mk128(acc.ilo, acc.ihi);
+        u128 wsel, internal;
+        long long mins_all;
+        tail_acc_sum(acc, wsel, internal, mins_all);
         st.f = st.f - (wsel - (internal >> 1));
         st.size -= F;
         st.round = i;
@@ -313,7 +313,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, acc.mins);
+        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, mins_all);
     }
     __syncthreads();
     for (long long u = tid; u < n; u += CTA_THREADS) {
@@ -334,7 +334,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
 
 __global__ void __launch_bounds__(CTA_THREADS, 2) k_peel_cta(const CtaJob *jobs, int njobs, int *next) {
     extern __shared__ __align__(16) long long s_seg[];  // 2 * CTA_MAX_SEG
-    __shared__ TailAcc s_acc[2];
+    __shared__ TailAcc<CTA_WARPS> s_acc[2];
     __shared__ long long s_w[CTA_WARPS];
     __shared__ long long s_pref[CTA_THREADS + 1];
     __shared__ long long s_fs[TAIL_FAST], s_fl[TAIL_FAST];
@@ -589,6 +589,93 @@ int cta_batch_finish(CtaBatch *B, cudaStream_t s, std::vector<int> *per_job_stat
     return DUPIN_OK;
 }
 
+// Streams for concurrent tails, created once per device and reused.
+static cudaStream_t tail_stream(int dev, size_t q) {
+    static std::mutex mu;
+    static std::map<int, std::vector<cudaStream_t>> pool;
+    const size_t kMax = 32;
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<cudaStream_t> &v = pool[dev];
+    const size_t want = std::min(q + 1, kMax);
+    while (v.size() < want) {
+        cudaStream_t t = nullptr;
+        if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) break;
+        v.push_back(t);
+    }
+    return v.empty() ? nullptr : v[q % v.size()];
+}
+
+// Several peels of large graphs (or of one graph under several parameter
+// sets).  The grid-wide stages run one after another on 'stream' (each is a
+// cooperative launch over the whole GPU); then each peel's tail sub-graph is
+// built on 'stream' and its one-CTA tail runs on a stream of its own, so the
+// latency-bound tails, one SM each, run side by side.  No tail overlaps a
+// grid-wide stage: the first tail starts after the last of them.  A graph
+// that appears several times gets one cached workspace per appearance.
+static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
+                                 const std::vector<int64_t> &idx, cudaStream_t s) {
+    const size_t k = idx.size();
+    std::vector<PeelPlan> plans(k);
+    std::vector<PeelWorkspace *> ws(k, nullptr);
+    std::map<dupin_graph *, int> uses;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto fail_at = [&](size_t q, int rc) {
+        char buf[512];
+        dupin_last_error(buf, sizeof(buf));
+        return dupin_fail(rc, "graph " + std::to_string((long long)idx[q]) + ": " + buf);
+    };
+    for (size_t q = 0; q < k; q++) {
+        dupin_graph *g = graphs[idx[q]];
+        if (g->device != dev) return dupin_fail(DUPIN_ERR_INVALID_ARG, "batched graphs must live on the current device");
+        int rc = peel_resolve(g, &params[idx[q]], &plans[q]);
+        if (rc) return fail_at(q, rc);
+        ws[q] = workspace_slot(g, uses[g]++, plans[q], &rc);
+        if (rc) return fail_at(q, rc);
+    }
+    for (size_t q = 0; q < k; q++) {
+        int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_FRONT, s);
+        if (rc) return fail_at(q, rc);
+    }
+    std::vector<cudaEvent_t> ev(2 * k, nullptr);
+    int rc = DUPIN_OK;
+    for (size_t q = 0; q < k && rc == DUPIN_OK; q++) {
+        rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BUILD, s);
+        if (rc) break;
+        cudaStream_t t = tail_stream(dev, q);
+        if (!t) {
+            rc = dupin_fail(DUPIN_ERR_CUDA, "could not create a stream for the tails");
+            break;
+        }
+        cudaError_t e = cudaEventCreateWithFlags(&ev[2 * q], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * q + 1], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(t, ev[2 * q], 0);
+        if (e != cudaSuccess) {
+            rc = dupin_cuda_fail(e, "tail stream setup");
+            break;
+        }
+        rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_TAIL, t);
+        if (rc) break;
+        e = cudaEventRecord(ev[2 * q + 1], t);
+        if (e != cudaSuccess) rc = dupin_cuda_fail(e, "tail stream join");
+    }
+    // join the tails only after all of them are queued: a join inside the loop
+    // would queue each build behind the previous tail
+    for (size_t q = 0; q < k && rc == DUPIN_OK; q++) {
+        cudaError_t e = cudaStreamWaitEvent(s, ev[2 * q + 1], 0);
+        if (e != cudaSuccess) rc = dupin_cuda_fail(e, "tail stream join");
+    }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc) return rc;
+    for (size_t q = 0; q < k; q++) {
+        rc = peel_finish(graphs[idx[q]], ws[q], &params[idx[q]], &results[idx[q]], s);
+        if (rc) return fail_at(q, rc);
+    }
+    return DUPIN_OK;
+}
+
 extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
                                 int64_t count, void *stream) {
     if (count < 0) return dupin_fail(DUPIN_ERR_INVALID_ARG, "count < 0");
@@ -613,6 +700,7 @@ extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *
     if (rc) return rc;
     rc = cta_batch_finish(B, s, nullptr);
     if (rc) return rc;
+    if (big.size() > 1) return peel_large_concurrent(graphs, params, results, big, s);
     for (int64_t j : big) {
         rc = dupin_peel(graphs[j], &params[j], &results[j], stream);
         if (rc) {

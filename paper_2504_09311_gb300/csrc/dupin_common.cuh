@@ -27,6 +27,8 @@ typedef unsigned __int128 u128;
 // once S fits the one-CTA tail, the tail takes over after such a round
 // whatever the live arc count.
 #define DUPIN_TAIL_SMALL_ROUND 64
+// ... provided its live sub-graph fits the tail's arc buffer (2^25 arcs)
+#define DUPIN_TAIL_BUF_ARCS (1LL << 25)
 
 // Peeling phases recorded in PeelCtl::status
 #define ST_RUNNING 0

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "dupin.h"
 #include "dupin_common.cuh"
@@ -44,7 +45,9 @@ struct PeelWorkspace {
     long long *tcw = nullptr;
     uint8_t *mask = nullptr;
     bool async = false;  // allocated with cudaMallocAsync (freed with cudaFreeAsync)
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // DUPIN_TIMING
+    // DUPIN_TIMING: front start, init done, grid-wide rounds done, build start,
+    // build done, tail done
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     long long bytes = 0;
 };
 
@@ -59,6 +62,7 @@ struct dupin_graph {
     int n_hubs = 0;
     long long bytes = 0;
     PeelWorkspace *ws = nullptr;
+    std::vector<PeelWorkspace *> ws_more;  // further workspaces for concurrent peels of this graph
 };
 
 // The caps of one peel, resolved from its params and the graph: the tail
@@ -74,11 +78,19 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
 void workspace_free(PeelWorkspace *ws);
 void workspace_free(PeelWorkspace *ws, cudaStream_t s);
 int workspace_ensure(dupin_graph *g, const PeelPlan &plan);
+// workspace k of graph g (0: the one dupin_peel uses), allocated or grown for plan
+PeelWorkspace *workspace_slot(dupin_graph *g, int k, const PeelPlan &plan, int *rc);
 
 // the three steps of dupin_peel: caps from params, kernels on a stream, results
 int peel_resolve(const dupin_graph *g, const dupin_params *p, PeelPlan *plan);
 int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
                  cudaStream_t s);
+// The stages of one peel: PEEL_FRONT = control reset, initial weights and the
+// grid-wide rounds (a cooperative launch over the whole GPU), PEEL_BUILD = the
+// tail sub-graph, PEEL_TAIL = the one-CTA rounds.
+enum { PEEL_FRONT = 1, PEEL_BUILD = 2, PEEL_TAIL = 4, PEEL_ALL = 7 };
+int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
+                        int stages, cudaStream_t s);
 int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, dupin_result *r, cudaStream_t s);
 
 // kernels shared by loading and peeling

@@ -151,6 +151,7 @@ static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
 static void graph_release(dupin_graph *g) {
     if (!g) return;
     workspace_free(g->ws);
+    for (PeelWorkspace *w : g->ws_more) workspace_free(w);
     cudaFree(g->hubs);
     cudaFree(g->rp);
     cudaFree(g->col);

@@ -297,24 +297,23 @@ __global__ void k_init_finish(PeelArgs A, long long n) {
 
 // ------------------------------------------------------ (b)-(c) bulk rounds
 
-// Stage one warp's frontier entries (lanes with 'stage' set): slots and arc
-// offsets within the block come from one shared counter packing
-// (entries << 40 | arcs).
+// Stage one warp's frontier entries (lanes with 'stage' set) at block-local
+// slots from a 32-bit shared counter: each entry's first arc and degree (the
+// arc offsets follow from a scan in phase B).  Shared-memory atomics stay
+// 32-bit: 64-bit ones are compare-and-swap loops that collapse under
+// contention.
 __device__ __forceinline__ void stage_entry(const PeelArgs &A, long long j0, bool stage, long long start,
-                                            long long deg, unsigned long long *s_pack) {
+                                            long long deg, unsigned *s_nst) {
     const int lane = threadIdx.x & 31;
     const unsigned bal = __ballot_sync(0xffffffffu, stage);
     if (!bal) return;
-    const long long incl = warp_incl_scan64(stage ? deg : 0);
-    const long long tot = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(s_pack, ((unsigned long long)__popc(bal) << 40) | (unsigned long long)tot);
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(s_nst, (unsigned)__popc(bal));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (stage) {
-        const long long slot = (long long)(base >> 40) + __popc(bal & ((1u << lane) - 1u));
-        const long long off = (long long)(base & ((1ull << 40) - 1)) + incl - deg;
+        const long long slot = (long long)base + __popc(bal & ((1u << lane) - 1u));
         A.stage_start[j0 + slot] = start;
-        A.stage_off[j0 + slot] = off;
+        A.stage_off[j0 + slot] = deg;
     }
 }
 
@@ -322,12 +321,14 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
     __shared__ long long s_v[BULK_WARPS][6];
     __shared__ unsigned long long s_lo[BULK_WARPS], s_hi[BULK_WARPS];
     __shared__ long long s_mn[BULK_WARPS];
-    __shared__ unsigned long long s_pack;
-    __shared__ unsigned long long s_surv;
+    __shared__ unsigned s_nst;   // frontier entries staged by the block
+    __shared__ unsigned s_surv;  // candidates / survivors placed by the block
+    __shared__ long long s_scan[BULK_WARPS];
     __shared__ long long s_base[WALK_WIN + 1];
     __shared__ long long s_start[WALK_WIN + 1];
     __shared__ int s_hub[DUPIN_HUB_MAX];
-    __shared__ unsigned long long s_hacc[DUPIN_HUB_MAX];
+    // a round's decrements of each hub, as two 32-bit words (hi gets the carries)
+    __shared__ unsigned s_hlo[DUPIN_HUB_MAX], s_hhi[DUPIN_HUB_MAX];
     // The state after the last completed round lives in shared memory, not in
     // registers: thread 0 updates it at the end of a round (phase D) and a
     // block barrier publishes it.  s_rd carries phase B's totals to phase D.
@@ -347,7 +348,8 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
     const int nh = g.n_hubs;
     for (int h = tid; h < nh; h += BULK_THREADS) {
         s_hub[h] = g.hubs[h];
-        s_hacc[h] = 0;
+        s_hlo[h] = 0;
+        s_hhi[h] = 0;
     }
     unsigned epoch = 0;  // grid barriers passed
     if (tid == 0) {
@@ -375,8 +377,8 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         // the one-CTA tail takes over once S fits it and either its arcs are
         // few or the rounds have become small (a round of few vertices costs
         // the tail microseconds and the grid-wide kernel its barriers)
-        if (size == 0 ||
-            (size <= A.tail_cap && (2 * s_elive <= A.tail_arcs || s_rd.U_sel <= DUPIN_TAIL_SMALL_ROUND)))
+        if (size == 0 || (size <= A.tail_cap && (2 * s_elive <= A.tail_arcs ||
+                                                  (s_rd.U_sel <= DUPIN_TAIL_SMALL_ROUND && 2 * s_elive <= A.tarc_cap))))
             break;
         if (s_st.round >= A.max_rounds) {
             if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
@@ -410,10 +412,10 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         bool minrule = false;
         long long U_sel = 0, U_stage = 0, totArcs = 0, slotBase = 0, arcBase = 0, survBase = 0;
         // ---------------- phase A: select
-        if (tid == 0) s_pack = 0;
+        if (tid == 0) s_nst = 0;
         __syncthreads();
         {
-            long long cnt = 0, surv = 0, minsurv = kMaxLL;
+            long long cnt = 0, surv = 0, minsurv = kMaxLL, sdeg = 0;
             unsigned long long wlo = 0, whi = 0;
             for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
                 const long long j = jb + lane;
@@ -433,11 +435,12 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                     live[j] = -1;
                     start = g.rp[id];
                     deg = g.rp[id + 1] - start;
+                    sdeg += deg;
                 }
-                stage_entry(A, j0, sel && deg > 0, start, deg, &s_pack);
+                stage_entry(A, j0, sel && deg > 0, start, deg, &s_nst);
             }
             BlockRed<BULK_WARPS, 6> r;
-            r.v[0] = cnt; r.v[1] = surv; r.v[2] = 0; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
+            r.v[0] = cnt; r.v[1] = surv; r.v[2] = sdeg; r.v[3] = 0; r.v[4] = 0; r.v[5] = 0;
             r.lo = wlo; r.hi = whi; r.mn = minsurv;
             block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
             BlockPart &p = A.part[b];
@@ -447,19 +450,20 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 p.ws_lo = r.lo;
                 p.ws_hi = r.hi;
                 p.min_surv = r.mn;
-                p.stage_cnt = (long long)(s_pack >> 40);
-                p.sel_deg = (long long)(s_pack & ((1ull << 40) - 1));
+                p.stage_cnt = (long long)s_nst;
+                p.sel_deg = r.v[2];
             }
             const long long m = r.mn;
             if (A.use_min && r.v[0] == 0 && m != kMaxLL) {
                 // minimum-rule candidates: the live vertices of weight m (their
                 // list positions in stage_id, the ones with arcs staged as usual)
-                __syncthreads();  // thread 0 has read s_pack
+                __syncthreads();  // thread 0 has read s_nst
                 if (tid == 0) {
-                    s_pack = 0;
+                    s_nst = 0;
                     s_surv = 0;
                 }
                 __syncthreads();
+                long long cdeg = 0;
                 for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
                     const long long j = jb + lane;
                     const int id = j < j1 ? live[j] : -1;
@@ -467,22 +471,27 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                     const unsigned cb = __ballot_sync(0xffffffffu, c);
                     long long start = 0, deg = 0;
                     if (cb) {
-                        unsigned long long base = 0;
-                        if (lane == 0) base = atomicAdd(&s_surv, (unsigned long long)__popc(cb));
+                        unsigned base = 0;
+                        if (lane == 0) base = atomicAdd(&s_surv, (unsigned)__popc(cb));
                         base = __shfl_sync(0xffffffffu, base, 0);
                         if (c) {
                             A.stage_id[j0 + (long long)base + __popc(cb & ((1u << lane) - 1u))] = (int)j;
                             start = g.rp[id];
                             deg = g.rp[id + 1] - start;
+                            cdeg += deg;
                         }
                     }
-                    stage_entry(A, j0, c && deg > 0, start, deg, &s_pack);
+                    stage_entry(A, j0, c && deg > 0, start, deg, &s_nst);
                 }
-                __syncthreads();
+                BlockRed<BULK_WARPS, 6> rc;
+                for (int q = 0; q < 6; q++) rc.v[q] = 0;
+                rc.v[0] = cdeg;
+                rc.lo = 0; rc.hi = 0; rc.mn = kMaxLL;
+                block_reduce<BULK_WARPS, 6>(rc, s_v, s_lo, s_hi, s_mn);
                 if (tid == 0) {
                     p.mc_cnt = (long long)s_surv;
-                    p.mc_stage = (long long)(s_pack >> 40);
-                    p.mc_deg = (long long)(s_pack & ((1ull << 40) - 1));
+                    p.mc_stage = (long long)s_nst;
+                    p.mc_deg = rc.v[0];
                 }
             } else if (tid == 0) {
                 p.mc_cnt = 0;
@@ -596,21 +605,28 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         }
         for (long long t = tid; t < nc; t += BULK_THREADS) s_cs[t] = split_at(totArcs, c_lo + t, G);
         __syncthreads();
-        for (long long q = tid; q < myStage; q += BULK_THREADS) {
-            const long long gs = slotBase + q;
-            const long long off = A.stage_off[j0 + q];
-            const long long goff = arcBase + off;
-            A.fstart[gs] = A.stage_start[j0 + q];
-            A.fbase[gs] = goff;
-            const long long nxt = (q + 1 < myStage) ? A.stage_off[j0 + q + 1] : myDeg;
-            const long long gend = arcBase + nxt;
-            int lo = 0, hi = (int)nc;  // first consumer whose first arc is >= goff
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_cs[mid] < goff) lo = mid + 1;
-                else hi = mid;
+        // the staged entries' arc offsets: a block scan of their degrees
+        long long carry = 0;
+        for (long long q0 = 0; q0 < myStage; q0 += BULK_THREADS) {
+            const long long q = q0 + tid;
+            const long long deg = q < myStage ? A.stage_off[j0 + q] : 0;
+            long long chunk;
+            const long long off = carry + block_excl_scan<BULK_WARPS>(deg, s_scan, chunk);
+            carry += chunk;
+            if (q < myStage) {
+                const long long gs = slotBase + q;
+                const long long goff = arcBase + off;
+                const long long gend = goff + deg;
+                A.fstart[gs] = A.stage_start[j0 + q];
+                A.fbase[gs] = goff;
+                int lo = 0, hi = (int)nc;  // first consumer whose first arc is >= goff
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_cs[mid] < goff) lo = mid + 1;
+                    else hi = mid;
+                }
+                for (int t = lo; t < (int)nc && s_cs[t] < gend; t++) A.cstart[c_lo + t] = gs;
             }
-            for (int t = lo; t < (int)nc && s_cs[t] < gend; t++) A.cstart[c_lo + t] = gs;
         }
         if (b == 0 && tid == 0) A.fbase[U_stage] = totArcs;
         if (compact) {
@@ -622,8 +638,8 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 const bool keep = id >= 0;
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 if (bal) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(&s_surv, (unsigned long long)__popc(bal));
+                    unsigned base = 0;
+                    if (lane == 0) base = atomicAdd(&s_surv, (unsigned)__popc(bal));
                     base = __shfl_sync(0xffffffffu, base, 0);
                     if (keep) nlive[survBase + (long long)base + __popc(bal & ((1u << lane) - 1u))] = id;
                 }
@@ -666,7 +682,10 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                                   const int h = -cv - 1;
                                   const int p = pr[s_hub[h]];
                                   if (p > (int)i) {
-                                      atomicAdd(&s_hacc[h], (unsigned long long)c);
+                                      const unsigned cl = (unsigned)c;
+                                      const unsigned old = atomicAdd(&s_hlo[h], cl);
+                                      const unsigned ch = (unsigned)((unsigned long long)c >> 32) + (old + cl < old ? 1u : 0u);
+                                      if (ch) atomicAdd(&s_hhi[h], ch);
                                       nrem += 2;
                                   } else if (p == (int)i) {
                                       add128(ilo, ihi, (unsigned long long)c, 0);
@@ -679,10 +698,11 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         if (nh > 0) {  // one reduction per hub touched by this block
             __syncthreads();
             for (int h = tid; h < nh; h += BULK_THREADS) {
-                const unsigned long long a = s_hacc[h];
+                const unsigned long long a = ((unsigned long long)s_hhi[h] << 32) + s_hlo[h];
                 if (a) {
                     atomicAdd((unsigned long long *)&A.w[s_hub[h]], (unsigned long long)0 - a);
-                    s_hacc[h] = 0;
+                    s_hlo[h] = 0;
+                    s_hhi[h] = 0;
                 }
             }
         }
@@ -858,7 +878,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
 // itself from the same shared data: two block barriers per round.
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ TailAcc s_acc[2];
+    __shared__ TailAcc<TAIL_WARPS> s_acc[2];
     __shared__ long long s_w[TAIL_WARPS];
     __shared__ long long s_pref[TAIL_THREADS + 1];
 
@@ -889,10 +909,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
     st.scan = ctl->scan_volume;
     for (long long p = tid; p <= L; p += TAIL_THREADS) toff[p] = (int)A.tlrp[p];
     for (long long p = tid; p < LP; p += TAIL_THREADS) tw[p] = p < L ? A.w[live[p]] : -1;  // pads: gone
-    if (tid < 2) {
-        TailAcc z = TAIL_ACC_ZERO;
-        s_acc[tid] = z;
-    }
+    if (tid < 2) s_acc[tid].F = 0;
     __syncthreads();
     // round i reads the minima in buffer (i & 1): fill the first round's buffer
     long long *first = segbuf + ((st.round + 1) & 1) * nseg;
@@ -915,7 +932,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         const long long i = R.i;
         const long long *cur = segbuf + (i & 1) * nseg;  // minima at the start of round i
         long long *nxt = segbuf + ((i + 1) & 1) * nseg;  // minima after round i
-        TailAcc &acc = s_acc[i & 1];
+        TailAcc<TAIL_WARPS> &acc = s_acc[i & 1];
         // ---- select: lanes test segments in parallel; a candidate segment
         // is then scanned by its warp (two vertices per lane)
         unsigned long long wlo = 0, whi = 0;
@@ -972,15 +989,13 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         warp_sum128(wlo, whi);
         mins = warp_min64(mins);
         if (lane == 0) {
-            acc_add128(&acc.wlo, &acc.whi, wlo, whi);
-            if (mins != kMaxLL) atomicMin(&acc.mins, mins);
+            acc.wlo[wid] = wlo;
+            acc.whi[wid] = whi;
+            acc.mins[wid] = mins;
         }
         __syncthreads();
-        // round i+1's accumulator was last read in round i-1: reset it now
-        if (tid == 0) {
-            TailAcc z = TAIL_ACC_ZERO;
-            s_acc[(i + 1) & 1] = z;
-        }
+        // round i+1's counter was last read in round i-1: reset it now
+        if (tid == 0) s_acc[(i + 1) & 1].F = 0;
         const int F = (int)acc.F;
         // ---- expand
         unsigned long long ilo = 0, ihi = 0;
@@ -1073,12 +1088,15 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         warp_sum128(ilo, ihi);
         mind = warp_min64(mind);
         if (lane == 0) {
-            acc_add128(&acc.ilo, &acc.ihi, ilo, ihi);
-            if (mind != kMaxLL) atomicMin(&acc.mins, mind);
+            acc.ilo[wid] = ilo;
+            acc.ihi[wid] = ihi;
+            if (mind < acc.mins[wid]) acc.mins[wid] = mind;
         }
         __syncthreads();
         // ---- every warp: close round i and plan round i + 1 (same values everywhere)
-        const u128 wsel = mk128(acc.wlo, acc.whi), internal = mk128(acc.ilo, acc.ihi);
+        u128 wsel, internal;
+        long long mins_all;
+        tail_acc_sum(acc, wsel, internal, mins_all);
         st.f = st.f - (wsel - (internal >> 1));
         st.scan += L;
         st.size -= F;
@@ -1099,7 +1117,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, acc.mins);
+        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, mins_all);
     }
     __syncthreads();
     for (long long p = tid; p < L; p += TAIL_THREADS) {
@@ -1218,12 +1236,12 @@ DevGraph dev_graph(const dupin_graph *g, int metric) {
     return d;
 }
 
-// arcs the tail buffer must hold: the live sub-graph has at most
-// min(all arcs, |S| (|S| - 1)) (the tail may start after a small round
-// whatever its arc count)
+// Arcs the tail buffer holds: the live sub-graph has at most
+// min(all arcs, |S| (|S| - 1)) arcs, and the grid-wide rounds go on while it
+// has more than DUPIN_TAIL_BUF_ARCS.
 static long long tail_arc_buffer(long long arcs, const PeelPlan &plan) {
     const long long tc = plan.tail_cap;
-    return std::min<long long>(arcs, tc * (tc > 0 ? tc - 1 : 0));
+    return std::min<long long>(std::min<long long>(arcs, tc * (tc > 0 ? tc - 1 : 0)), DUPIN_TAIL_BUF_ARCS);
 }
 
 long long workspace_bytes(long long n, long long arcs, bool has_cw, const PeelPlan &plan, int grid) {
@@ -1250,7 +1268,7 @@ void workspace_free(PeelWorkspace *ws, cudaStream_t s) {
         if (ws->async) cudaFreeAsync(q, s);
         else cudaFree(q);
     }
-    for (int j = 0; j < 5; j++)
+    for (int j = 0; j < 6; j++)
         if (ws->ev[j]) cudaEventDestroy(ws->ev[j]);
     delete ws;
 }
@@ -1310,21 +1328,32 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
     return ws;
 }
 
-int workspace_ensure(dupin_graph *g, const PeelPlan &plan) {
-    PeelWorkspace *ws = g->ws;
+static int workspace_ensure_ref(dupin_graph *g, PeelWorkspace *&slot, const PeelPlan &plan) {
+    PeelWorkspace *ws = slot;
     const long long tarc = tail_arc_buffer(g->arcs, plan);
     if (ws && ws->tail_cap >= plan.tail_cap && ws->tr_cap >= plan.tr_cap && ws->tarc_cap >= tarc) return DUPIN_OK;
     PeelPlan big = plan;
     if (ws) {  // grow to cover both the old and the new caps
         big.tail_cap = std::max(plan.tail_cap, ws->tail_cap);
         big.tr_cap = std::max(plan.tr_cap, ws->tr_cap);
-        big.tail_arcs = std::max(tarc, ws->tarc_cap);
         workspace_free(ws);
-        g->ws = nullptr;
+        slot = nullptr;
     }
     int rc;
-    g->ws = workspace_create(g->n, g->arcs, g->cw != nullptr, big, false, 0, &rc);
+    slot = workspace_create(g->n, g->arcs, g->cw != nullptr, big, false, 0, &rc);
     return rc;
+}
+
+int workspace_ensure(dupin_graph *g, const PeelPlan &plan) { return workspace_ensure_ref(g, g->ws, plan); }
+
+PeelWorkspace *workspace_slot(dupin_graph *g, int k, const PeelPlan &plan, int *rc) {
+    if (k == 0) {
+        *rc = workspace_ensure(g, plan);
+        return *rc ? nullptr : g->ws;
+    }
+    if ((int)g->ws_more.size() < k) g->ws_more.resize(k, nullptr);
+    *rc = workspace_ensure_ref(g, g->ws_more[k - 1], plan);
+    return *rc ? nullptr : g->ws_more[k - 1];
 }
 
 static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const dupin_params *p,
@@ -1374,46 +1403,60 @@ __global__ void k_ctl_reset(PeelCtl *c) {
     *c = z;
 }
 
-int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
-                 cudaStream_t s) {
+int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
+                        int stages, cudaStream_t s) {
     PeelArgs A = make_args(g, ws, p, plan);
     const long long tail_cap = plan.tail_cap;
     const bool timing = (p->flags & DUPIN_TIMING) != 0;
     if (timing && !ws->ev[0]) {
-        for (int j = 0; j < 5; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
+        for (int j = 0; j < 6; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
     }
-    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[0], s));
-    k_ctl_reset<<<1, 1, 0, s>>>(ws->ctl);
-    int rc = launch_init_weights(A.g, p->metric, ws->w, ws->pr, ws->live0, ws->ctl, false, s);
-    if (rc) return rc;
-    k_init_finish<<<1, 1, 0, s>>>(A, g->n);
-    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[1], s));
-    if (g->n > tail_cap || g->arcs > A.tail_arcs) {
-        void *args[] = {&A};
-        cudaError_t e = cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(ws->grid), dim3(BULK_THREADS), args, 0, s);
-        if (e != cudaSuccess) return dupin_cuda_fail(e, "cooperative launch of k_peel_bulk");
+    int rc;
+    if (stages & PEEL_FRONT) {
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[0], s));
+        k_ctl_reset<<<1, 1, 0, s>>>(ws->ctl);
+        rc = launch_init_weights(A.g, p->metric, ws->w, ws->pr, ws->live0, ws->ctl, false, s);
+        if (rc) return rc;
+        k_init_finish<<<1, 1, 0, s>>>(A, g->n);
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[1], s));
+        if (g->n > tail_cap || g->arcs > A.tail_arcs) {
+            void *args[] = {&A};
+            cudaError_t e =
+                cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(ws->grid), dim3(BULK_THREADS), args, 0, s);
+            if (e != cudaSuccess) return dupin_cuda_fail(e, "cooperative launch of k_peel_bulk");
+        }
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
     }
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
-    DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tcnt, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
-    DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tfill, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
-    k_tail_prep<<<sms * 2, 256, 0, s>>>(A);
-    k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A, ws->tdeg, nullptr);
-    k_tail_arcs<0><<<sms * 2, BULK_THREADS, 0, s>>>(A);
-    // tcnt -> tlrp
-    PeelArgs A2 = A;
-    k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A2, ws->tlrp, ws->tcnt);
-    k_tail_arcs<1><<<sms * 2, BULK_THREADS, 0, s>>>(A);
-    rc = set_tail_smem();
-    if (rc) return rc;
-    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[3], s));
-    k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(tail_cap), s>>>(A);
-    if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[4], s));
+    if (stages & PEEL_BUILD) {
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[3], s));
+        DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tcnt, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
+        DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tfill, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
+        k_tail_prep<<<sms * 2, 256, 0, s>>>(A);
+        k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A, ws->tdeg, nullptr);
+        k_tail_arcs<0><<<sms * 2, BULK_THREADS, 0, s>>>(A);
+        // tcnt -> tlrp
+        PeelArgs A2 = A;
+        k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A2, ws->tlrp, ws->tcnt);
+        k_tail_arcs<1><<<sms * 2, BULK_THREADS, 0, s>>>(A);
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[4], s));
+    }
+    if (stages & PEEL_TAIL) {
+        rc = set_tail_smem();
+        if (rc) return rc;
+        k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(tail_cap), s>>>(A);
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[5], s));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return dupin_cuda_fail(e, "peel kernels");
     return DUPIN_OK;
+}
+
+int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
+                 cudaStream_t s) {
+    return enqueue_peel_stages(g, ws, p, plan, PEEL_ALL, s);
 }
 
 int peel_resolve(const dupin_graph *g, const dupin_params *p, PeelPlan *plan) {
@@ -1437,7 +1480,12 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
     r->tail_arcs = c.tail_arcs;
     for (int j = 0; j < 4; j++) r->phase_ms[j] = 0.f;
     if ((p->flags & DUPIN_TIMING) && ws->ev[0]) {
-        for (int j = 0; j < 4; j++) cudaEventElapsedTime(&r->phase_ms[j], ws->ev[j], ws->ev[j + 1]);
+        // init, grid-wide rounds, tail build, tail (the build may start later than
+        // the grid-wide rounds end when several peels run together)
+        cudaEventElapsedTime(&r->phase_ms[0], ws->ev[0], ws->ev[1]);
+        cudaEventElapsedTime(&r->phase_ms[1], ws->ev[1], ws->ev[2]);
+        cudaEventElapsedTime(&r->phase_ms[2], ws->ev[3], ws->ev[4]);
+        cudaEventElapsedTime(&r->phase_ms[3], ws->ev[4], ws->ev[5]);
     }
     if (c.error) {
         const char *why = c.error == DUPIN_ERR_NO_PROGRESS ? "max_rounds reached before the set became empty"

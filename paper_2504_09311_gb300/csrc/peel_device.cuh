@@ -145,15 +145,48 @@ struct RoundState {
 
 
 // Shared accumulator of one tail round (double-buffered by round parity).
+// F is a 32-bit shared counter; the sums are written per warp by its lane 0
+// and added up by every thread when it closes the round: shared-memory
+// atomics on 64-bit words are compare-and-swap loops that collapse when
+// several warps hit one word.
+template <int NW>
 struct TailAcc {
-    unsigned long long wlo, whi;  // sum of the removed vertices' weights
-    unsigned long long ilo, ihi;  // sum of c over arcs inside U
-    long long mins;               // minimum live weight after the round
-    unsigned int F;               // |U_i|
-    unsigned int pad;
+    unsigned F;                          // |U_i|
+    unsigned long long wlo[NW], whi[NW];  // sum of the removed vertices' weights
+    unsigned long long ilo[NW], ihi[NW];  // sum of c over arcs inside U
+    long long mins[NW];                   // minimum live weight after the round
 };
 
-#define TAIL_ACC_ZERO {0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0}
+// the round's totals from the warps' parts: lane j < NW loads part j and a
+// butterfly over the lanes leaves the totals in every lane (NW a power of
+// two, <= 32)
+template <int NW>
+__device__ __forceinline__ void tail_acc_sum(const TailAcc<NW> &acc, u128 &wsel, u128 &internal, long long &mins) {
+    static_assert(NW > 0 && NW <= 32 && (NW & (NW - 1)) == 0, "warps per block: a power of two");
+    const int lane = threadIdx.x & 31;
+    const bool in = lane < NW;
+    unsigned long long wl = in ? acc.wlo[lane] : 0, wh = in ? acc.whi[lane] : 0;
+    unsigned long long il = in ? acc.ilo[lane] : 0, ih = in ? acc.ihi[lane] : 0;
+    long long m = in ? acc.mins[lane] : 0x7fffffffffffffffLL;
+#pragma unroll
+    for (int d = 1; d < NW; d <<= 1) {
+        const unsigned long long owl = __shfl_xor_sync(0xffffffffu, wl, d), owh = __shfl_xor_sync(0xffffffffu, wh, d);
+        const unsigned long long oil = __shfl_xor_sync(0xffffffffu, il, d), oih = __shfl_xor_sync(0xffffffffu, ih, d);
+        const long long om = __shfl_xor_sync(0xffffffffu, m, d);
+        add128(wl, wh, owl, owh);
+        add128(il, ih, oil, oih);
+        m = om < m ? om : m;
+    }
+    // lanes 0 .. NW-1 hold the totals (a power-of-two NW); broadcast lane 0's
+    wl = __shfl_sync(0xffffffffu, wl, 0);
+    wh = __shfl_sync(0xffffffffu, wh, 0);
+    il = __shfl_sync(0xffffffffu, il, 0);
+    ih = __shfl_sync(0xffffffffu, ih, 0);
+    m = __shfl_sync(0xffffffffu, m, 0);
+    wsel = mk128(wl, wh);
+    internal = mk128(il, ih);
+    mins = m;
+}
 
 // The parameters of one round, computed identically by every warp.
 struct TailRound {
@@ -165,15 +198,6 @@ struct TailRound {
     int minrule;                  // threshold selects nobody: take the minimum
     int done;                     // S is empty
 };
-
-__device__ __forceinline__ void acc_add128(unsigned long long *lo, unsigned long long *hi, unsigned long long xlo,
-                                           unsigned long long xhi) {
-    if (xlo) {
-        unsigned long long old = atomicAdd(lo, xlo);
-        if (old + xlo < old) xhi += 1;
-    }
-    if (xhi) atomicAdd(hi, xhi);
-}
 
 #define TAIL_FAST 32
 #define TAIL_SEG 64  // vertices per segment (one warp, two per lane)

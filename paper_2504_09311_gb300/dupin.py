@@ -280,7 +280,23 @@ def peel_device(g: Graph, params: Params, peel_round=None, best_mask=None, strea
     return r
 
 
-def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=True, want_trace=False, stream=None):
+def peel_batch_device(graphs: Sequence[Graph], params: Sequence[Params], peel_rounds, best_masks, stream=None):
+    """dupin_peel_batch writing each peel_round / best_mask into its own device tensor
+    (DUPIN_RESULT_DEVICE); returns the Result array (host scalars)."""
+    k = len(graphs)
+    G = (ctypes.c_void_p * k)(*[g.handle.value for g in graphs])
+    P = (Params * k)(*params)
+    R = (Result * k)()
+    for j in range(k):
+        P[j].flags |= RESULT_DEVICE
+        R[j] = _result_struct(peel_rounds[j], best_masks[j], None, 0)
+    check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
+                                 ctypes.cast(R, ctypes.c_void_p), k, _stream(stream)))
+    return R
+
+
+def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=True, want_trace=False, stream=None,
+               want_mask=False):
     """dupin_peel_batch with host result buffers; returns a list of PeelOutput."""
     k = len(graphs)
     G = (ctypes.c_void_p * k)(*[g.handle.value for g in graphs])
@@ -289,17 +305,18 @@ def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=Tr
     keep = []
     for j, g in enumerate(graphs):
         pr = np.empty(g.n, np.int32) if want_rounds else None
+        mk = np.empty(g.n, np.uint8) if want_mask else None
         trace = None
         cap = 0
         if want_trace:
             cap = g.n + 2
             trace = (np.zeros(cap, np.int64), np.zeros(cap, np.uint64), np.zeros(cap, np.int64),
                      np.zeros(cap, np.int64))
-        R[j] = _result_struct(pr, None, trace, cap)
-        keep.append((pr, trace))
+        R[j] = _result_struct(pr, mk, trace, cap)
+        keep.append((pr, mk, trace))
     check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
                                  ctypes.cast(R, ctypes.c_void_p), k, _stream(stream)))
-    return [_output(R[j], keep[j][0], None, keep[j][1]) for j in range(k)]
+    return [_output(R[j], keep[j][0], keep[j][1], keep[j][2]) for j in range(k)]
 
 
 def peel_noalloc(n, row_ptr, col_idx, arc_w, vertex_w, params: Params, peel_round, best_mask=None, trace=None,

@@ -76,6 +76,50 @@ def test_batch_equals_single(dupin):
         dg.free()
 
 
+def test_batch_large_concurrent(dupin):
+    """Several large peels in one call -- one graph under three eps, another
+    under two settings, with a small graph mixed in -- run their grid-wide
+    stages in turn and their tails side by side; every result equals its own
+    dupin_peel (host results, then device results)."""
+    import torch
+
+    big1 = synth.bipartite_zipf(200_000, 100_000, 900_000, 1.8, 2, 60, 60, 0.4, 10, seed=11)
+    big1.c = synth.fd_weights(big1)
+    big2 = synth.rmat_weighted(19, 8, "dw", seed=5)
+    small = synth.transaction_window(30000, seed=12)
+    gs = [big1, big1, big2, small, big1, big2]
+    dg1, dg2, dgs_ = dupin.Graph.from_synth(big1), dupin.Graph.from_synth(big2), dupin.Graph.from_synth(small)
+    dgs = [dg1, dg1, dg2, dgs_, dg1, dg2]
+    ps = [dupin.make_params("fd", 1, (0, 1)), dupin.make_params("fd", 1, (1, 20)),
+          dupin.make_params("dw", 1, (1, 10)), dupin.make_params("fd", 1, (1, 10)),
+          dupin.make_params("fd", 1, (1, 5)), dupin.make_params("dw", 2, (1, 10), flags=dupin.GPO)]
+    outs = dupin.peel_batch(dgs, ps, want_rounds=True, want_trace=True)
+    refs = [dupin.peel(dg, p.metric, p.k_mult, (p.eps_num, p.eps_den), flags=p.flags) for dg, p in zip(dgs, ps)]
+    for j in range(len(gs)):
+        same(outs[j], refs[j], j)
+    # device-resident results through the same path
+    k = len(gs)
+    prs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in gs]
+    mks = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for g in gs]
+    P = (dupin.Params * k)()
+    R = (dupin.Result * k)()
+    G = (ctypes.c_void_p * k)(*[dg.handle.value for dg in dgs])
+    for j in range(k):
+        P[j] = ps[j]
+        P[j].flags |= dupin.RESULT_DEVICE
+        R[j].peel_round = prs[j].data_ptr()
+        R[j].best_mask = mks[j].data_ptr()
+    dupin.check(dupin.lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
+                                             ctypes.cast(R, ctypes.c_void_p), k, None))
+    torch.cuda.synchronize()
+    for j in range(k):
+        assert np.array_equal(prs[j].cpu().numpy(), refs[j].peel_round), j
+        assert np.array_equal(mks[j].cpu().numpy(), refs[j].best_mask), j
+        assert R[j].best_round == refs[j].best_round and R[j].n_rounds == refs[j].n_rounds, j
+    for dg in (dg1, dg2, dgs_):
+        dg.free()
+
+
 def test_batch_repeated_graph_and_device_results(dupin):
     import torch
 
