@@ -39,6 +39,11 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "fd_2Mx1M_40M": dict(metric="fd", eps=[(0, 1), (1, 20), (1, 5)], k=1),
     "rmat24_dw": dict(metric="dw", eps=[(1, 10)], k=1),
+    "rmat24_dg": dict(metric="dg", eps=[(1, 10)], k=1),
+    "rmat24_fd": dict(metric="fd", eps=[(1, 10)], k=1),
+    # R-MAT scale 22 (4.2M vertices, ~65M edges): the profiling case of the R-MAT runs
+    "rmat22_dg": dict(metric="dg", eps=[(1, 10)], k=1),
+    "rmat22_fd": dict(metric="fd", eps=[(1, 10)], k=1),
     "dg_block_10kx5k": dict(metric="dg", eps=[(1, 10)], k=1),
     # the FD generator at a quarter of the size: the profiling case (arcs still exceed L2)
     "fd_500kx250k_8M": dict(metric="fd", eps=[(0, 1), (1, 20), (1, 5)], k=1),
@@ -50,8 +55,9 @@ def make_graph(name: str):
 
     if name == "fd_2Mx1M_40M":
         return synth.fd_camouflage(seed=1)
-    if name == "rmat24_dw":
-        return synth.rmat_weighted(24, 16, "dw", seed=1)
+    if name.startswith("rmat"):
+        scale, metric = name[len("rmat"):].split("_")
+        return synth.rmat_weighted(int(scale), 16, metric, seed=1)
     if name == "dg_block_10kx5k":
         return synth.dg_planted_block(seed=1)
     if name == "fd_500kx250k_8M":

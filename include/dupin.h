@@ -133,7 +133,7 @@ typedef struct {
     int64_t tail_arc_cap; /* <= 0: automatic (2^16); else, once |S| <= tail_cap, the
                              one CTA takes over when the live sub-graph has at most
                              this many arcs (2 |E(S)|) or after a round that removed
-                             at most 64 vertices (if it has at most 2^25 arcs),
+                             at most 64 vertices (if it has at most 2^27 arcs),
                              whichever comes first */
 } dupin_params;
 

@@ -606,7 +606,8 @@ static cudaStream_t tail_stream(int dev, size_t q) {
 }
 
 // Several peels of large graphs (or of one graph under several parameter
-// sets).  The grid-wide stages run one after another on 'stream' (each is a
+// sets).  The initial weights are computed once per graph and metric; the
+// grid-wide stages run one after another on 'stream' (each is a
 // cooperative launch over the whole GPU); then each peel's tail sub-graph is
 // built on 'stream' and its one-CTA tail runs on a stream of its own, so the
 // latency-bound tails, one SM each, run side by side.  No tail overlaps a
@@ -633,8 +634,17 @@ static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params 
         ws[q] = workspace_slot(g, uses[g]++, plans[q], &rc);
         if (rc) return fail_at(q, rc);
     }
+    // initial weights: once per (graph, metric); the other peels of the pair
+    // copy them (before any grid-wide round changes them)
     for (size_t q = 0; q < k; q++) {
-        int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_FRONT, s);
+        const PeelWorkspace *from = nullptr;
+        for (size_t q2 = 0; q2 < q && !from; q2++)
+            if (graphs[idx[q2]] == graphs[idx[q]] && params[idx[q2]].metric == params[idx[q]].metric) from = ws[q2];
+        int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_INIT, s, from);
+        if (rc) return fail_at(q, rc);
+    }
+    for (size_t q = 0; q < k; q++) {
+        int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s);
         if (rc) return fail_at(q, rc);
     }
     std::vector<cudaEvent_t> ev(2 * k, nullptr);

@@ -27,8 +27,8 @@ typedef unsigned __int128 u128;
 // once S fits the one-CTA tail, the tail takes over after such a round
 // whatever the live arc count.
 #define DUPIN_TAIL_SMALL_ROUND 64
-// ... provided its live sub-graph fits the tail's arc buffer (2^25 arcs)
-#define DUPIN_TAIL_BUF_ARCS (1LL << 25)
+// ... provided its live sub-graph fits the tail's arc buffer (2^27 arcs)
+#define DUPIN_TAIL_BUF_ARCS (1LL << 27)
 
 // Peeling phases recorded in PeelCtl::status
 #define ST_RUNNING 0
@@ -248,14 +248,15 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p) {
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
 
 // Grid-wide barrier for a cooperative launch (every block resident).
-// ctl->bar_count counts the arrivals since the control block was reset, so
-// barrier number e (e = 1, 2, ... in every block) is complete once it reaches
-// e * nblocks: one release-add to arrive and acquire loads to wait, with no
-// reset step between barriers.  The error flag is read alongside.  Waiting
-// is bounded: after DUPIN_SPIN_LIMIT polls the block records
+// ctl->bar_count counts the arrivals since the control block was reset; a
+// barrier is complete once it reaches the running total of the block counts
+// of all barriers so far (kept by the caller, advanced here by nblocks;
+// thread 0's copy is the one used).  One release-add to arrive and acquire
+// loads to wait, with no reset step between barriers; the error flag is read
+// alongside.
+// Waiting is bounded: after DUPIN_SPIN_LIMIT polls the block records
 // DUPIN_ERR_TIMEOUT and every block leaves at its next barrier.  Returns
-// false when the peel must stop.  'epoch' is the caller's count of barriers
-// passed (used by thread 0 only).
+// false when the peel must stop.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -268,12 +269,12 @@ __device__ __forceinline__ unsigned atom_add_release_u32(unsigned *p, unsigned x
     return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(PeelCtl *ctl, unsigned nblocks, unsigned &epoch) {
+__device__ __forceinline__ bool grid_barrier(PeelCtl *ctl, unsigned nblocks, unsigned &target_acc) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        epoch++;
-        const unsigned target = epoch * nblocks;  // wraps consistently with the counter
+        target_acc += nblocks;
+        const unsigned target = target_acc;  // wraps consistently with the counter
         __threadfence();  // the block's writes (ordered by the block barrier) before the arrival
         unsigned v = atom_add_release_u32(&ctl->bar_count, 1u) + 1u;
         int err = ld_volatile_i32(&ctl->error);

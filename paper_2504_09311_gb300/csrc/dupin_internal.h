@@ -45,9 +45,9 @@ struct PeelWorkspace {
     long long *tcw = nullptr;
     uint8_t *mask = nullptr;
     bool async = false;  // allocated with cudaMallocAsync (freed with cudaFreeAsync)
-    // DUPIN_TIMING: front start, init done, grid-wide rounds done, build start,
-    // build done, tail done
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // DUPIN_TIMING: init start, init done, grid-wide rounds start and done,
+    // build start and done, tail done
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     long long bytes = 0;
 };
 
@@ -85,12 +85,15 @@ PeelWorkspace *workspace_slot(dupin_graph *g, int k, const PeelPlan &plan, int *
 int peel_resolve(const dupin_graph *g, const dupin_params *p, PeelPlan *plan);
 int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
                  cudaStream_t s);
-// The stages of one peel: PEEL_FRONT = control reset, initial weights and the
-// grid-wide rounds (a cooperative launch over the whole GPU), PEEL_BUILD = the
-// tail sub-graph, PEEL_TAIL = the one-CTA rounds.
-enum { PEEL_FRONT = 1, PEEL_BUILD = 2, PEEL_TAIL = 4, PEEL_ALL = 7 };
+// The stages of one peel: PEEL_INIT = control reset and initial weights,
+// PEEL_BULK = the grid-wide rounds (a cooperative launch over the whole GPU),
+// PEEL_BUILD = the tail sub-graph, PEEL_TAIL = the one-CTA rounds.
+enum { PEEL_INIT = 1, PEEL_BUILD = 2, PEEL_TAIL = 4, PEEL_BULK = 8, PEEL_FRONT = 9, PEEL_ALL = 15 };
+// 'init_from' (stage PEEL_INIT only): a workspace whose initial weights for
+// the same graph and metric are already computed on this stream and not yet
+// changed by its grid-wide rounds; they are copied instead of recomputed.
 int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
-                        int stages, cudaStream_t s);
+                        int stages, cudaStream_t s, const PeelWorkspace *init_from = nullptr);
 int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, dupin_result *r, cudaStream_t s);
 
 // kernels shared by loading and peeling

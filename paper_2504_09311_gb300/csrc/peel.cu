@@ -77,7 +77,8 @@ __global__ void k_init_vertex(DevGraph g, int dg, long long *w, int *pr, int *li
 // 32-arc chunks, finds each arc's row from 32 cached row ends (5 shuffle
 // steps), reduces rows within the chunk with a segmented scan and keeps the
 // open last row in registers, so a row spanning many chunks is flushed once
-// per warp.  CHECK also validates ids, self-loops and int64 overflow.
+// per warp.  The loads of INIT_UNROLL chunks are issued together.  CHECK
+// also validates ids, self-loops and int64 overflow.
 template <bool CHECK>
 __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long long *w, PeelCtl *ctl) {
     const int lane = threadIdx.x & 31;
@@ -92,22 +93,20 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
     bool bad = false;
     long long r_end = g.rp[r + 1];  // end of row r
     long long lacc = 0;             // per-lane partial sum of row r over whole-row chunks
-    for (long long x0 = we0; x0 < we1; x0 += 32) {
+    // one 32-arc chunk whose weights (and, with CHECK, heads) are already loaded
+    auto chunk = [&](const long long x0, const long long val, const int cvx) {
         const long long x = x0 + lane;
         const bool valid = x < we1;
-        long long val = 0;
-        if (valid) val = g.cw[x];
         if (CHECK && valid) {
-            int v = g.col[x];
-            if (v < 0 || v >= n || val < 0) bad = true;
+            if (cvx < 0 || cvx >= n || val < 0) bad = true;
         }
         // fast path: the whole chunk lies in row r (long rows, hubs)
         const long long cend = x0 + 32 < we1 ? x0 + 32 : we1;
         if (cend <= r_end) {
-            if (CHECK && valid && g.col[x] == r) bad = true;  // self-loop
+            if (CHECK && valid && cvx == r) bad = true;  // self-loop
             if (CHECK && (unsigned long long)lacc + (unsigned long long)val < (unsigned long long)lacc) bad = true;
             lacc += val;
-            continue;
+            return;
         }
         // leaving row r inside this chunk: fold the lanes' partials into the carry
         {
@@ -148,7 +147,7 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
             if (!__any_sync(0xffffffffu, owner < 0)) break;
             rr += 32;
         }
-        if (CHECK && valid && g.col[x] == owner) bad = true;
+        if (CHECK && valid && cvx == owner) bad = true;
         // segmented inclusive scan by owner
         long long sv = val;
 #pragma unroll
@@ -193,6 +192,20 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init_arcs(DevGraph g, long lon
         carry_own = oL;
         r = oL;  // the next chunk starts in this row or later
         r_end = g.rp[r + 1];
+    };
+    // INIT_UNROLL chunks per step: their loads are issued before any is processed
+    for (long long xb = we0; xb < we1; xb += 32 * INIT_UNROLL) {
+        long long vals[INIT_UNROLL];
+        int cvs[INIT_UNROLL];
+#pragma unroll
+        for (int u = 0; u < INIT_UNROLL; u++) {
+            const long long x = xb + 32 * u + lane;
+            vals[u] = x < we1 ? g.cw[x] : 0;
+            cvs[u] = (CHECK && x < we1) ? g.col[x] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < INIT_UNROLL; u++)
+            if (xb + 32 * u < we1) chunk(xb + 32 * u, vals[u], cvs[u]);
     }
     {
         long long sum = warp_sum64(lacc);
@@ -317,7 +330,7 @@ __device__ __forceinline__ void stage_entry(const PeelArgs &A, long long j0, boo
     }
 }
 
-__global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
+__global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
     __shared__ long long s_v[BULK_WARPS][6];
     __shared__ unsigned long long s_lo[BULK_WARPS], s_hi[BULK_WARPS];
     __shared__ long long s_mn[BULK_WARPS];
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
         s_hlo[h] = 0;
         s_hhi[h] = 0;
     }
-    unsigned epoch = 0;  // grid barriers passed
+    unsigned bar_target = 0;  // running total of the arrivals the grid barriers wait for
     if (tid == 0) {
         RoundState &st = s_st;
         st.round = ctl->round;
@@ -499,7 +512,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 p.mc_deg = 0;
             }
         }
-        if (!grid_barrier(ctl, G, epoch)) return;
+        if (!grid_barrier(ctl, G, bar_target)) return;
         // ---------------- phase B (part 1): totals and this block's offsets
         long long myStage, myDeg, myCand = 0;
         {
@@ -645,54 +658,82 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 }
             }
         }
-        if (!grid_barrier(ctl, G, epoch)) return;
+        if (!grid_barrier(ctl, G, bar_target)) return;
 
         // ---------------- phase C: expand
-        long long mindec = kMaxLL;
+        // The block walks an equal share [E0, E1) of the round's arcs through
+        // windows of WALK_WIN frontier entries in shared memory; each thread
+        // takes BULK_ILP arcs at a time and issues their loads together.
         unsigned long long ilo = 0, ihi = 0;
         long long nrem = 0;  // 2 per arc from U to S \ U, 1 per arc inside U
         if (totArcs > 0) {
             const long long E0 = split_at(totArcs, b, G);
             const long long E1 = split_at(totArcs, b + 1, G);
-            if (E0 < E1) {
-                const long long k0 = A.cstart[b];
-                const long long *fb = A.fbase;
-                const long long *fs = A.fstart;
-                const int *col = g.col;
-                const long long *cw = g.cw;
-                int *pr = A.pr;
-                long long *w = A.w;
-                walk_arcs([=](long long k) { return fb[k]; },
-                          [=](long long k) { return fs[k]; }, U_stage, E0, E1, k0, s_base, s_start,
-                          [&](long long k, long long pos) {
-                              (void)k;
-                              const int cv = col[pos];
-                              const long long c = dg ? DUPIN_Q_ONE : cw[pos];
-                              if (cv >= 0) {
-                                  const int p = pr[cv];
-                                  if (p > (int)i) {
-                                      // result unused: a fire-and-forget reduction
-                                      atomicAdd((unsigned long long *)&w[cv], (unsigned long long)(-c));
-                                      nrem += 2;
-                                  } else if (p == (int)i) {
-                                      add128(ilo, ihi, (unsigned long long)c, 0);
-                                      nrem++;
-                                  }
-                              } else {  // hub head: aggregate in shared memory
-                                  const int h = -cv - 1;
-                                  const int p = pr[s_hub[h]];
-                                  if (p > (int)i) {
-                                      const unsigned cl = (unsigned)c;
-                                      const unsigned old = atomicAdd(&s_hlo[h], cl);
-                                      const unsigned ch = (unsigned)((unsigned long long)c >> 32) + (old + cl < old ? 1u : 0u);
-                                      if (ch) atomicAdd(&s_hhi[h], ch);
-                                      nrem += 2;
-                                  } else if (p == (int)i) {
-                                      add128(ilo, ihi, (unsigned long long)c, 0);
-                                      nrem++;
-                                  }
-                              }
-                          });
+            const long long *fb = A.fbase;
+            const long long *fs = A.fstart;
+            const int *col = g.col;
+            const long long *cw = g.cw;
+            int *pr = A.pr;
+            long long *w = A.w;
+            long long e = E0, kk = E0 < E1 ? A.cstart[b] : 0;
+            while (e < E1) {  // block-uniform
+                __syncthreads();
+                for (int t = tid; t <= WALK_WIN; t += BULK_THREADS) {
+                    const long long idx = kk + t;
+                    s_base[t] = idx <= U_stage ? fb[idx] : kMaxLL;
+                    s_start[t] = idx < U_stage ? fs[idx] : 0;
+                }
+                __syncthreads();
+                const long long wend = s_base[WALK_WIN];
+                const long long hi = E1 < wend ? E1 : wend;
+                for (long long xb = e + tid; xb < hi; xb += (long long)BULK_ILP * BULK_THREADS) {
+                    long long pos[BULK_ILP];
+#pragma unroll
+                    for (int u = 0; u < BULK_ILP; u++) {
+                        const long long x = xb + (long long)u * BULK_THREADS;
+                        const int t = smem_last_le_fixed(s_base, x);
+                        pos[u] = x < hi ? s_start[t] + (x - s_base[t]) : -1;
+                    }
+                    int cv[BULK_ILP];
+                    long long cc[BULK_ILP];
+#pragma unroll
+                    for (int u = 0; u < BULK_ILP; u++) {
+                        if (pos[u] >= 0) {
+                            cv[u] = col[pos[u]];
+                            cc[u] = dg ? DUPIN_Q_ONE : cw[pos[u]];
+                        }
+                    }
+                    int pp[BULK_ILP];
+#pragma unroll
+                    for (int u = 0; u < BULK_ILP; u++)
+                        if (pos[u] >= 0) pp[u] = pr[cv[u] >= 0 ? cv[u] : s_hub[-cv[u] - 1]];
+#pragma unroll
+                    for (int u = 0; u < BULK_ILP; u++) {
+                        if (pos[u] < 0) continue;
+                        const int p = pp[u];
+                        const long long c = cc[u];
+                        if (p > (int)i) {
+                            const int cvu = cv[u];
+                            if (cvu >= 0) {
+                                // result unused: a fire-and-forget reduction
+                                atomicAdd((unsigned long long *)&w[cvu], (unsigned long long)(-c));
+                            } else {  // hub head: aggregate in shared memory
+                                const int h = -cvu - 1;
+                                const unsigned cl = (unsigned)c;
+                                const unsigned old = atomicAdd(&s_hlo[h], cl);
+                                const unsigned ch =
+                                    (unsigned)((unsigned long long)c >> 32) + (old + cl < old ? 1u : 0u);
+                                if (ch) atomicAdd(&s_hhi[h], ch);
+                            }
+                            nrem += 2;
+                        } else if (p == (int)i) {
+                            add128(ilo, ihi, (unsigned long long)c, 0);
+                            nrem++;
+                        }
+                    }
+                }
+                kk += smem_last_le(s_base, WALK_WIN + 1, hi);
+                e = hi;
             }
         }
         if (nh > 0) {  // one reduction per hub touched by this block
@@ -710,7 +751,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
             BlockRed<BULK_WARPS, 6> r;
             for (int j = 0; j < 6; j++) r.v[j] = 0;
             r.v[0] = nrem;
-            r.lo = ilo; r.hi = ihi; r.mn = mindec;
+            r.lo = ilo; r.hi = ihi; r.mn = kMaxLL;
             block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
             if (tid == 0) {
                 A.part[b].in_lo = r.lo;
@@ -719,7 +760,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 2) k_peel_bulk(PeelArgs A) {
                 A.part[b].rem_cnt = r.v[0];
             }
         }
-        if (!grid_barrier(ctl, G, epoch)) return;
+        if (!grid_barrier(ctl, G, bar_target)) return;
 
         // ---------------- phase D: close the round (every block)
         {
@@ -1268,7 +1309,7 @@ void workspace_free(PeelWorkspace *ws, cudaStream_t s) {
         if (ws->async) cudaFreeAsync(q, s);
         else cudaFree(q);
     }
-    for (int j = 0; j < 6; j++)
+    for (int j = 0; j < 7; j++)
         if (ws->ev[j]) cudaEventDestroy(ws->ev[j]);
     delete ws;
 }
@@ -1403,35 +1444,64 @@ __global__ void k_ctl_reset(PeelCtl *c) {
     *c = z;
 }
 
+// A follower of a batched call: the initial weights of the same graph and
+// metric copied from another workspace, the live state set up as the
+// initial-weight kernels would, and the sums f(V) and min w copied.
+__global__ void k_init_follow(long long n, const long long *src_w, long long *w, int *pr, int *live0) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+        w[u] = src_w[u];
+        pr[u] = DUPIN_LIVE;
+        live0[u] = (int)u;
+    }
+}
+
+__global__ void k_init_follow_ctl(const PeelCtl *src, PeelCtl *dst) {
+    dst->init_lo = src->init_lo;
+    dst->init_hi = src->init_hi;
+    dst->init_min = src->init_min;
+    dst->init_overflow = src->init_overflow;
+}
+
 int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
-                        int stages, cudaStream_t s) {
+                        int stages, cudaStream_t s, const PeelWorkspace *init_from) {
     PeelArgs A = make_args(g, ws, p, plan);
     const long long tail_cap = plan.tail_cap;
     const bool timing = (p->flags & DUPIN_TIMING) != 0;
     if (timing && !ws->ev[0]) {
-        for (int j = 0; j < 6; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
+        for (int j = 0; j < 7; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
     }
     int rc;
-    if (stages & PEEL_FRONT) {
+    if (stages & PEEL_INIT) {
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[0], s));
         k_ctl_reset<<<1, 1, 0, s>>>(ws->ctl);
-        rc = launch_init_weights(A.g, p->metric, ws->w, ws->pr, ws->live0, ws->ctl, false, s);
-        if (rc) return rc;
+        if (init_from) {
+            int sms = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            k_init_follow<<<sms * 8, 256, 0, s>>>(g->n, init_from->w, ws->w, ws->pr, ws->live0);
+            k_init_follow_ctl<<<1, 1, 0, s>>>(init_from->ctl, ws->ctl);
+        } else {
+            rc = launch_init_weights(A.g, p->metric, ws->w, ws->pr, ws->live0, ws->ctl, false, s);
+            if (rc) return rc;
+        }
         k_init_finish<<<1, 1, 0, s>>>(A, g->n);
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[1], s));
+    }
+    if (stages & PEEL_BULK) {
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
         if (g->n > tail_cap || g->arcs > A.tail_arcs) {
             void *args[] = {&A};
             cudaError_t e =
                 cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(ws->grid), dim3(BULK_THREADS), args, 0, s);
             if (e != cudaSuccess) return dupin_cuda_fail(e, "cooperative launch of k_peel_bulk");
         }
-        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[3], s));
     }
     if (stages & PEEL_BUILD) {
         int sms = 0, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[3], s));
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[4], s));
         DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tcnt, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
         DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tfill, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
         k_tail_prep<<<sms * 2, 256, 0, s>>>(A);
@@ -1441,13 +1511,13 @@ int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_par
         PeelArgs A2 = A;
         k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A2, ws->tlrp, ws->tcnt);
         k_tail_arcs<1><<<sms * 2, BULK_THREADS, 0, s>>>(A);
-        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[4], s));
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[5], s));
     }
     if (stages & PEEL_TAIL) {
         rc = set_tail_smem();
         if (rc) return rc;
         k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(tail_cap), s>>>(A);
-        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[5], s));
+        if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[6], s));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return dupin_cuda_fail(e, "peel kernels");
@@ -1480,12 +1550,12 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
     r->tail_arcs = c.tail_arcs;
     for (int j = 0; j < 4; j++) r->phase_ms[j] = 0.f;
     if ((p->flags & DUPIN_TIMING) && ws->ev[0]) {
-        // init, grid-wide rounds, tail build, tail (the build may start later than
-        // the grid-wide rounds end when several peels run together)
+        // init, grid-wide rounds, tail build, tail (the stages of several peels
+        // run together interleave, so each has its own start event)
         cudaEventElapsedTime(&r->phase_ms[0], ws->ev[0], ws->ev[1]);
-        cudaEventElapsedTime(&r->phase_ms[1], ws->ev[1], ws->ev[2]);
-        cudaEventElapsedTime(&r->phase_ms[2], ws->ev[3], ws->ev[4]);
-        cudaEventElapsedTime(&r->phase_ms[3], ws->ev[4], ws->ev[5]);
+        cudaEventElapsedTime(&r->phase_ms[1], ws->ev[2], ws->ev[3]);
+        cudaEventElapsedTime(&r->phase_ms[2], ws->ev[4], ws->ev[5]);
+        cudaEventElapsedTime(&r->phase_ms[3], ws->ev[5], ws->ev[6]);
     }
     if (c.error) {
         const char *why = c.error == DUPIN_ERR_NO_PROGRESS ? "max_rounds reached before the set became empty"

@@ -3,11 +3,17 @@
 #pragma once
 #include "dupin_common.cuh"
 
-#define BULK_THREADS 512
+#define BULK_THREADS 1024
 #define BULK_WARPS (BULK_THREADS / 32)
 #define WALK_WIN 1024
+#ifndef BULK_ILP
+#define BULK_ILP 1  // arcs in flight per thread in the grid-wide expand (1 measured best)
+#endif
 #define INIT_THREADS 256
 #define INIT_WARPS (INIT_THREADS / 32)
+#ifndef INIT_UNROLL
+#define INIT_UNROLL 4  // 32-arc chunks whose loads a warp issues together in the initial weights
+#endif
 #ifndef TAIL_THREADS
 #define TAIL_THREADS 256
 #endif
@@ -89,6 +95,17 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long *s_w
     total = s_w[NWARPS - 1];
     __syncthreads();
     return before + incl - x;
+}
+
+// last t in [0, WALK_WIN] with s[t] <= x (s non-decreasing, s[0] <= x):
+// a fixed number of predicated steps, so that several searches interleave
+__device__ __forceinline__ int smem_last_le_fixed(const long long *s, long long x) {
+    static_assert((WALK_WIN & (WALK_WIN - 1)) == 0, "WALK_WIN: a power of two");
+    int t = 0;
+#pragma unroll
+    for (int step = WALK_WIN; step > 0; step >>= 1)
+        if (t + step <= WALK_WIN && s[t + step] <= x) t += step;
+    return t;
 }
 
 // last t in [0, n) with s[t] <= x (s non-decreasing, s[0] <= x)
