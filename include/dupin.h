@@ -29,6 +29,9 @@
  *   - Candidates for the best set are S_0 .. S_{R-1} (non-empty); ties keep
  *     the earliest round (Algorithm 1's strict ">").
  *   - DUPIN_GPO adds Algorithm 3's global threshold tau_max.
+ *   - DUPIN_LPO adds Algorithm 4's local trims: after every round, while some
+ *     live w_u < g(S), a trim round removes {u : w_u < max(tau_max, g(S))};
+ *     each trim is a round of its own (peel_round, trace, best candidate).
  *
  * Conventions for every function:
  *   - returns DUPIN_OK (0) or a negative DUPIN_ERR_* code and never throws;
@@ -119,6 +122,8 @@ int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs
 
 /* dupin_params.flags */
 #define DUPIN_GPO 1u           /* Algorithm 3: global threshold tau_max (Sec. 5.1) */
+#define DUPIN_LPO 2u           /* Algorithm 4: after every round, trim rounds while some
+                                  w_u < g(S) (Sec. 5.2); implies DUPIN_GPO */
 #define DUPIN_RESULT_DEVICE 8u /* best_mask / peel_round / trace_* are device pointers */
 #define DUPIN_TIMING 16u       /* fill the phase_ms[] durations (CUDA events on 'stream') */
 

@@ -39,7 +39,7 @@ struct CtaJob {
     const long long *a;   // nullptr: 0
     const int *hubs;      // heads of hub-coded arcs
     long long kD, D, max_rounds;
-    int use_min, gpo;
+    int use_min, gpo, lpo;
     long long *w;      // [n] workspace
     int *front;        // [n] workspace
     int *pr;           // [n] output
@@ -143,6 +143,9 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
     st.best_size = n;
     st.bf = st.f;
     st.gpo_le = 0;
+    st.gpo_lt = -1;
+    st.gm_f = 0;
+    st.gm_s = 0;
     st.n_min_rule = 0;
     st.scan = 0;
     if (tid == 0 && J.tr_cap > 0) {
@@ -151,7 +154,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         J.tr_size[0] = n;
         J.tr_peeled[0] = 0;
     }
-    TailRound R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, seg_global_min(first, nseg));
+    TailRound R = tail_plan(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, seg_global_min(first, nseg));
     int err = 0;
     while (!R.done) {
         if (R.i > J.max_rounds) {
@@ -313,7 +316,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, st, mins_all);
+        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, mins_all);
     }
     __syncthreads();
     for (long long u = tid; u < n; u += CTA_THREADS) {
@@ -453,7 +456,8 @@ int cta_batch_enqueue(dupin_graph *const *graphs, const dupin_params *params, du
         J.D = p.eps_den;
         J.max_rounds = p.max_rounds > 0 ? p.max_rounds : g->n + 1;
         J.use_min = J.kD < 2 * J.D ? 1 : 0;
-        J.gpo = (p.flags & DUPIN_GPO) ? 1 : 0;
+        J.gpo = (p.flags & (DUPIN_GPO | DUPIN_LPO)) ? 1 : 0;
+        J.lpo = (p.flags & DUPIN_LPO) ? 1 : 0;
         J.w = (long long *)(arena + off_w[k]);
         J.front = (int *)(arena + off_f[k]);
         const bool dev = (p.flags & DUPIN_RESULT_DEVICE) != 0;

@@ -52,6 +52,7 @@ struct PeelCtl {
     long long best_round, best_size;
     unsigned long long bf_lo, bf_hi;
     long long gpo_le;
+    long long gpo_lt;  // Algorithm 4's strict form of tau_max: ceil(...) - 1
     long long n_min_rule;
     long long scan_volume;
     long long bulk_rounds;
@@ -77,7 +78,8 @@ struct BlockPart {
     long long mc_cnt;     // minimum-rule candidates (live vertices of weight min_surv)
     long long mc_stage;   // ... with at least one arc
     long long mc_deg;     // ... and their arcs
-    long long pad[2];
+    long long min_surv2;  // the smallest live weight above min_surv (minimum-rule blocks)
+    long long pad[1];
 };
 
 // Hubs: up to DUPIN_HUB_MAX highest-degree vertices (degree >= DUPIN_HUB_MIN_DEG).
@@ -119,6 +121,7 @@ struct PeelArgs {
     long long D;        // eps denominator
     int use_min;        // k (1 + eps) < 2: the minimum rule can fire
     int gpo;            // Algorithm 3
+    int lpo;            // Algorithm 4 (with gpo)
     long long max_rounds;
     long long tail_cap;     // the tail takes over once |S| <= tail_cap ...
     long long tail_arcs;    // ... and 2 |E(S)| <= tail_arcs
@@ -145,22 +148,46 @@ __host__ __device__ __forceinline__ u128 mk128(unsigned long long lo, unsigned l
     return ((u128)hi << 64) | (u128)lo;
 }
 
-// floor(X / Y) for 1 <= Y < 2^64, saturated to INT64_MAX, with integer
-// operations only (binary long division of the last 63 quotient bits; the
-// quotient is below 2^63 once saturation is ruled out).  Used once per round.
-__device__ __forceinline__ long long floor_div_sat(u128 X, unsigned long long Y) {
-    if (X >= ((u128)Y << 63)) return 0x7fffffffffffffffLL;
-    u128 rem = X >> 63;  // < Y
-    unsigned long long q = 0;
-    for (int b = 62; b >= 0; --b) {
-        rem = (rem << 1) | (u128)((unsigned long long)(X >> b) & 1ull);
-        q <<= 1;
-        if (rem >= (u128)Y) {
-            rem -= Y;
-            q |= 1ull;
-        }
+// floor((u1 2^64 + u0) / v) for u1 < v (the quotient fits in 64 bits):
+// Knuth's Algorithm D (TAOCP vol. 2, 4.3.1) with 32-bit digits -- normalise v,
+// estimate each of the two quotient digits from the top two dividend digits
+// and the top divisor digit, and correct the estimate (at most twice).
+__host__ __device__ __forceinline__ unsigned long long div_u128_u64(unsigned long long u1, unsigned long long u0,
+                                                                    unsigned long long v) {
+    const unsigned long long B = 1ull << 32;
+#ifdef __CUDA_ARCH__
+    const int s = __clzll((long long)v);
+#else
+    const int s = __builtin_clzll(v);
+#endif
+    v <<= s;
+    const unsigned long long vn1 = v >> 32, vn0 = v & 0xffffffffull;
+    const unsigned long long un32 = s ? (u1 << s) | (u0 >> (64 - s)) : u1;
+    const unsigned long long un10 = u0 << s;
+    const unsigned long long un1 = un10 >> 32, un0 = un10 & 0xffffffffull;
+    unsigned long long q1 = un32 / vn1, rhat = un32 - q1 * vn1;
+    while (q1 >= B || q1 * vn0 > ((rhat << 32) | un1)) {
+        q1--;
+        rhat += vn1;
+        if (rhat >= B) break;
     }
-    return (long long)q;
+    const unsigned long long un21 = (un32 << 32) + un1 - q1 * v;  // exact: the true value is below 2^64
+    unsigned long long q0 = un21 / vn1;
+    rhat = un21 - q0 * vn1;
+    while (q0 >= B || q0 * vn0 > ((rhat << 32) | un0)) {
+        q0--;
+        rhat += vn1;
+        if (rhat >= B) break;
+    }
+    return (q1 << 32) | q0;
+}
+
+// floor(X / Y) for 1 <= Y < 2^64, saturated to INT64_MAX, with integer
+// operations only (the quotient is below 2^63 once saturation is ruled out,
+// so X's high word is below Y).  Used once per round.
+__host__ __device__ __forceinline__ long long floor_div_sat(u128 X, unsigned long long Y) {
+    if (X >= ((u128)Y << 63)) return 0x7fffffffffffffffLL;
+    return (long long)div_u128_u64((unsigned long long)(X >> 64), (unsigned long long)X, Y);
 }
 
 // exact threshold floor(num_mul * f / (den_mul * size)), saturated to INT64_MAX
@@ -173,6 +200,20 @@ __device__ __forceinline__ long long floor_ratio(unsigned long long num_mul, u12
         return q > (u128)0x7fffffffffffffffULL ? 0x7fffffffffffffffLL : (long long)q;
     }
     return floor_div_sat(num, (unsigned long long)den);
+}
+
+// ceil(num_mul * f / (den_mul * size)) - 1 (the largest w with w < the
+// ratio), saturated to INT64_MAX; -1 when the ratio is 0
+__device__ __forceinline__ long long below_ratio(unsigned long long num_mul, u128 f, unsigned long long den_mul,
+                                                 long long size) {
+    const u128 num = (u128)num_mul * f;
+    if (num == 0) return -1;
+    const u128 den = (u128)den_mul * (u128)(unsigned long long)size;
+    if (den >> 64) {
+        u128 q = (num - 1) / den;
+        return q > (u128)0x7fffffffffffffffULL ? 0x7fffffffffffffffLL : (long long)q;
+    }
+    return floor_div_sat(num - 1, (unsigned long long)den);
 }
 
 // w * Y <= X exactly, for 0 <= w < 2^63 (the division-free form of w <= floor(X / Y))

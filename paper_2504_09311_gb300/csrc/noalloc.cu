@@ -107,8 +107,8 @@ extern "C" int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32
     if (p.k_mult < 1 || p.k_mult > 64) return dupin_fail(DUPIN_ERR_INVALID_ARG, "k_mult must be in 1..64");
     if (p.eps_den < 1 || p.eps_den > (1LL << 24) || p.eps_num < 0 || p.eps_num > (1LL << 30))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "eps must be eps_num/eps_den, 0 <= eps_num <= 2^30, 1 <= eps_den <= 2^24");
-    if (p.flags & ~(uint32_t)DUPIN_GPO)
-        return dupin_fail(DUPIN_ERR_INVALID_ARG, "dupin_peel_noalloc accepts only the DUPIN_GPO flag");
+    if (p.flags & ~(uint32_t)(DUPIN_GPO | DUPIN_LPO))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "dupin_peel_noalloc accepts only the DUPIN_GPO and DUPIN_LPO flags");
     if (p.metric != DUPIN_DG && !arc_w) return dupin_fail(DUPIN_ERR_INVALID_ARG, "DW/FD need arc weights");
     if (n > tail_cap_limit())
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "this device's shared memory cannot hold the graph's state");
@@ -166,7 +166,8 @@ extern "C" int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32
     A.kD = (long long)p.k_mult * (p.eps_den + p.eps_num);
     A.D = p.eps_den;
     A.use_min = A.kD < 2 * A.D ? 1 : 0;
-    A.gpo = (p.flags & DUPIN_GPO) ? 1 : 0;
+    A.gpo = (p.flags & (DUPIN_GPO | DUPIN_LPO)) ? 1 : 0;
+    A.lpo = (p.flags & DUPIN_LPO) ? 1 : 0;
     A.max_rounds = p.max_rounds > 0 ? p.max_rounds : n + 1;
     A.tail_cap = DUPIN_NOALLOC_MAX_N;
     A.tail_arcs = arcs;

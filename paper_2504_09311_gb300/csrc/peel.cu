@@ -292,6 +292,7 @@ __global__ void k_init_finish(PeelArgs A, long long n) {
     c->bf_lo = c->f_lo;
     c->bf_hi = c->f_hi;
     c->gpo_le = 0;
+    c->gpo_lt = -1;
     c->n_min_rule = 0;
     c->scan_volume = 0;
     c->bar_count = 0;
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
     __shared__ struct {
         unsigned long long wlo, whi;  // sum of the selected vertices' weights
         long long U_sel, newSize;
+        long long minsurv;  // minimum weight of this round's survivors before its decrements
         int minrule, compact;
     } s_rd;
 
@@ -377,6 +379,9 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
         st.best_size = ctl->best_size;
         st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
         st.gpo_le = ctl->gpo_le;
+        st.gpo_lt = ctl->gpo_lt;
+        st.gm_f = 0;
+        st.gm_s = 0;
         st.n_min_rule = ctl->n_min_rule;
         st.scan = ctl->scan_volume;
         s_elive = ctl->elive;
@@ -401,13 +406,30 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
         long long T;
         {
             const u128 f = s_st.f;
-            T = floor_ratio((unsigned long long)A.kD, f, (unsigned long long)A.D, size);
-            if (A.gpo) {
-                const long long le = floor_ratio((unsigned long long)A.D, f, (unsigned long long)A.kD, size);
-                const long long gl = le > s_st.gpo_le ? le : s_st.gpo_le;
-                T = gl > T ? gl : T;
-                __syncthreads();  // every thread has read s_st.gpo_le
-                if (tid == 0) s_st.gpo_le = gl;
+            const u128 f1 = f - 1;
+            if (A.lpo && s_st.round > 0 && f != 0 &&
+                mul_le(s_st.minw, (unsigned long long)size, (unsigned long long)(f1 >> 64), (unsigned long long)f1)) {
+                // Algorithm 4's trim round: some live w < g(S) (the exact minimum
+                // live weight says so); it removes w < max(tau_max, g(S))
+                const long long bg = floor_div_sat(f1, (unsigned long long)size);
+                T = bg > s_st.gpo_lt ? bg : s_st.gpo_lt;
+            } else {
+                T = floor_ratio((unsigned long long)A.kD, f, (unsigned long long)A.D, size);
+                if (A.gpo) {
+                    const long long le = floor_ratio((unsigned long long)A.D, f, (unsigned long long)A.kD, size);
+                    const long long gl = le > s_st.gpo_le ? le : s_st.gpo_le;
+                    long long gt = s_st.gpo_lt;
+                    if (A.lpo) {
+                        const long long lt = below_ratio((unsigned long long)A.D, f, (unsigned long long)A.kD, size);
+                        gt = lt > gt ? lt : gt;
+                    }
+                    T = gl > T ? gl : T;
+                    __syncthreads();  // every thread has read s_st.gpo_le / gpo_lt
+                    if (tid == 0) {
+                        s_st.gpo_le = gl;
+                        s_st.gpo_lt = gt;
+                    }
+                }
             }
         }
         const int live_sel = s_st.live_sel;
@@ -476,11 +498,13 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
                     s_surv = 0;
                 }
                 __syncthreads();
-                long long cdeg = 0;
+                long long cdeg = 0, min2 = kMaxLL;  // min2: the smallest live weight above m
                 for (long long jb = j0 + wid * 32; jb < j1; jb += BULK_THREADS) {
                     const long long j = jb + lane;
                     const int id = j < j1 ? live[j] : -1;
-                    const bool c = id >= 0 && A.w[id] == m;
+                    const long long wv = id >= 0 ? A.w[id] : kMaxLL;
+                    const bool c = id >= 0 && wv == m;
+                    if (id >= 0 && wv > m && wv < min2) min2 = wv;
                     const unsigned cb = __ballot_sync(0xffffffffu, c);
                     long long start = 0, deg = 0;
                     if (cb) {
@@ -499,17 +523,19 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
                 BlockRed<BULK_WARPS, 6> rc;
                 for (int q = 0; q < 6; q++) rc.v[q] = 0;
                 rc.v[0] = cdeg;
-                rc.lo = 0; rc.hi = 0; rc.mn = kMaxLL;
+                rc.lo = 0; rc.hi = 0; rc.mn = min2;
                 block_reduce<BULK_WARPS, 6>(rc, s_v, s_lo, s_hi, s_mn);
                 if (tid == 0) {
                     p.mc_cnt = (long long)s_surv;
                     p.mc_stage = (long long)s_nst;
                     p.mc_deg = rc.v[0];
+                    p.min_surv2 = rc.mn;
                 }
             } else if (tid == 0) {
                 p.mc_cnt = 0;
                 p.mc_stage = 0;
                 p.mc_deg = 0;
+                p.min_surv2 = kMaxLL;
             }
         }
         if (!grid_barrier(ctl, G, bar_target)) return;
@@ -540,6 +566,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
             if (tid == 0) {
                 s_rd.wlo = r.lo;
                 s_rd.whi = r.hi;
+                s_rd.minsurv = r.mn;  // the survivors' minimum (before this round's decrements)
             }
             myStage = A.part[b].stage_cnt;
             myDeg = A.part[b].sel_deg;
@@ -553,6 +580,8 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
                 for (int t = tid; t < (int)G; t += BULK_THREADS) {
                     const BlockPart &p = A.part[t];
                     const bool q = p.min_surv == minAll;
+                    const long long ms = q ? p.min_surv2 : p.min_surv;  // survivors of the minimum rule
+                    r.mn = ms < r.mn ? ms : r.mn;
                     if (q) {
                         r.v[0] += p.mc_cnt;
                         r.v[1] += p.mc_stage;
@@ -578,6 +607,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
                     const u128 ws = (u128)(unsigned long long)U_sel * (unsigned long long)minAll;
                     s_rd.wlo = (unsigned long long)ws;
                     s_rd.whi = (unsigned long long)(ws >> 64);
+                    s_rd.minsurv = r.mn;
                 }
             }
         }
@@ -666,6 +696,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
         // takes BULK_ILP arcs at a time and issues their loads together.
         unsigned long long ilo = 0, ihi = 0;
         long long nrem = 0;  // 2 per arc from U to S \ U, 1 per arc inside U
+        long long mindec = kMaxLL;  // with Algorithm 4: the smallest weight after a decrement
         if (totArcs > 0) {
             const long long E0 = split_at(totArcs, b, G);
             const long long E1 = split_at(totArcs, b + 1, G);
@@ -715,8 +746,14 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
                         if (p > (int)i) {
                             const int cvu = cv[u];
                             if (cvu >= 0) {
-                                // result unused: a fire-and-forget reduction
-                                atomicAdd((unsigned long long *)&w[cvu], (unsigned long long)(-c));
+                                if (A.lpo) {
+                                    const long long nv =
+                                        (long long)atomicAdd((unsigned long long *)&w[cvu], (unsigned long long)(-c)) - c;
+                                    mindec = nv < mindec ? nv : mindec;
+                                } else {
+                                    // result unused: a fire-and-forget reduction
+                                    atomicAdd((unsigned long long *)&w[cvu], (unsigned long long)(-c));
+                                }
                             } else {  // hub head: aggregate in shared memory
                                 const int h = -cvu - 1;
                                 const unsigned cl = (unsigned)c;
@@ -741,7 +778,9 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
             for (int h = tid; h < nh; h += BULK_THREADS) {
                 const unsigned long long a = ((unsigned long long)s_hhi[h] << 32) + s_hlo[h];
                 if (a) {
-                    atomicAdd((unsigned long long *)&A.w[s_hub[h]], (unsigned long long)0 - a);
+                    const long long nv =
+                        (long long)(atomicAdd((unsigned long long *)&A.w[s_hub[h]], (unsigned long long)0 - a) - a);
+                    mindec = nv < mindec ? nv : mindec;
                     s_hlo[h] = 0;
                     s_hhi[h] = 0;
                 }
@@ -751,7 +790,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
             BlockRed<BULK_WARPS, 6> r;
             for (int j = 0; j < 6; j++) r.v[j] = 0;
             r.v[0] = nrem;
-            r.lo = ilo; r.hi = ihi; r.mn = kMaxLL;
+            r.lo = ilo; r.hi = ihi; r.mn = mindec;
             block_reduce<BULK_WARPS, 6>(r, s_v, s_lo, s_hi, s_mn);
             if (tid == 0) {
                 A.part[b].in_lo = r.lo;
@@ -778,6 +817,9 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
                 // an edge leaves E(S) with its first removed end: counted 2 on
                 // its one arc from U to S \ U, 1 on each of its two arcs inside U
                 s_elive -= r.v[0] / 2;
+                // exact minimum live weight (Algorithm 4 needs it): a survivor's
+                // last decrement result is its final weight
+                if (A.lpo) st.minw = s_rd.minsurv < r.mn ? s_rd.minsurv : r.mn;
                 const u128 internal = mk128(r.lo, r.hi);
                 const u128 wsel = mk128(s_rd.wlo, s_rd.whi);
                 st.f = st.f - (wsel - (internal >> 1));
@@ -818,6 +860,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
         ctl->bf_lo = (unsigned long long)st.bf;
         ctl->bf_hi = (unsigned long long)(st.bf >> 64);
         ctl->gpo_le = st.gpo_le;
+        ctl->gpo_lt = st.gpo_lt;
         ctl->n_min_rule = st.n_min_rule;
         ctl->scan_volume = st.scan;
         ctl->bulk_rounds = st.round;
@@ -946,6 +989,9 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
     st.best_size = ctl->best_size;
     st.bf = mk128(ctl->bf_lo, ctl->bf_hi);
     st.gpo_le = ctl->gpo_le;
+    st.gpo_lt = ctl->gpo_lt;
+    st.gm_f = 0;
+    st.gm_s = 0;
     st.n_min_rule = ctl->n_min_rule;
     st.scan = ctl->scan_volume;
     for (long long p = tid; p <= L; p += TAIL_THREADS) toff[p] = (int)A.tlrp[p];
@@ -963,7 +1009,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         if (lane == 0) first[q] = m;
     }
     __syncthreads();
-    TailRound R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, seg_global_min(first, nseg));
+    TailRound R = tail_plan(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, seg_global_min(first, nseg));
     int err = 0;
     while (!R.done) {
         if (R.i > A.max_rounds) {
@@ -1158,7 +1204,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, st, mins_all);
+        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, mins_all);
     }
     __syncthreads();
     for (long long p = tid; p < L; p += TAIL_THREADS) {
@@ -1176,6 +1222,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         ctl->bf_lo = (unsigned long long)st.bf;
         ctl->bf_hi = (unsigned long long)(st.bf >> 64);
         ctl->gpo_le = st.gpo_le;
+        ctl->gpo_lt = st.gpo_lt;
         ctl->n_min_rule = st.n_min_rule;
         ctl->scan_volume = st.scan;
         if (!err) ctl->status = ST_DONE;
@@ -1257,7 +1304,7 @@ static int check_params(const dupin_graph *g, const dupin_params *p) {
     if (p->k_mult < 1 || p->k_mult > 64) return dupin_fail(DUPIN_ERR_INVALID_ARG, "k_mult must be in 1..64");
     if (p->eps_den < 1 || p->eps_den > (1LL << 24) || p->eps_num < 0 || p->eps_num > (1LL << 30))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "eps must be eps_num/eps_den with 0 <= eps_num <= 2^30, 1 <= eps_den <= 2^24");
-    if (p->flags & ~(uint32_t)(DUPIN_GPO | DUPIN_RESULT_DEVICE | DUPIN_TIMING))
+    if (p->flags & ~(uint32_t)(DUPIN_GPO | DUPIN_LPO | DUPIN_RESULT_DEVICE | DUPIN_TIMING))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown flag");
     if (p->metric != DUPIN_DG && g->cw == nullptr)
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "DW/FD need edge weights; the graph was loaded without them");
@@ -1421,7 +1468,8 @@ static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const d
     A.kD = (long long)p->k_mult * (p->eps_den + p->eps_num);
     A.D = p->eps_den;
     A.use_min = A.kD < 2 * A.D ? 1 : 0;
-    A.gpo = (p->flags & DUPIN_GPO) ? 1 : 0;
+    A.gpo = (p->flags & (DUPIN_GPO | DUPIN_LPO)) ? 1 : 0;  // Algorithm 4 carries Algorithm 3
+    A.lpo = (p->flags & DUPIN_LPO) ? 1 : 0;
     A.max_rounds = plan.max_rounds;
     A.tail_cap = plan.tail_cap;
     A.tail_arcs = std::min<long long>(plan.tail_arcs, ws->tarc_cap);

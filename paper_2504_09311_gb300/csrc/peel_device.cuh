@@ -157,7 +157,9 @@ struct RoundState {
     long long minw;
     long long best_round, best_size;
     u128 bf;
-    long long gpo_le, n_min_rule, scan;
+    long long gpo_le, gpo_lt, n_min_rule, scan;
+    u128 gm_f;       // the largest g(S) = gm_f / gm_s a main round has started from
+    long long gm_s;  // (0: none yet); tau_max only changes when g(S) exceeds it
 };
 
 
@@ -213,6 +215,7 @@ struct TailRound {
     long long gle;                // Algorithm 3's floor(tau_max), -1 without GPO
     long long minw;               // minimum live weight
     int minrule;                  // threshold selects nobody: take the minimum
+    int trim;                     // Algorithm 4's trim round
     int done;                     // S is empty
 };
 
@@ -228,23 +231,51 @@ __device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) 
 
 // Every warp (all lanes, identical result): plan round st.round + 1 from the
 // state and the minimum live weight m -- thresholds and the minimum rule.
-__device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int use_min, int gpo, RoundState &st,
-                                               long long m) {
-    const u128 X = mul_u128_u64(st.f, (unsigned long long)kD);
+// With Algorithm 4 (lpo) the round is a trim round while some live w < g(S),
+// i.e. m |S| <= f - 1: it removes w < max(tau_max, g), in the same
+// division-free form (w <= gpo_lt or w |S| <= f - 1).  A main round refines
+// tau_max (Algorithm 3) in both its forms.
+__device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int use_min, int gpo, int lpo,
+                                               RoundState &st, long long m) {
     TailRound R;
     R.i = st.round + 1;
+    R.minw = m;
+    R.done = st.size == 0 ? 1 : 0;
+    R.minrule = 0;
+    R.trim = 0;
+    if (lpo && st.round > 0 && st.size > 0 && st.f != 0) {  // trims follow a round
+        const u128 X = st.f - 1;
+        const unsigned long long Xhi = (unsigned long long)(X >> 64), Xlo = (unsigned long long)X;
+        if (mul_le(m, (unsigned long long)st.size, Xhi, Xlo)) {
+            R.trim = 1;
+            R.Xhi = Xhi;
+            R.Xlo = Xlo;
+            R.Y = (unsigned long long)st.size;
+            R.gle = st.gpo_lt;
+            return R;
+        }
+    }
+    const u128 X = mul_u128_u64(st.f, (unsigned long long)kD);
     R.Xhi = (unsigned long long)(X >> 64);
     R.Xlo = (unsigned long long)X;
     R.Y = (unsigned long long)D * (unsigned long long)st.size;
     R.gle = -1;
     if (gpo && st.size > 0) {
-        long long le = floor_ratio((unsigned long long)D, st.f, (unsigned long long)kD, st.size);
-        st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
+        // floor and ceil-1 are monotone in g, so tau_max's integer forms can
+        // only grow when g(S) exceeds the largest g seen so far
+        if (st.gm_s == 0 || frac_gt(st.f, st.size, st.gm_f, st.gm_s)) {
+            st.gm_f = st.f;
+            st.gm_s = st.size;
+            const long long le = floor_ratio((unsigned long long)D, st.f, (unsigned long long)kD, st.size);
+            st.gpo_le = le > st.gpo_le ? le : st.gpo_le;
+            if (lpo) {
+                const long long lt = below_ratio((unsigned long long)D, st.f, (unsigned long long)kD, st.size);
+                st.gpo_lt = lt > st.gpo_lt ? lt : st.gpo_lt;
+            }
+        }
         R.gle = st.gpo_le;
     }
-    R.minw = m;
     R.minrule = (use_min && st.size > 0 && !mul_le(m, R.Y, R.Xhi, R.Xlo) && m > R.gle) ? 1 : 0;
-    R.done = st.size == 0 ? 1 : 0;
     return R;
 }
 

@@ -21,6 +21,7 @@ DG, DW, FD = 0, 1, 2
 METRICS = {"dg": DG, "dw": DW, "fd": FD}
 DEVICE_PTRS = 1
 GPO = 1
+LPO = 2  # Algorithm 4 (implies GPO)
 RESULT_DEVICE = 8
 TIMING = 16
 

@@ -62,7 +62,7 @@ def test_batch_equals_single(dupin):
     for j, g in enumerate(gs):
         k = 1 + (j % 2)
         eps = [(1, 10), (0, 1), (1, 5)][j % 3]
-        flags = dupin.GPO if j % 5 == 4 else 0
+        flags = dupin.GPO if j % 5 == 4 else (dupin.LPO if j % 7 == 3 else 0)
         params.append(dupin.make_params(metrics[j], k, eps, flags=flags))
     outs = dupin.peel_batch(dgs, params, want_rounds=True, want_trace=True)
     for j, (g, dg, p) in enumerate(zip(gs, dgs, params)):

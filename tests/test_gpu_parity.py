@@ -49,7 +49,7 @@ def assert_same(out, ref, ctx=""):
 def run_both(dupin, g, metric, k, eps, flags=0, tail_cap=0, tail_arc_cap=0):
     og = oracle.Graph.from_synth(g, metric)
     dg = dupin.Graph.from_synth(g)
-    ref = oracle.peel_batch(og, k, eps, flags=flags & oracle.FLAG_GPO)
+    ref = oracle.peel_batch(og, k, eps, flags=flags & (oracle.FLAG_GPO | oracle.FLAG_LPO))
     out = dupin.peel(dg, metric, k, eps, flags=flags, tail_cap=tail_cap, tail_arc_cap=tail_arc_cap)
     dg.free()
     og.close()
@@ -143,6 +143,22 @@ def test_tail_waits_for_few_arcs(dupin, tail_arc_cap):
                     small = r > 0 and ref.trace_peeled[r] <= 64
                     assert ref.trace_size[r] > tail_cap or (live_arcs_after(g, ref.peel_round, r) > tail_arc_cap
                                                             and not small), ctx
+
+
+@pytest.mark.parametrize("tail_cap", [0, 1, 500])
+def test_lpo(dupin, tail_cap):
+    """Algorithm 4: trim rounds (w < max(tau_max, g)) after every round, in the
+    one-CTA tail (tail_cap 0), the grid-wide kernel (tail_cap 1) and across the
+    hand-over (500): bit-exact against the oracle's replay."""
+    fd = synth.bipartite_zipf(3000, 1500, 20000, 1.6, 1, 30, 30, 0.5, 12, seed=4)
+    fd.c = synth.fd_weights(fd)
+    cases = [(synth.rmat_weighted(13, 16, "dw", seed=3), "dw"), (fd, "fd"),
+             (synth.dg_planted_block(seed=2, nU=3000, nI=1500, draws=20000, block=60, p=0.5), "dg")]
+    for g, metric in cases:
+        for k in (1, 2):
+            for eps in ((0, 1), (1, 10)):
+                out, ref = run_both(dupin, g, metric, k, eps, flags=dupin.LPO, tail_cap=tail_cap)
+                assert_same(out, ref, (metric, k, eps, tail_cap))
 
 
 def test_planted_block_config(dupin):
