@@ -256,6 +256,18 @@ def cpu_baseline(g, metric, eps, k):
             "seconds": t2 - t1}
 
 
+def max_over_ranks(ms: float, dist) -> float:
+    """The step time every rank reports is the slowest rank's (host tensors, so
+    the gloo process group carries it)."""
+    if not dist:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
@@ -358,11 +370,7 @@ def main():
     if dist:
         dist.barrier()
     clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
     edges_per_step = g.m * len(params)
     value = world * edges_per_step / (ms / 1e3)
 
