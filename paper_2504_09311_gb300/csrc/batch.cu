@@ -594,6 +594,9 @@ int cta_batch_finish(CtaBatch *B, cudaStream_t s, std::vector<int> *per_job_stat
 }
 
 // Streams for concurrent tails, created once per device and reused.
+// peels whose tails may overlap later grid-wide stages
+#define TAIL_OVERLAP_MAX 8
+
 static cudaStream_t tail_stream(int dev, size_t q) {
     static std::mutex mu;
     static std::map<int, std::vector<cudaStream_t>> pool;
@@ -612,11 +615,10 @@ static cudaStream_t tail_stream(int dev, size_t q) {
 // Several peels of large graphs (or of one graph under several parameter
 // sets).  The initial weights are computed once per graph and metric; the
 // grid-wide stages run one after another on 'stream' (each is a
-// cooperative launch over the whole GPU); then each peel's tail sub-graph is
-// built on 'stream' and its one-CTA tail runs on a stream of its own, so the
-// latency-bound tails, one SM each, run side by side.  No tail overlaps a
-// grid-wide stage: the first tail starts after the last of them.  A graph
-// that appears several times gets one cached workspace per appearance.
+// cooperative launch); each peel's tail sub-graph is built on 'stream' and
+// its one-CTA tail runs on a stream of its own, so the latency-bound tails,
+// one SM each, run side by side.  A graph that appears several times gets
+// one cached workspace per appearance.
 static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
                                  const std::vector<int64_t> &idx, cudaStream_t s) {
     const size_t k = idx.size();
@@ -647,13 +649,26 @@ static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params 
         int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_INIT, s, from);
         if (rc) return fail_at(q, rc);
     }
-    for (size_t q = 0; q < k; q++) {
-        int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s);
-        if (rc) return fail_at(q, rc);
+    // With few peels, peel q's grid-wide stage runs beside the tails of peels
+    // 0 .. q-1 on one block per SM fewer per running tail (each tail holds one
+    // SM), so that its cooperative grid always fits; with many peels every
+    // grid-wide stage runs first, on all SMs, and the tails after them.
+    const bool overlap = k <= TAIL_OVERLAP_MAX;
+    if (!overlap) {
+        for (size_t q = 0; q < k; q++) {
+            int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s);
+            if (rc) return fail_at(q, rc);
+        }
     }
     std::vector<cudaEvent_t> ev(2 * k, nullptr);
     int rc = DUPIN_OK;
     for (size_t q = 0; q < k && rc == DUPIN_OK; q++) {
+        if (overlap) {
+            const int grid = ws[q]->grid - (int)q;
+            rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s, nullptr,
+                                     grid > 0 ? grid : 1);
+            if (rc) break;
+        }
         rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BUILD, s);
         if (rc) break;
         cudaStream_t t = tail_stream(dev, q);

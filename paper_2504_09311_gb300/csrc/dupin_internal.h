@@ -92,8 +92,10 @@ enum { PEEL_INIT = 1, PEEL_BUILD = 2, PEEL_TAIL = 4, PEEL_BULK = 8, PEEL_FRONT =
 // 'init_from' (stage PEEL_INIT only): a workspace whose initial weights for
 // the same graph and metric are already computed on this stream and not yet
 // changed by its grid-wide rounds; they are copied instead of recomputed.
+// 'bulk_grid' (stage PEEL_BULK): blocks of the cooperative launch, 0 = one per
+// SM; fewer leave SMs to one-CTA tails that run at the same time.
 int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
-                        int stages, cudaStream_t s, const PeelWorkspace *init_from = nullptr);
+                        int stages, cudaStream_t s, const PeelWorkspace *init_from = nullptr, int bulk_grid = 0);
 int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, dupin_result *r, cudaStream_t s);
 
 // kernels shared by loading and peeling

@@ -331,7 +331,9 @@ __device__ __forceinline__ void stage_entry(const PeelArgs &A, long long j0, boo
     }
 }
 
-__global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
+// The grid-wide rounds of one peel, run by blocks b = 0 .. G-1 of a cooperative
+// launch (all of it, or one group of it).
+__device__ __forceinline__ void peel_bulk_body(const PeelArgs &A, const int b, const unsigned G) {
     __shared__ long long s_v[BULK_WARPS][6];
     __shared__ unsigned long long s_lo[BULK_WARPS], s_hi[BULK_WARPS];
     __shared__ long long s_mn[BULK_WARPS];
@@ -355,8 +357,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
         int minrule, compact;
     } s_rd;
 
-    const unsigned G = gridDim.x;
-    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     PeelCtl *ctl = A.ctl;
     const DevGraph g = A.g;
     const bool dg = g.cw == nullptr;
@@ -868,6 +869,8 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
         if (ctl->error == 0) ctl->status = st.size == 0 ? ST_DONE : ST_TAIL;
     }
 }
+
+__global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) { peel_bulk_body(A, blockIdx.x, gridDim.x); }
 
 // ------------------------------------------------------- (d) tail sub-graph
 
@@ -1511,7 +1514,7 @@ __global__ void k_init_follow_ctl(const PeelCtl *src, PeelCtl *dst) {
 }
 
 int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
-                        int stages, cudaStream_t s, const PeelWorkspace *init_from) {
+                        int stages, cudaStream_t s, const PeelWorkspace *init_from, int bulk_grid) {
     PeelArgs A = make_args(g, ws, p, plan);
     const long long tail_cap = plan.tail_cap;
     const bool timing = (p->flags & DUPIN_TIMING) != 0;
@@ -1538,9 +1541,10 @@ int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_par
     if (stages & PEEL_BULK) {
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
         if (g->n > tail_cap || g->arcs > A.tail_arcs) {
+            const int grid = bulk_grid > 0 && bulk_grid < ws->grid ? bulk_grid : ws->grid;
             void *args[] = {&A};
             cudaError_t e =
-                cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(ws->grid), dim3(BULK_THREADS), args, 0, s);
+                cudaLaunchCooperativeKernel((void *)k_peel_bulk, dim3(grid), dim3(BULK_THREADS), args, 0, s);
             if (e != cudaSuccess) return dupin_cuda_fail(e, "cooperative launch of k_peel_bulk");
         }
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[3], s));
