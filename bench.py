@@ -33,6 +33,8 @@ import time
 
 import numpy as np
 
+from typing import Optional
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -256,6 +258,37 @@ def cpu_baseline(g, metric, eps, k):
             "seconds": t2 - t1}
 
 
+TAIL_KERNEL_BEGIN = "__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {"
+TAIL_KERNEL_END = "// best_mask[u] = (peel_round[u] > best_round) for a best round known on the host"
+
+
+def tail_kernel_source_hash() -> Optional[str]:
+    """sha256 of k_peel_tail's definition and the two device headers it uses."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2504_09311_gb300", "csrc")
+    try:
+        peel = open(os.path.join(csrc, "peel.cu")).read()
+        a, b = peel.index(TAIL_KERNEL_BEGIN), peel.index(TAIL_KERNEL_END)
+        text = peel[a:b] + open(os.path.join(csrc, "peel_device.cuh")).read() + \
+            open(os.path.join(csrc, "dupin_common.cuh")).read()
+    except (OSError, ValueError):
+        return None
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
+def measured_traffic(kernel: str) -> Optional[float]:
+    """DRAM bytes per launch that ncu measured for the kernel on this workload
+    (profiles/dram_traffic.json), or None once its sources have changed."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if kernel != "k_peel_tail" or not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_sha256") != tail_kernel_source_hash():
+        return None
+    return float(d["bytes_per_launch"])
+
+
 def max_over_ranks(ms: float, dist) -> float:
     """The step time every rank reports is the slowest rank's (host tensors, so
     the gloo process group carries it)."""
@@ -390,7 +423,7 @@ def main():
     achieved = bytes_dom / (mean_phase[dom] / 1e3) / 1e9 if mean_phase[dom] > 0 else 0.0
     kernel = {"init": "k_init_vertex+k_init_arcs+k_init_reduce", "bulk": "k_peel_bulk",
               "build": "k_tail_prep+k_tail_scan+k_tail_arcs", "tail": "k_peel_tail"}[names[dom]]
-    traffic = None
+    traffic = measured_traffic(kernel) if args.workload == "fd_2Mx1M_40M" else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
                 "peak_source": f"{peak_kind} hbm_gbs",
