@@ -470,7 +470,7 @@ def main():
         e2e = {"value": world * edges_per_step / dt, "unit": "edges/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
                "includes": "graph load from pinned host memory + validation + one batched call of the 3 peels "
-                           "(workspaces allocated for the new graph) + result copies + free"}
+                           "(peel workspaces from the cache of freed graphs' workspaces) + result copies + free"}
 
     batched = None if args.no_batch else bench_batched(dupin, stream, args)
     serving = None if args.no_serve else bench_serving(dupin, args)

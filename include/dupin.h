@@ -112,8 +112,15 @@ typedef struct {
  */
 int dupin_graph_load(const dupin_graph_desc *desc, void *stream, dupin_graph **out);
 
-/* Release a graph and its cached peeling workspace.  NULL is accepted. */
+/*
+ * Release a graph.  NULL is accepted.  Its peeling workspaces (device
+ * memory sized for the graph) are kept, at most 8 per process, for later
+ * graphs they fit; dupin_trim_cache() frees the kept ones.
+ */
 int dupin_graph_free(dupin_graph *g);
+
+/* Free the peeling workspaces kept from freed graphs (see dupin_graph_free). */
+int dupin_trim_cache(void);
 
 /* n = vertices, m = undirected edges, arcs = 2m, device_bytes = bytes held. */
 int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs, int64_t *device_bytes);

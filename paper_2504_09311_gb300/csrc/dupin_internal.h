@@ -25,7 +25,8 @@ int dupin_cuda_fail(cudaError_t e, const char *what);
 // reused by later peels of the same graph.
 struct PeelWorkspace {
     long long n = 0, arcs = 0, tail_cap = 0, tr_cap = 0, tarc_cap = 0;
-    int grid = 0;  // blocks of the persistent kernel
+    int grid = 0;    // blocks of the persistent kernel
+    int device = 0;  // where it was allocated
     long long *w = nullptr;
     int *pr = nullptr;
     int *live0 = nullptr, *live1 = nullptr;
@@ -77,6 +78,8 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
                                 cudaStream_t s, int *rc);
 void workspace_free(PeelWorkspace *ws);
 void workspace_free(PeelWorkspace *ws, cudaStream_t s);
+// a freed graph's workspace: kept for a later graph it fits, or freed
+void workspace_release(PeelWorkspace *ws);
 int workspace_ensure(dupin_graph *g, const PeelPlan &plan);
 // workspace k of graph g (0: the one dupin_peel uses), allocated or grown for plan
 PeelWorkspace *workspace_slot(dupin_graph *g, int k, const PeelPlan &plan, int *rc);

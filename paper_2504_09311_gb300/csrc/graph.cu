@@ -150,8 +150,8 @@ static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
 
 static void graph_release(dupin_graph *g) {
     if (!g) return;
-    workspace_free(g->ws);
-    for (PeelWorkspace *w : g->ws_more) workspace_free(w);
+    workspace_release(g->ws);
+    for (PeelWorkspace *w : g->ws_more) workspace_release(w);
     cudaFree(g->hubs);
     cudaFree(g->rp);
     cudaFree(g->col);

@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <string>
 
+#include <mutex>
+
 #include "dupin_internal.h"
 #include "peel_device.cuh"
 
@@ -1370,6 +1372,7 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
                                 cudaStream_t s, int *rc) {
     const long long tail_cap = plan.tail_cap, tr_cap = plan.tr_cap;
     PeelWorkspace *ws = new PeelWorkspace();
+    cudaGetDevice(&ws->device);
     ws->n = n;
     ws->arcs = arcs;
     ws->tail_cap = tail_cap;
@@ -1419,19 +1422,77 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
     return ws;
 }
 
+// Workspaces of freed graphs wait here for a later graph they fit (a caller
+// that loads a new graph for every peel then pays no cudaMalloc / cudaFree for
+// the peel state), at most WS_POOL_MAX of them; dupin_trim_cache frees them.
+#define WS_POOL_MAX 8
+static std::mutex g_pool_mu;
+static std::vector<PeelWorkspace *> g_pool;
+
+static bool workspace_fits(const PeelWorkspace *ws, int dev, long long n, long long tarc, bool has_cw,
+                           const PeelPlan &plan) {
+    return ws->device == dev && !ws->async && ws->n >= n && ws->tarc_cap >= tarc && ws->tail_cap >= plan.tail_cap &&
+           ws->tr_cap >= plan.tr_cap && (ws->tcw != nullptr || !has_cw);
+}
+
+// the smallest pooled workspace that fits, taken out of the pool (or null)
+static PeelWorkspace *workspace_take(int dev, long long n, long long tarc, bool has_cw, const PeelPlan &plan) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    int best = -1;
+    for (int j = 0; j < (int)g_pool.size(); j++)
+        if (workspace_fits(g_pool[j], dev, n, tarc, has_cw, plan) &&
+            (best < 0 || g_pool[j]->bytes < g_pool[best]->bytes))
+            best = j;
+    if (best < 0) return nullptr;
+    PeelWorkspace *ws = g_pool[best];
+    g_pool.erase(g_pool.begin() + best);
+    return ws;
+}
+
+void workspace_release(PeelWorkspace *ws) {
+    if (!ws) return;
+    if (!ws->async) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if ((int)g_pool.size() < WS_POOL_MAX) {
+            g_pool.push_back(ws);
+            return;
+        }
+    }
+    workspace_free(ws);
+}
+
+extern "C" int dupin_trim_cache(void) {
+    std::vector<PeelWorkspace *> v;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        v.swap(g_pool);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (PeelWorkspace *ws : v) {
+        cudaSetDevice(ws->device);
+        workspace_free(ws);
+    }
+    cudaSetDevice(dev);
+    return DUPIN_OK;
+}
+
 static int workspace_ensure_ref(dupin_graph *g, PeelWorkspace *&slot, const PeelPlan &plan) {
     PeelWorkspace *ws = slot;
     const long long tarc = tail_arc_buffer(g->arcs, plan);
-    if (ws && ws->tail_cap >= plan.tail_cap && ws->tr_cap >= plan.tr_cap && ws->tarc_cap >= tarc) return DUPIN_OK;
+    const bool has_cw = g->cw != nullptr;
+    if (ws && workspace_fits(ws, g->device, g->n, tarc, has_cw, plan)) return DUPIN_OK;
     PeelPlan big = plan;
     if (ws) {  // grow to cover both the old and the new caps
         big.tail_cap = std::max(plan.tail_cap, ws->tail_cap);
         big.tr_cap = std::max(plan.tr_cap, ws->tr_cap);
-        workspace_free(ws);
+        workspace_release(ws);
         slot = nullptr;
     }
+    slot = workspace_take(g->device, g->n, tail_arc_buffer(g->arcs, big), has_cw, big);
+    if (slot) return DUPIN_OK;
     int rc;
-    slot = workspace_create(g->n, g->arcs, g->cw != nullptr, big, false, 0, &rc);
+    slot = workspace_create(g->n, g->arcs, has_cw, big, false, 0, &rc);
     return rc;
 }
 

@@ -71,7 +71,8 @@ class ServeStats(ctypes.Structure):
 # every symbol include/dupin.h declares
 EXPORTS = ["dupin_graph_load", "dupin_graph_free", "dupin_graph_info", "dupin_peel", "dupin_peel_batch",
            "dupin_serve_create", "dupin_serve_submit", "dupin_serve_poll", "dupin_serve_wait", "dupin_serve_stats",
-           "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc", "dupin_struct_size"]
+           "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc", "dupin_struct_size",
+           "dupin_trim_cache"]
 
 NOALLOC_MAX_N = 8192
 
@@ -112,6 +113,11 @@ def lib():
                 raise RuntimeError(f"libdupin.so was built with another layout of {nm.decode()}: rebuild it")
         _lib = L
     return _lib
+
+
+def trim_cache() -> None:
+    """Free the peeling workspaces kept from freed graphs."""
+    check(lib().dupin_trim_cache())
 
 
 def last_error() -> str:

@@ -151,6 +151,28 @@ def test_batch_repeated_graph_and_device_results(dupin):
     dg.free()
 
 
+def test_workspace_cache_across_graphs(dupin):
+    """A freed graph's workspaces serve later graphs they fit (a larger graph's
+    for a smaller one, DW-sized for DG); results do not change."""
+    small = synth.rmat_weighted(14, 8, "dw", seed=21)
+    big = synth.bipartite_zipf(200_000, 100_000, 900_000, 1.8, 1, 50, 50, 0.4, 10, seed=22)
+    big.c = synth.fd_weights(big)
+    dg_s = dupin.Graph.from_synth(small)
+    ref = [dupin.peel(dg_s, "dw", 1, (1, 10), tail_cap=tc) for tc in (0, 1)]
+    dg_s.free()
+    dupin.trim_cache()
+    for rep in range(2):
+        dg_b = dupin.Graph.from_synth(big)
+        outs = dupin.peel_batch([dg_b] * 2, [dupin.make_params("fd", 1, e) for e in ((1, 10), (1, 5))])
+        assert all(o.n_rounds > 0 for o in outs)
+        dg_b.free()  # its workspaces go to the cache
+        dg_s = dupin.Graph.from_synth(small)
+        for tc, r in zip((0, 1), ref):
+            same(dupin.peel(dg_s, "dw", 1, (1, 10), tail_cap=tc), r, (rep, tc))
+        dg_s.free()
+    dupin.trim_cache()
+
+
 def test_serving_alone_and_in_a_mix(dupin):
     gs = window_graphs(16, seed=5, lo=1000, hi=40000)
     big = synth.bipartite_zipf(40_000, 20_000, 200_000, 1.8, 1, 40, 40, 0.4, 10, seed=4)
