@@ -463,6 +463,8 @@ def main():
             pinned.append(t.numpy())
         h2d = sum(a.nbytes for a in pinned if a is not None)
         d2h = 0
+        # the results land in page-locked host buffers (allocated once)
+        res_bufs = [dupin.result_buffers(g.n, True, True, True, pinned=True) for _ in epss]
 
         def e2e_step():
             nonlocal d2h
@@ -473,7 +475,7 @@ def main():
             d2h = 0
             ps = [dupin.make_params(metric, k, e) for e in epss]
             for o in dupin.peel_batch([gg] * len(ps), ps, want_rounds=True, want_trace=True, want_mask=True,
-                                      stream=stream):
+                                      stream=stream, buffers=res_bufs):
                 d2h += o.peel_round.nbytes + o.best_mask.nbytes + 32 * (o.n_rounds + 1)
             gg.free()
 

@@ -113,13 +113,15 @@ typedef struct {
 int dupin_graph_load(const dupin_graph_desc *desc, void *stream, dupin_graph **out);
 
 /*
- * Release a graph.  NULL is accepted.  Its peeling workspaces (device
- * memory sized for the graph) are kept, at most 8 per process, for later
- * graphs they fit; dupin_trim_cache() frees the kept ones.
+ * Release a graph (after all work on it is done; the call waits for the
+ * device).  NULL is accepted.  Its arrays return to the library's memory
+ * pool and its peeling workspaces are kept, at most 8 per process, for later
+ * graphs they fit; dupin_trim_cache() releases both.
  */
 int dupin_graph_free(dupin_graph *g);
 
-/* Free the peeling workspaces kept from freed graphs (see dupin_graph_free). */
+/* Free the peeling workspaces kept from freed graphs and release the graph
+ * memory the library's pool keeps on the current device (see dupin_graph_free). */
 int dupin_trim_cache(void);
 
 /* n = vertices, m = undirected edges, arcs = 2m, device_bytes = bytes held. */

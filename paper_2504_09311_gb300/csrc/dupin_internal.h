@@ -80,6 +80,8 @@ void workspace_free(PeelWorkspace *ws);
 void workspace_free(PeelWorkspace *ws, cudaStream_t s);
 // a freed graph's workspace: kept for a later graph it fits, or freed
 void workspace_release(PeelWorkspace *ws);
+// release the freed graph buffers the library's memory pool keeps (current device)
+void graph_pool_trim();
 int workspace_ensure(dupin_graph *g, const PeelPlan &plan);
 // workspace k of graph g (0: the one dupin_peel uses), allocated or grown for plan
 PeelWorkspace *workspace_slot(dupin_graph *g, int k, const PeelPlan &plan, int *rc);

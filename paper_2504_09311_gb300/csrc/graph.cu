@@ -16,7 +16,55 @@
 
 #include <string>
 
+#include <map>
+#include <mutex>
 #include "dupin_internal.h"
+
+// Device buffers of graphs come from a memory pool of the library's own,
+// stream-ordered, that keeps freed memory (dupin_trim_cache releases it): a
+// caller that loads a new graph for every peel then pays no cudaMalloc /
+// cudaFree for the adjacency and the loader's temporaries.
+static cudaMemPool_t graph_pool(int dev) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+    return pool;
+}
+
+static cudaError_t galloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool = graph_pool(dev);
+    if (!bytes) bytes = 8;
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
+static void gfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+void graph_pool_trim() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool = graph_pool(dev);
+    if (pool) cudaMemPoolTrimTo(pool, 0);
+}
 
 __global__ void k_add_offset_i64(long long *x, long long n, long long add) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -103,7 +151,7 @@ static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
     unsigned long long *hist = nullptr;
     int *nh = nullptr, *slot_of = nullptr;
     unsigned long long h[64];
-    cudaError_t e = cudaMalloc((void **)&hist, 64 * sizeof(unsigned long long) + sizeof(int));
+    cudaError_t e = galloc((void **)&hist, 64 * sizeof(unsigned long long) + sizeof(int), s);
     if (e != cudaSuccess) return dupin_cuda_fail(e, "hub histogram");
     nh = (int *)(hist + 64);
     e = cudaMemsetAsync(hist, 0, 64 * sizeof(unsigned long long) + sizeof(int), s);
@@ -113,7 +161,7 @@ static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFree(hist);
+        gfree(hist, s);
         return dupin_cuda_fail(e, "hub histogram");
     }
     // smallest power-of-two threshold >= DUPIN_HUB_MIN_DEG keeping at most
@@ -127,12 +175,12 @@ static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
         bstar = b;
     }
     if (bstar < 0 || cum == 0) {
-        cudaFree(hist);
+        gfree(hist, s);
         return DUPIN_OK;
     }
     const long long thr = 1LL << bstar;
-    e = cudaMalloc((void **)&g->hubs, sizeof(int) * (size_t)cum);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&slot_of, sizeof(int) * (size_t)g->n);
+    e = galloc((void **)&g->hubs, sizeof(int) * (size_t)cum, s);
+    if (e == cudaSuccess) e = galloc((void **)&slot_of, sizeof(int) * (size_t)g->n, s);
     if (e == cudaSuccess) {
         k_fill_i32<<<grid, 256, 0, s>>>(slot_of, g->n, -1);
         k_pick_hubs<<<grid, 256, 0, s>>>(g->rp, g->n, thr, slot_of, g->hubs, nh, (int)cum);
@@ -140,8 +188,8 @@ static int select_hubs(dupin_graph *g, int grid, cudaStream_t s) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(slot_of);
-    cudaFree(hist);
+    gfree(slot_of, s);
+    gfree(hist, s);
     if (e != cudaSuccess) return dupin_cuda_fail(e, "hub selection");
     g->n_hubs = (int)cum;
     g->bytes += (long long)sizeof(int) * (long long)cum;
@@ -152,11 +200,14 @@ static void graph_release(dupin_graph *g) {
     if (!g) return;
     workspace_release(g->ws);
     for (PeelWorkspace *w : g->ws_more) workspace_release(w);
-    cudaFree(g->hubs);
-    cudaFree(g->rp);
-    cudaFree(g->col);
-    cudaFree(g->cw);
-    cudaFree(g->a);
+    // no work on the graph may be in flight when it is freed (as cudaFree would
+    // have enforced); then its buffers go back to the pool
+    cudaDeviceSynchronize();
+    gfree(g->hubs, 0);
+    gfree(g->rp, 0);
+    gfree(g->col, 0);
+    gfree(g->cw, 0);
+    gfree(g->a, 0);
     delete g;
 }
 
@@ -196,7 +247,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **p, size_t bytes) {
         if (e != cudaSuccess) return;
-        e = cudaMalloc(p, bytes ? bytes : 8);
+        e = galloc(p, bytes ? bytes : 8, s);
         if (e == cudaSuccess) g->bytes += (long long)bytes;
     };
     alloc((void **)&g->rp, sizeof(long long) * (size_t)(n + 1));
@@ -204,10 +255,10 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
     if (has_w) alloc((void **)&g->cw, sizeof(long long) * (size_t)arcs);
     if (d->vertex_w) alloc((void **)&g->a, sizeof(long long) * (size_t)n);
     int *bad = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc((void **)&bad, sizeof(int));
+    if (e == cudaSuccess) e = galloc((void **)&bad, sizeof(int), s);
     if (e != cudaSuccess) {
         graph_release(g);
-        cudaFree(bad);
+        gfree(bad, s);
         cudaGetLastError();
         return dupin_fail(e == cudaErrorMemoryAllocation ? DUPIN_ERR_OOM : DUPIN_ERR_CUDA,
                           std::string("graph allocation: ") + cudaGetErrorString(e));
@@ -222,7 +273,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         if (_e != cudaSuccess) {                     \
             int _r = dupin_cuda_fail(_e, #expr);     \
             graph_release(g);                        \
-            cudaFree(bad);                           \
+            gfree(bad, s);                           \
             return _r;                               \
         }                                            \
     } while (0)
@@ -249,7 +300,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         else c0 = d->csc_ptr[0];
         if (c0 != 0) {
             graph_release(g);
-            cudaFree(bad);
+            gfree(bad, s);
             return dupin_fail(DUPIN_ERR_INVALID_ARG, "csc_ptr[0] must be 0");
         }
     } else {
@@ -268,17 +319,17 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
     TRY(cudaStreamSynchronize(s));
     if (hbad) {
         graph_release(g);
-        cudaFree(bad);
+        gfree(bad, s);
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "invalid CSR: offsets, ids or weights out of range");
     }
     // ids in range, no self-loops, and w_u(V) < 2^63 for the weights given
     {
         long long *w = nullptr;
         PeelCtl *ctl = nullptr;
-        TRY(cudaMalloc((void **)&w, sizeof(long long) * (size_t)(n > 0 ? n : 1)));
-        e = cudaMalloc((void **)&ctl, sizeof(PeelCtl));
+        TRY(galloc((void **)&w, sizeof(long long) * (size_t)(n > 0 ? n : 1), s));
+        e = galloc((void **)&ctl, sizeof(PeelCtl), s);
         if (e != cudaSuccess) {
-            cudaFree(w);
+            gfree(w, s);
             TRY(e);
         }
         PeelCtl hc;
@@ -293,7 +344,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         // without weights every arc is 1.0: validate ids with a temporary unit weight array
         long long *unit = nullptr;
         if (!has_w && arcs > 0) {
-            e = cudaMalloc((void **)&unit, sizeof(long long) * (size_t)arcs);
+            e = galloc((void **)&unit, sizeof(long long) * (size_t)arcs, s);
             if (e == cudaSuccess) k_fill_i64<<<grid, 256, 0, s>>>(unit, arcs, 1LL << 32);
         }
         dg.cw = has_w ? g->cw : unit;
@@ -302,18 +353,18 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         if (e == cudaSuccess && dg.cw) rc = launch_init_weights(dg, DUPIN_DW, w, nullptr, nullptr, ctl, true, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(w);
-        cudaFree(ctl);
-        cudaFree(unit);
+        gfree(w, s);
+        gfree(ctl, s);
+        gfree(unit, s);
         if (e != cudaSuccess || rc) {
             int r2 = rc ? rc : dupin_cuda_fail(e, "graph validation");
             graph_release(g);
-            cudaFree(bad);
+            gfree(bad, s);
             return r2;
         }
         if (hc.init_overflow) {
             graph_release(g);
-            cudaFree(bad);
+            gfree(bad, s);
             if (hc.init_overflow == 2) return dupin_fail(DUPIN_ERR_INVALID_ARG, "negative vertex weight");
             return dupin_fail(has_w ? DUPIN_ERR_OVERFLOW : DUPIN_ERR_INVALID_ARG,
                               "invalid graph: a neighbour id out of range, a self-loop, a negative weight, or a "
@@ -321,7 +372,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         }
     }
 #undef TRY
-    cudaFree(bad);
+    gfree(bad, s);
     rc = select_hubs(g, grid, s);
     if (rc) {
         graph_release(g);

@@ -1474,6 +1474,7 @@ extern "C" int dupin_trim_cache(void) {
         workspace_free(ws);
     }
     cudaSetDevice(dev);
+    graph_pool_trim();
     return DUPIN_OK;
 }
 

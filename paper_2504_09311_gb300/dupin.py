@@ -231,12 +231,23 @@ class PeelOutput:
     n_min_rule: int
     peel_round: Optional[object] = None
     best_mask: Optional[object] = None
-    trace_f: Optional[list] = None
+    trace_f_hi: Optional[object] = None  # f of every S_i as (hi, lo) words
+    trace_f_lo: Optional[object] = None
     trace_size: Optional[object] = None
     trace_peeled: Optional[object] = None
     n_bulk_rounds: int = 0
     phase_ms: Optional[list] = None
     tail_arcs: int = 0
+
+    @property
+    def trace_f(self) -> Optional[list]:
+        """f(S_i) for i = 0 .. n_rounds as Python ints (Q32.32), built on first use."""
+        if self.trace_f_hi is None:
+            return None
+        if not hasattr(self, "_trace_f"):
+            self._trace_f = [(int(h) << 64) + int(lo) for h, lo in zip(self.trace_f_hi.tolist(),
+                                                                       self.trace_f_lo.tolist())]
+        return self._trace_f
 
 
 def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> Result:
@@ -257,7 +268,7 @@ def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
         R = r.n_rounds + 1
         fh, fl, sz, pe = trace
         if isinstance(fh, np.ndarray):
-            out.trace_f = [(int(fh[i]) << 64) + int(np.uint64(fl[i])) for i in range(R)]
+            out.trace_f_hi, out.trace_f_lo = fh[:R], fl[:R]
             out.trace_size, out.trace_peeled = sz[:R], pe[:R]
     return out
 
@@ -302,23 +313,40 @@ def peel_batch_device(graphs: Sequence[Graph], params: Sequence[Params], peel_ro
     return R
 
 
+def result_buffers(n: int, want_rounds=True, want_mask=False, want_trace=False, pinned=False):
+    """Host result buffers (peel_round, best_mask, trace) for a graph of n vertices;
+    pinned=True places them in page-locked memory (through torch), so the result
+    copies run at full link speed."""
+    def arr(count, dtype):
+        if not pinned:
+            return np.empty(count, dtype)
+        import torch
+
+        tt = {np.dtype(np.int32): torch.int32, np.dtype(np.uint8): torch.uint8, np.dtype(np.int64): torch.int64,
+              np.dtype(np.uint64): torch.int64}[np.dtype(dtype)]
+        return torch.empty(count, dtype=tt, pin_memory=True).numpy().view(dtype)
+
+    pr = arr(n, np.int32) if want_rounds else None
+    mk = arr(n, np.uint8) if want_mask else None
+    trace = None
+    if want_trace:
+        cap = n + 2
+        trace = (arr(cap, np.int64), arr(cap, np.uint64), arr(cap, np.int64), arr(cap, np.int64))
+    return pr, mk, trace
+
+
 def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=True, want_trace=False, stream=None,
-               want_mask=False):
-    """dupin_peel_batch with host result buffers; returns a list of PeelOutput."""
+               want_mask=False, buffers=None):
+    """dupin_peel_batch with host result buffers; returns a list of PeelOutput.
+    buffers: optional per-graph (peel_round, best_mask, trace) from result_buffers()."""
     k = len(graphs)
     G = (ctypes.c_void_p * k)(*[g.handle.value for g in graphs])
     P = (Params * k)(*params)
     R = (Result * k)()
     keep = []
     for j, g in enumerate(graphs):
-        pr = np.empty(g.n, np.int32) if want_rounds else None
-        mk = np.empty(g.n, np.uint8) if want_mask else None
-        trace = None
-        cap = 0
-        if want_trace:
-            cap = g.n + 2
-            trace = (np.zeros(cap, np.int64), np.zeros(cap, np.uint64), np.zeros(cap, np.int64),
-                     np.zeros(cap, np.int64))
+        pr, mk, trace = buffers[j] if buffers is not None else result_buffers(g.n, want_rounds, want_mask, want_trace)
+        cap = len(trace[0]) if trace is not None else 0
         R[j] = _result_struct(pr, mk, trace, cap)
         keep.append((pr, mk, trace))
     check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
