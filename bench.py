@@ -173,6 +173,7 @@ def bench_batched(dupin, stream, args):
     tgen = time.perf_counter() - t0
     dgs = [dupin.Graph.from_synth(g) for g in gs]
     ps = [dupin.make_params("fd", 1, (1, 10)) for _ in gs]
+    cta_threads = dupin.batch_tune(dgs, ps, stream=stream)  # the autotuner picks the launch shape
     for _ in range(2):
         dupin.peel_batch(dgs, ps, want_rounds=False, stream=stream)
     torch.cuda.synchronize()
@@ -194,7 +195,8 @@ def bench_batched(dupin, stream, args):
     return {"workload": f"{args.windows} bipartite windows, edges log-uniform 1k..500k (total {edges}), FD, "
                         "eps=1/10, k=1", "graphs_per_s": args.windows / tb, "edges_per_s": edges / tb,
             "ms": tb * 1e3, "one_launch_per_graph_graphs_per_s": args.windows / tl, "speedup": tl / tb,
-            "identical_to_single": bool(same), "generation_s": round(tgen, 1)}
+            "identical_to_single": bool(same), "generation_s": round(tgen, 1),
+            "cta_threads": cta_threads, "one_cta_max_vertices": dupin.BATCH_CTA_MAX_N}
 
 
 def bench_serving(dupin, args, requests=2000, rate=2000.0):

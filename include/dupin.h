@@ -207,6 +207,36 @@ int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result,
 int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *params, dupin_result *results,
                      int64_t count, void *stream);
 
+/*
+ * Launch shape of the one-CTA-per-graph kernel used by dupin_peel_batch (and
+ * by the server) for graphs of at most DUPIN_BATCH_CTA_MAX_N vertices: CTAs of
+ * 128 threads (4 per SM) or of 256 threads (2 per SM).  Results do not depend
+ * on the shape; only the time does.  The choice is per device and process.
+ * By default a launch of at most 2 x (SM count) graphs (one wave of 256-thread
+ * CTAs: the GPU is not full, and wider CTAs finish each graph sooner) takes
+ * 256 threads and a larger launch 128.
+ *
+ * dupin_batch_set_threads: threads = 128 or 256 makes every launch on the
+ * current device take that shape; 0 restores the default rule; INVALID_ARG
+ * otherwise.
+ * dupin_batch_get_threads: writes the shape that launches of more than one
+ * wave take on the current device to *threads.
+ * dupin_batch_tune: the autotuner.  Peels the batch's graphs of at most
+ * DUPIN_BATCH_CTA_MAX_N vertices (larger ones are ignored) once per shape to
+ * warm up, then twice more per shape, timing each call on the host (the call
+ * synchronises 'stream'); the faster shape becomes the one that launches of
+ * more than one wave take on the current device (smaller launches keep 256
+ * threads), and its thread count is written to *threads (if non-NULL).  No
+ * result is returned; the graphs are not changed.  Errors as
+ * dupin_peel_batch, the shape then unchanged; INVALID_ARG if no graph of the
+ * batch is small enough.
+ */
+#define DUPIN_BATCH_CTA_MAX_N 131072
+int dupin_batch_set_threads(int threads);
+int dupin_batch_get_threads(int *threads);
+int dupin_batch_tune(dupin_graph *const *graphs, const dupin_params *params, int64_t count, void *stream,
+                     int *threads);
+
 /* ------------------------------------------------- peel without allocation */
 
 /*

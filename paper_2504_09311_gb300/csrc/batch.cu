@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -24,10 +25,11 @@
 #include "dupin_internal.h"
 #include "peel_device.cuh"
 
-#define CTA_THREADS 256
-#define CTA_WARPS (CTA_THREADS / 32)
-#define CTA_MAX_SEG 4096
+// Two launch shapes of the batched kernel, picked per device (default, or by
+// dupin_batch_tune): 128 threads x 4 CTAs per SM, or 256 threads x 2.
+#define CTA_MAX_SEG 2048
 #define CTA_MAX_N ((long long)CTA_MAX_SEG * TAIL_SEG)
+static_assert(CTA_MAX_N == DUPIN_BATCH_CTA_MAX_N, "header limit out of date");
 #define CTA_BIGROW 2048
 #define CTA_BIGLIST 64
 
@@ -50,7 +52,8 @@ struct CtaJob {
     long long *out;    // [8]: R, best round, best size, best f hi, best f lo, minimum-rule rounds, error, 0
 };
 
-__device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf, TailAcc<CTA_WARPS> *s_acc, long long *s_w,
+template <int NT>
+__device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf, TailAcc<NT / 32> *s_acc, long long *s_w,
                                              long long *s_pref, long long *s_fs, long long *s_fl, int *s_big,
                                              int *s_nbig, unsigned long long *s_lo, unsigned long long *s_hi) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -65,13 +68,13 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
 
     // ---- initial peeling weights w_u = a_u + sum_v c_uv (Sec. 2.2)
     if (tid == 0) *s_nbig = 0;
-    for (long long u = tid; u < n; u += CTA_THREADS) {
+    for (long long u = tid; u < n; u += NT) {
         const long long d = rp[u + 1] - rp[u];
         w[u] = dg ? (d << 32) : (J.a ? J.a[u] : 0);
     }
     __syncthreads();
     if (!dg) {
-        for (long long u = wid; u < n; u += CTA_WARPS) {
+        for (long long u = wid; u < n; u += (NT / 32)) {
             const long long b = rp[u], e = rp[u + 1];
             if (e - b > CTA_BIGROW) {
                 int k = 0;
@@ -93,13 +96,13 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         for (int k = 0; k < nb; k++) {
             const long long u = s_big[k];
             long long sum = 0;
-            for (long long p = rp[u] + tid; p < rp[u + 1]; p += CTA_THREADS) sum += cw[p];
+            for (long long p = rp[u] + tid; p < rp[u + 1]; p += NT) sum += cw[p];
             sum = warp_sum64(sum);
             if (lane == 0) s_w[wid] = sum;
             __syncthreads();
             if (tid == 0) {
                 long long t = 0;
-                for (int q = 0; q < CTA_WARPS; q++) t += s_w[q];
+                for (int q = 0; q < (NT / 32); q++) t += s_w[q];
                 w[u] += t;
             }
             __syncthreads();
@@ -109,7 +112,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
     // f(V) = sum_u (w_u + a_u) / 2; segment minima of round 1
     {
         unsigned long long lo = 0, hi = 0;
-        for (long long u = tid; u < n; u += CTA_THREADS) {
+        for (long long u = tid; u < n; u += NT) {
             add128(lo, hi, (unsigned long long)w[u], 0);
             if (!dg && J.a) add128(lo, hi, (unsigned long long)J.a[u], 0);
         }
@@ -120,7 +123,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         }
     }
     long long *first = segbuf + (1 & 1) * nseg;
-    for (int q = wid; q < nseg; q += CTA_WARPS) {
+    for (int q = wid; q < nseg; q += (NT / 32)) {
         const long long p = (long long)q * TAIL_SEG + 2 * lane;
         const long long w0 = p < n ? w[p] : -1, w1 = p + 1 < n ? w[p + 1] : -1;
         long long m = kMaxLL;
@@ -134,7 +137,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
     RoundState st;
     {
         unsigned long long lo = 0, hi = 0;
-        for (int q = 0; q < CTA_WARPS; q++) add128(lo, hi, s_lo[q], s_hi[q]);
+        for (int q = 0; q < (NT / 32); q++) add128(lo, hi, s_lo[q], s_hi[q]);
         st.f = mk128(lo, hi) >> 1;
     }
     st.round = 0;
@@ -164,11 +167,11 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         const long long i = R.i;
         const long long *cur = segbuf + (i & 1) * nseg;
         long long *nxt = segbuf + ((i + 1) & 1) * nseg;
-        TailAcc<CTA_WARPS> &acc = s_acc[i & 1];
+        TailAcc<NT / 32> &acc = s_acc[i & 1];
         // ---- select
         unsigned long long wlo = 0, whi = 0;
         long long mins = kMaxLL;  // new minimum over the segments this lane looked at
-        for (int q0 = wid * 32; q0 < nseg; q0 += CTA_THREADS) {
+        for (int q0 = wid * 32; q0 < nseg; q0 += NT) {
             const int q = q0 + lane;
             const long long sm = q < nseg ? cur[q] : kMaxLL;
             if (q < nseg) nxt[q] = sm;
@@ -254,7 +257,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         if (F <= TAIL_FAST) {
             int q = 0;
             long long qs = 0, ql = F > 0 ? s_fl[0] : 0;
-            for (long long x = tid;; x += CTA_THREADS) {
+            for (long long x = tid;; x += NT) {
                 while (q < F && x >= qs + ql) {
                     qs += ql;
                     q++;
@@ -264,7 +267,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
                 arc(s_fs[q] + (x - qs));
             }
         } else {
-            for (int c0 = 0; c0 < F; c0 += CTA_THREADS) {
+            for (int c0 = 0; c0 < F; c0 += NT) {
                 const int qq = c0 + tid;
                 long long deg = 0;
                 if (qq < F) {
@@ -272,12 +275,12 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
                     deg = rp[p + 1] - rp[p];
                 }
                 long long tot;
-                long long ex = block_excl_scan<CTA_WARPS>(deg, s_w, tot);
+                long long ex = block_excl_scan<NT / 32>(deg, s_w, tot);
                 s_pref[tid] = ex;
-                const int nq = (F - c0) < CTA_THREADS ? (F - c0) : CTA_THREADS;
+                const int nq = (F - c0) < NT ? (F - c0) : NT;
                 if (tid == 0) s_pref[nq] = tot;
                 __syncthreads();
-                for (long long x = tid; x < tot; x += CTA_THREADS) {
+                for (long long x = tid; x < tot; x += NT) {
                     const int e = smem_last_le(s_pref, nq, x);
                     const int p = J.front[c0 + e];
                     arc(rp[p] + (x - s_pref[e]));
@@ -319,7 +322,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         R = tail_plan(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, mins_all);
     }
     __syncthreads();
-    for (long long u = tid; u < n; u += CTA_THREADS) {
+    for (long long u = tid; u < n; u += NT) {
         const long long wv = w[u];
         J.pr[u] = wv < 0 ? (int)(-wv) : 0x7fffffff;
     }
@@ -335,15 +338,16 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
     }
 }
 
-__global__ void __launch_bounds__(CTA_THREADS, 2) k_peel_cta(const CtaJob *jobs, int njobs, int *next) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_peel_cta(const CtaJob *jobs, int njobs, int *next) {
     extern __shared__ __align__(16) long long s_seg[];  // 2 * CTA_MAX_SEG
-    __shared__ TailAcc<CTA_WARPS> s_acc[2];
-    __shared__ long long s_w[CTA_WARPS];
-    __shared__ long long s_pref[CTA_THREADS + 1];
+    __shared__ TailAcc<NT / 32> s_acc[2];
+    __shared__ long long s_w[(NT / 32)];
+    __shared__ long long s_pref[NT + 1];
     __shared__ long long s_fs[TAIL_FAST], s_fl[TAIL_FAST];
     __shared__ int s_big[CTA_BIGLIST];
     __shared__ int s_nbig;
-    __shared__ unsigned long long s_lo[CTA_WARPS], s_hi[CTA_WARPS];
+    __shared__ unsigned long long s_lo[(NT / 32)], s_hi[(NT / 32)];
     __shared__ int s_job;
     for (;;) {
         if (threadIdx.x == 0) s_job = atomicAdd(next, 1);
@@ -354,17 +358,51 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_peel_cta(const CtaJob *jobs,
         const CtaJob J = jobs[j];
         const int nseg = (int)((J.n + TAIL_SEG - 1) / TAIL_SEG);
         (void)nseg;
-        cta_peel_one(J, s_seg, s_acc, s_w, s_pref, s_fs, s_fl, s_big, &s_nbig, s_lo, s_hi);
+        cta_peel_one<NT>(J, s_seg, s_acc, s_w, s_pref, s_fs, s_fl, s_big, &s_nbig, s_lo, s_hi);
         __syncthreads();
     }
+}
+
+// the launch shapes: threads per CTA, CTAs per SM the kernel is bounded for
+struct CtaShape {
+    int threads;
+    const void *fn;
+};
+static const CtaShape kCtaShapes[2] = {{128, (const void *)k_peel_cta<128, 4>}, {256, (const void *)k_peel_cta<256, 2>}};
+// Per device: the shape of launches with more graphs than one wave of the
+// widest shape holds ('large', tuned or default), or one shape for every
+// launch ('forced').  A launch that fits one wave of 256-thread CTAs leaves
+// SMs idle with either shape, so it takes the wider CTAs, which finish each
+// graph sooner (the serving case: few requests per launch).
+struct ShapeSel {
+    int large = 0;
+    bool forced = false;
+};
+static std::mutex g_shape_mu;
+static std::map<int, ShapeSel> g_shape;
+static thread_local int t_tune_shape = -1;  // the autotuner's shape under test
+
+static ShapeSel shape_sel(int dev) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_shape.find(dev);
+    return it == g_shape.end() ? ShapeSel() : it->second;
+}
+
+static int cta_shape_for(int dev, size_t njobs, int sms) {
+    if (t_tune_shape >= 0) return t_tune_shape;
+    const ShapeSel sel = shape_sel(dev);
+    if (sel.forced) return sel.large;
+    return njobs <= (size_t)2 * sms ? 1 : sel.large;
 }
 
 static int set_cta_smem() {
     static bool done = false;
     if (done) return DUPIN_OK;
-    cudaError_t e = cudaFuncSetAttribute(k_peel_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * CTA_MAX_SEG * sizeof(long long)));
-    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaFuncSetAttribute(k_peel_cta)");
+    for (const CtaShape &c : kCtaShapes) {
+        cudaError_t e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(2 * CTA_MAX_SEG * sizeof(long long)));
+        if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaFuncSetAttribute(k_peel_cta)");
+    }
     done = true;
     return DUPIN_OK;
 }
@@ -489,14 +527,17 @@ int cta_batch_enqueue(dupin_graph *const *graphs, const dupin_params *params, du
     int sms = 0, dev = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel_cta, CTA_THREADS, 2 * CTA_MAX_SEG * sizeof(long long));
+    const CtaShape &shape = kCtaShapes[cta_shape_for(dev, nj, sms)];
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shape.fn, shape.threads, 2 * CTA_MAX_SEG * sizeof(long long));
     if (occ < 1) occ = 1;
     const int grid = (int)std::min<long long>((long long)nj, (long long)sms * occ);
     e = cudaMemcpyAsync(arena, jobs.data(), sizeof(CtaJob) * nj, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(next, 0, sizeof(int), s);
     if (e == cudaSuccess) {
-        k_peel_cta<<<grid, CTA_THREADS, 2 * CTA_MAX_SEG * sizeof(long long), s>>>((const CtaJob *)arena, (int)nj, next);
-        e = cudaGetLastError();
+        const CtaJob *jobs_dev = (const CtaJob *)arena;
+        int njobs = (int)nj;
+        void *args[] = {(void *)&jobs_dev, (void *)&njobs, (void *)&next};
+        e = cudaLaunchKernel(shape.fn, dim3(grid), dim3(shape.threads), args, 2 * CTA_MAX_SEG * sizeof(long long), s);
     }
     if (e != cudaSuccess) {
         cudaFreeAsync(B->arena, s);
@@ -738,5 +779,74 @@ extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *
             return dupin_fail(rc, "graph " + std::to_string((long long)j) + ": " + buf);
         }
     }
+    return DUPIN_OK;
+}
+
+extern "C" int dupin_batch_set_threads(int threads) {
+    ShapeSel sel;
+    if (threads == 128) sel = ShapeSel{0, true};
+    else if (threads == 256) sel = ShapeSel{1, true};
+    else if (threads != 0) return dupin_fail(DUPIN_ERR_INVALID_ARG, "threads must be 0, 128 or 256");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape[dev] = sel;
+    return DUPIN_OK;
+}
+
+extern "C" int dupin_batch_get_threads(int *threads) {
+    if (!threads) return dupin_fail(DUPIN_ERR_INVALID_ARG, "threads is NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaGetDevice");
+    *threads = kCtaShapes[shape_sel(dev).large].threads;
+    return DUPIN_OK;
+}
+
+// The autotuner: time every launch shape on the caller's own batch and keep
+// the fastest for this device's launches of more than one wave.
+extern "C" int dupin_batch_tune(dupin_graph *const *graphs, const dupin_params *params, int64_t count,
+                                void *stream, int *threads) {
+    if (count < 0) return dupin_fail(DUPIN_ERR_INVALID_ARG, "count < 0");
+    if (count > 0 && (!graphs || !params)) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graphs and params must be non-NULL");
+    std::vector<dupin_graph *> gs;
+    std::vector<dupin_params> ps;
+    for (int64_t j = 0; j < count; j++) {
+        if (!graphs[j]) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph " + std::to_string((long long)j) + " is NULL");
+        if (graphs[j]->n < 1 || graphs[j]->n > CTA_MAX_N) continue;
+        dupin_params p = params[j];
+        p.flags &= ~DUPIN_RESULT_DEVICE;  // results stay in the batch arena
+        gs.push_back(graphs[j]);
+        ps.push_back(p);
+    }
+    if (gs.empty()) return dupin_fail(DUPIN_ERR_INVALID_ARG, "no graph of the batch fits one CTA");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaGetDevice");
+    std::vector<dupin_result> res(gs.size());
+    const int nshape = (int)(sizeof(kCtaShapes) / sizeof(kCtaShapes[0]));
+    std::vector<double> best(nshape, 1e300);
+    int rc = DUPIN_OK;
+    for (int rep = 0; rep < 3 && rc == DUPIN_OK; rep++) {
+        for (int i = 0; i < nshape && rc == DUPIN_OK; i++) {
+            t_tune_shape = i;
+            memset(res.data(), 0, sizeof(dupin_result) * res.size());
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = dupin_peel_batch(gs.data(), ps.data(), res.data(), (int64_t)gs.size(), stream);
+            const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            t_tune_shape = -1;
+            if (rep > 0) best[i] = std::min(best[i], t);  // the first pass warms up
+        }
+    }
+    if (rc) return rc;
+    int pick = 0;
+    for (int i = 1; i < nshape; i++)
+        if (best[i] < best[pick]) pick = i;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        g_shape[dev] = ShapeSel{pick, false};
+    }
+    if (threads) *threads = kCtaShapes[pick].threads;
     return DUPIN_OK;
 }

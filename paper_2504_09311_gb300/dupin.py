@@ -72,9 +72,10 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ["dupin_graph_load", "dupin_graph_free", "dupin_graph_info", "dupin_peel", "dupin_peel_batch",
            "dupin_serve_create", "dupin_serve_submit", "dupin_serve_poll", "dupin_serve_wait", "dupin_serve_stats",
            "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc", "dupin_struct_size",
-           "dupin_trim_cache"]
+           "dupin_trim_cache", "dupin_batch_set_threads", "dupin_batch_get_threads", "dupin_batch_tune"]
 
 NOALLOC_MAX_N = 8192
+BATCH_CTA_MAX_N = 131072
 
 _lib = None
 
@@ -103,6 +104,9 @@ def lib():
         L.dupin_peel_noalloc.argtypes = [i64, P, P, P, P, ctypes.POINTER(Params), P, ctypes.POINTER(Result), P]
         L.dupin_version.restype = ctypes.c_char_p
         L.dupin_struct_size.argtypes = [ctypes.c_char_p]
+        L.dupin_batch_set_threads.argtypes = [ctypes.c_int]
+        L.dupin_batch_get_threads.argtypes = [P]
+        L.dupin_batch_tune.argtypes = [P, P, i64, P, P]
         for nm in EXPORTS:
             if nm not in ("dupin_version", "dupin_struct_size"):
                 getattr(L, nm).restype = ctypes.c_int
@@ -352,6 +356,28 @@ def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=Tr
     check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
                                  ctypes.cast(R, ctypes.c_void_p), k, _stream(stream)))
     return [_output(R[j], keep[j][0], keep[j][1], keep[j][2]) for j in range(k)]
+
+
+def batch_threads(threads=None) -> int:
+    """Get (or, with threads = 128 / 256 / 0 for the default, set) the current
+    device's launch shape of the one-CTA-per-graph batched kernel."""
+    if threads is not None:
+        check(lib().dupin_batch_set_threads(int(threads)))
+    t = ctypes.c_int()
+    check(lib().dupin_batch_get_threads(ctypes.byref(t)))
+    return t.value
+
+
+def batch_tune(graphs: Sequence[Graph], params: Sequence[Params], stream=None) -> int:
+    """dupin_batch_tune: time each launch shape on this batch, keep the faster
+    for the current device; returns its threads per CTA."""
+    k = len(graphs)
+    G = (ctypes.c_void_p * k)(*[g.handle.value for g in graphs])
+    P = (Params * k)(*params)
+    t = ctypes.c_int()
+    check(lib().dupin_batch_tune(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p), k,
+                                 _stream(stream), ctypes.byref(t)))
+    return t.value
 
 
 def peel_noalloc(n, row_ptr, col_idx, arc_w, vertex_w, params: Params, peel_round, best_mask=None, trace=None,

@@ -76,6 +76,50 @@ def test_batch_equals_single(dupin):
         dg.free()
 
 
+def test_batch_shapes_and_tune(dupin):
+    """Both launch shapes of the one-CTA kernel give the same results, the
+    graphs on either side of the one-CTA limit included; the autotuner keeps
+    one of the two shapes."""
+    lim = dupin.BATCH_CTA_MAX_N
+    gs = window_graphs(12, seed=5)
+    for n in (lim, lim + 1):  # the largest one-CTA graph, the smallest that is not
+        g = synth.random_general(n, 4 * n, seed=n)
+        synth.with_weights(g, "fd", seed=1)
+        gs.append(g)
+    assert gs[-2].n == lim and gs[-1].n == lim + 1
+    dgs = [dupin.Graph.from_synth(g) for g in gs]
+    params = [dupin.make_params("fd", 1 + j % 2, (1, 10), flags=dupin.LPO if j % 4 == 1 else 0)
+              for j in range(len(gs))]
+    keep = dupin.batch_threads()
+    try:
+        outs = {}
+        for t in (128, 256):
+            assert dupin.batch_threads(t) == t
+            outs[t] = dupin.peel_batch(dgs, params, want_rounds=True, want_trace=True)
+        for j in range(len(gs)):
+            same(outs[128][j], outs[256][j], j)
+        for j in (0, len(gs) - 2, len(gs) - 1):
+            p = params[j]
+            r = oracle.peel_batch(oracle.Graph.from_synth(gs[j], "fd"), p.k_mult, (p.eps_num, p.eps_den),
+                                  flags=oracle.FLAG_LPO if p.flags & dupin.LPO else 0)
+            assert np.array_equal(outs[128][j].peel_round, r.peel_round), j
+            assert outs[128][j].trace_f == r.trace_f, j
+        dupin.batch_threads(0)  # the default rule: this small launch takes 256 threads
+        for j, o in enumerate(dupin.peel_batch(dgs, params, want_rounds=True, want_trace=True)):
+            same(o, outs[256][j], j)
+        t = dupin.batch_tune(dgs, params)
+        assert t in (128, 256) and dupin.batch_threads() == t
+        with pytest.raises(dupin.DupinError):
+            dupin.batch_tune(dgs[-1:], params[-1:])  # nothing small enough to time
+        assert dupin.batch_threads() == t
+        with pytest.raises(dupin.DupinError):
+            dupin.batch_threads(64)
+    finally:
+        dupin.batch_threads(keep)
+        for dg in dgs:
+            dg.free()
+
+
 def test_batch_large_concurrent(dupin):
     """Several large peels in one call -- one graph under three eps, another
     under two settings, with a small graph mixed in -- run their grid-wide
