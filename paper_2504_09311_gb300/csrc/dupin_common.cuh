@@ -233,8 +233,12 @@ __device__ __forceinline__ u128 mul_u128_u64(u128 a, unsigned long long b) {
 }
 
 // a/b > c/d for the best-prefix rule (strict: earliest round wins ties);
-// a, c < 2^96 and b, d < 2^31, so both products fit in 128 bits
+// a, c < 2^96 and b, d < 2^31, so both products fit in 128 bits.  NARROW:
+// a, c < 2^64 (one 64 x 64 -> 128-bit product each).
+template <bool NARROW = false>
 __device__ __forceinline__ bool frac_gt(u128 a, long long b, u128 c, long long d) {
+    if (NARROW)
+        return (u128)(unsigned long long)a * (unsigned long long)d > (u128)(unsigned long long)c * (unsigned long long)b;
     return mul_u128_u64(a, (unsigned long long)d) > mul_u128_u64(c, (unsigned long long)b);
 }
 
@@ -260,13 +264,24 @@ __device__ __forceinline__ long long warp_sum64(long long x) {
     return x;
 }
 
+// minimum over the warp, in every lane: the high words' minimum, then the
+// minimum low word among the lanes that hold it (two 32-bit warp reductions)
 __device__ __forceinline__ long long warp_min64(long long x) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        long long o = __shfl_down_sync(0xffffffffu, x, d);
-        x = o < x ? o : x;
-    }
-    return x;
+    const int hi = (int)(x >> 32);
+    const int mh = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? (unsigned)x : 0xffffffffu);
+    return (long long)(((unsigned long long)(unsigned)mh << 32) | ml);
+}
+
+// sum over the warp, in every lane, exact while the total is below 2^64:
+// three 32-bit warp reductions of 21-bit chunks (a chunk's sum over 32
+// lanes stays below 2^27)
+__device__ __forceinline__ unsigned long long warp_sum64_redux(unsigned long long x) {
+    const unsigned M = (1u << 21) - 1;
+    const unsigned s0 = __reduce_add_sync(0xffffffffu, (unsigned)x & M);
+    const unsigned s1 = __reduce_add_sync(0xffffffffu, (unsigned)(x >> 21) & M);
+    const unsigned s2 = __reduce_add_sync(0xffffffffu, (unsigned)(x >> 42));
+    return (unsigned long long)s0 + ((unsigned long long)s1 << 21) + ((unsigned long long)s2 << 42);
 }
 
 // inclusive warp scan of a 64-bit value

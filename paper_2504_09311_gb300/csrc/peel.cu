@@ -965,14 +965,13 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
 // selected vertices, expands the frontier's arcs (from L2) with shared-memory
 // atomics, and then every warp closes the round and plans the next one
 // itself from the same shared data: two block barriers per round.
-__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ TailAcc<TAIL_WARPS> s_acc[2];
-    __shared__ long long s_w[TAIL_WARPS];
-    __shared__ long long s_pref[TAIL_THREADS + 1];
-
+// NARROW: f < 2^62 and the best f < 2^64 when the tail starts, so every sum
+// a round forms (at most 2f) fits 64 bits; the sums then take 64-bit adds
+// and 32-bit warp reductions, the products 64 x 64 -> 128-bit multiplies.
+template <bool NARROW>
+__device__ __forceinline__ void peel_tail_body(const PeelArgs &A, unsigned char *smem, TailAcc<TAIL_WARPS> *s_acc,
+                                               long long *s_w, long long *s_pref) {
     PeelCtl *ctl = A.ctl;
-    if (ctl->status != ST_TAIL || ctl->error) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long L = ctl->live_len;
     const int nseg = (int)((L + TAIL_SEG - 1) / TAIL_SEG);
@@ -1014,7 +1013,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         if (lane == 0) first[q] = m;
     }
     __syncthreads();
-    TailRound R = tail_plan(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, seg_global_min(first, nseg));
+    TailRound R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, seg_global_min(first, nseg));
     int err = 0;
     while (!R.done) {
         if (R.i > A.max_rounds) {
@@ -1067,18 +1066,24 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                     unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
                     if (s0) {
                         tw[p] = -i;
-                        add128(wlo, whi, (unsigned long long)v.x, 0);
+                        if (NARROW) wlo += (unsigned long long)v.x;
+                        else add128(wlo, whi, (unsigned long long)v.x, 0);
                         tf[slot++] = (unsigned short)p;
                     }
                     if (s1) {
                         tw[p + 1] = -i;
-                        add128(wlo, whi, (unsigned long long)v.y, 0);
+                        if (NARROW) wlo += (unsigned long long)v.y;
+                        else add128(wlo, whi, (unsigned long long)v.y, 0);
                         tf[slot] = (unsigned short)(p + 1);
                     }
                 }
             }
         }
-        warp_sum128(wlo, whi);
+        if (NARROW) {
+            if (__any_sync(0xffffffffu, wlo != 0)) wlo = warp_sum64_redux(wlo);
+        } else if (__any_sync(0xffffffffu, (wlo | whi) != 0)) {
+            warp_sum128(wlo, whi);
+        }
         mins = warp_min64(mins);
         if (lane == 0) {
             acc.wlo[wid] = wlo;
@@ -1099,7 +1104,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                 atomicMin(&nxt[v / TAIL_SEG], old - c);
                 mind = old - c < mind ? old - c : mind;
             } else if (wv == -i) {
-                add128(ilo, ihi, (unsigned long long)c, 0);
+                if (NARROW) ilo += (unsigned long long)c;
+                else add128(ilo, ihi, (unsigned long long)c, 0);
             }
         };
         // TAIL_ILP arcs per thread at a time: their loads from L2 are issued
@@ -1119,32 +1125,35 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                 if (pos[u] >= 0) apply(cv[u], cc[u]);
         };
         if (F <= TAIL_FAST) {
-            // every thread walks the concatenation of the F arc ranges
-            // (offsets in shared memory), advancing a running offset
-            int q = 0, qp = F > 0 ? tf[0] : 0;
-            long long qs = 0, ql = F > 0 ? toff[qp + 1] - toff[qp] : 0;
-            for (long long x0 = tid;; x0 += TAIL_ILP * TAIL_THREADS) {
+            // the frontier's arcs in chunks of 32 consecutive arcs of one
+            // vertex: chunk c goes to warp c % TAIL_WARPS, TAIL_ILP of a warp's
+            // chunks in flight at once; the walk is the same in every lane
+            // (broadcast shared loads, no divergence)
+            int e = 0, cbase = 0;
+            int p0 = F > 0 ? tf[0] : 0;
+            int a0 = F > 0 ? toff[p0] : 0, a1 = F > 0 ? toff[p0 + 1] : 0;
+            int c = wid;
+            while (e < F) {
                 long long pos[TAIL_ILP];
-                int got = 0;
 #pragma unroll
                 for (int u = 0; u < TAIL_ILP; u++) {
-                    const long long x = x0 + (long long)u * TAIL_THREADS;
-                    while (q < F && x >= qs + ql) {
-                        qs += ql;
-                        q++;
-                        if (q < F) {
-                            qp = tf[q];
-                            ql = toff[qp + 1] - toff[qp];
+                    pos[u] = -1;
+                    while (e < F && c >= cbase + ((a1 - a0 + 31) >> 5)) {
+                        cbase += (a1 - a0 + 31) >> 5;
+                        e++;
+                        if (e < F) {
+                            p0 = tf[e];
+                            a0 = toff[p0];
+                            a1 = toff[p0 + 1];
                         }
                     }
-                    pos[u] = -1;
-                    if (q < F) {
-                        pos[u] = toff[qp] + (x - qs);
-                        got++;
+                    if (e < F) {
+                        const int a = a0 + (c - cbase) * 32 + lane;
+                        if (a < a1) pos[u] = a;
+                        c += TAIL_WARPS;
                     }
                 }
                 arcs(pos);
-                if (got < TAIL_ILP) break;
             }
         } else {
             for (int c0 = 0; c0 < F; c0 += TAIL_THREADS) {
@@ -1177,7 +1186,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
                 __syncthreads();
             }
         }
-        warp_sum128(ilo, ihi);
+        if (NARROW) {
+            if (__any_sync(0xffffffffu, ilo != 0)) ilo = warp_sum64_redux(ilo);
+        } else if (__any_sync(0xffffffffu, (ilo | ihi) != 0)) {
+            warp_sum128(ilo, ihi);
+        }
         mind = warp_min64(mind);
         if (lane == 0) {
             acc.ilo[wid] = ilo;
@@ -1188,18 +1201,20 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         // ---- every warp: close round i and plan round i + 1 (same values everywhere)
         u128 wsel, internal;
         long long mins_all;
-        tail_acc_sum(acc, wsel, internal, mins_all);
+        tail_acc_sum<TAIL_WARPS, NARROW>(acc, wsel, internal, mins_all);
         st.f = st.f - (wsel - (internal >> 1));
         st.scan += L;
         st.size -= F;
         st.round = i;
         st.n_min_rule += R.minrule ? 1 : 0;
-        if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
+        // the best prefix and the trace are kept by the last warp alone: its
+        // select covers the fewest segments (the tail has at most 234 of 64)
+        if (wid == TAIL_WARPS - 1 && st.size > 0 && frac_gt<NARROW>(st.f, st.size, st.bf, st.best_size)) {
             st.bf = st.f;
             st.best_size = st.size;
             st.best_round = i;
         }
-        if (tid == 0 && i < A.tr_cap) {
+        if (tid == (TAIL_WARPS - 1) * 32 && i < A.tr_cap) {
             A.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
             A.tr_f_lo[i] = (unsigned long long)st.f;
             A.tr_size[i] = st.size;
@@ -1209,7 +1224,13 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, mins_all);
+        R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, mins_all);
+    }
+    if (tid == (TAIL_WARPS - 1) * 32) {
+        s_pref[0] = st.best_round;
+        s_pref[1] = st.best_size;
+        s_pref[2] = (long long)(unsigned long long)st.bf;
+        s_pref[3] = (long long)(unsigned long long)(st.bf >> 64);
     }
     __syncthreads();
     for (long long p = tid; p < L; p += TAIL_THREADS) {
@@ -1217,6 +1238,9 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         if (wv < 0) A.pr[live[p]] = (int)(-wv);
     }
     if (tid == 0) {
+        st.best_round = s_pref[0];
+        st.best_size = s_pref[1];
+        st.bf = mk128((unsigned long long)s_pref[2], (unsigned long long)s_pref[3]);
         if (err) set_error(ctl, err);
         ctl->round = st.round;
         ctl->size = st.size;
@@ -1232,6 +1256,20 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
         ctl->scan_volume = st.scan;
         if (!err) ctl->status = ST_DONE;
     }
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TailAcc<TAIL_WARPS> s_acc[2];
+    __shared__ long long s_w[TAIL_WARPS];
+    __shared__ long long s_pref[TAIL_THREADS + 1];
+    const PeelCtl *ctl = A.ctl;
+    if (ctl->status != ST_TAIL || ctl->error) return;
+    // f only decreases, and a round's sums (removed weights, arcs inside
+    // the removed set) are at most 2f; the best f so far must fit 64 bits too
+    if (ctl->f_hi == 0 && ctl->f_lo < (1ull << 62) && ctl->bf_hi == 0)
+        peel_tail_body<true>(A, smem, s_acc, s_w, s_pref);
+    else peel_tail_body<false>(A, smem, s_acc, s_w, s_pref);
 }
 
 // best_mask[u] = (peel_round[u] > best_round) for a best round known on the host

@@ -178,12 +178,19 @@ struct TailAcc {
 
 // the round's totals from the warps' parts: lane j < NW loads part j and a
 // butterfly over the lanes leaves the totals in every lane (NW a power of
-// two, <= 32)
-template <int NW>
+// two, <= 32).  NARROW: the totals are below 2^64 (high words unused), and
+// 32-bit warp reductions replace the butterfly.
+template <int NW, bool NARROW = false>
 __device__ __forceinline__ void tail_acc_sum(const TailAcc<NW> &acc, u128 &wsel, u128 &internal, long long &mins) {
     static_assert(NW > 0 && NW <= 32 && (NW & (NW - 1)) == 0, "warps per block: a power of two");
     const int lane = threadIdx.x & 31;
     const bool in = lane < NW;
+    if (NARROW) {
+        wsel = (u128)warp_sum64_redux(in ? acc.wlo[lane] : 0ull);
+        internal = (u128)warp_sum64_redux(in ? acc.ilo[lane] : 0ull);
+        mins = warp_min64(in ? acc.mins[lane] : 0x7fffffffffffffffLL);
+        return;
+    }
     unsigned long long wl = in ? acc.wlo[lane] : 0, wh = in ? acc.whi[lane] : 0;
     unsigned long long il = in ? acc.ilo[lane] : 0, ih = in ? acc.ihi[lane] : 0;
     long long m = in ? acc.mins[lane] : 0x7fffffffffffffffLL;
@@ -234,7 +241,9 @@ __device__ __forceinline__ bool seg_candidate(long long sm, const TailRound &R) 
 // With Algorithm 4 (lpo) the round is a trim round while some live w < g(S),
 // i.e. m |S| <= f - 1: it removes w < max(tau_max, g), in the same
 // division-free form (w <= gpo_lt or w |S| <= f - 1).  A main round refines
-// tau_max (Algorithm 3) in both its forms.
+// tau_max (Algorithm 3) in both its forms.  NARROW: f and the g(S) it is compared with
+// are below 2^64.
+template <bool NARROW = false>
 __device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int use_min, int gpo, int lpo,
                                                RoundState &st, long long m) {
     TailRound R;
@@ -255,7 +264,8 @@ __device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int us
             return R;
         }
     }
-    const u128 X = mul_u128_u64(st.f, (unsigned long long)kD);
+    const u128 X = NARROW ? (u128)(unsigned long long)st.f * (unsigned long long)kD
+                          : mul_u128_u64(st.f, (unsigned long long)kD);
     R.Xhi = (unsigned long long)(X >> 64);
     R.Xlo = (unsigned long long)X;
     R.Y = (unsigned long long)D * (unsigned long long)st.size;
@@ -263,7 +273,7 @@ __device__ __forceinline__ TailRound tail_plan(long long kD, long long D, int us
     if (gpo && st.size > 0) {
         // floor and ceil-1 are monotone in g, so tau_max's integer forms can
         // only grow when g(S) exceeds the largest g seen so far
-        if (st.gm_s == 0 || frac_gt(st.f, st.size, st.gm_f, st.gm_s)) {
+        if (st.gm_s == 0 || frac_gt<NARROW>(st.f, st.size, st.gm_f, st.gm_s)) {
             st.gm_f = st.f;
             st.gm_s = st.size;
             const long long le = floor_ratio((unsigned long long)D, st.f, (unsigned long long)kD, st.size);

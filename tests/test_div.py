@@ -17,7 +17,7 @@ def test_floor_div_sat_matches_int128(tmp_path):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     exe = str(tmp_path / "div_check")
-    subprocess.run([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I",
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I", os.path.join(ROOT, "include"), "-I",
                     os.path.join(ROOT, "paper_2504_09311_gb300", "csrc"), "-o", exe,
                     os.path.join(ROOT, "tests", "div_check.cu")], check=True, capture_output=True)
     out = subprocess.run([exe, "2000000"], check=True, capture_output=True, text=True).stdout
