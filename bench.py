@@ -260,7 +260,7 @@ def cpu_baseline(g, metric, eps, k):
             "seconds": t2 - t1}
 
 
-TAIL_KERNEL_BEGIN = "__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(PeelArgs A) {"
+TAIL_KERNEL_BEGIN = "template <bool NARROW>\n__device__ __forceinline__ void peel_tail_body("
 TAIL_KERNEL_END = "// best_mask[u] = (peel_round[u] > best_round) for a best round known on the host"
 
 
