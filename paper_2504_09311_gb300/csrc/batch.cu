@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <map>
@@ -157,170 +158,197 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
         J.tr_size[0] = n;
         J.tr_peeled[0] = 0;
     }
-    TailRound R = tail_plan(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, seg_global_min(first, nseg));
     int err = 0;
-    while (!R.done) {
-        if (R.i > J.max_rounds) {
-            err = DUPIN_ERR_NO_PROGRESS;
-            break;
-        }
-        const long long i = R.i;
-        const long long *cur = segbuf + (i & 1) * nseg;
-        long long *nxt = segbuf + ((i + 1) & 1) * nseg;
-        TailAcc<NT / 32> &acc = s_acc[i & 1];
-        // ---- select
-        unsigned long long wlo = 0, whi = 0;
-        long long mins = kMaxLL;  // new minimum over the segments this lane looked at
-        for (int q0 = wid * 32; q0 < nseg; q0 += NT) {
-            const int q = q0 + lane;
-            const long long sm = q < nseg ? cur[q] : kMaxLL;
-            if (q < nseg) nxt[q] = sm;
-            const bool cand = seg_candidate(sm, R);
-            if (!cand) mins = sm < mins ? sm : mins;  // untouched by the select
-            unsigned cm = __ballot_sync(0xffffffffu, cand);
-            __syncwarp();
-            while (cm) {
-                const int qq = q0 + __ffs(cm) - 1;
-                cm &= cm - 1;
-                const long long p = (long long)qq * TAIL_SEG + 2 * lane;
-                const long long w0 = p < n ? w[p] : -1, w1 = p + 1 < n ? w[p + 1] : -1;
-                bool s0, s1;
-                if (R.minrule) {
-                    s0 = w0 >= 0 && w0 <= R.minw;
-                    s1 = w1 >= 0 && w1 <= R.minw;
-                } else {
-                    s0 = w0 >= 0 && (w0 <= R.gle || mul_le(w0, R.Y, R.Xhi, R.Xlo));
-                    s1 = w1 >= 0 && (w1 <= R.gle || mul_le(w1, R.Y, R.Xhi, R.Xlo));
-                }
-                long long m = kMaxLL;
-                if (w0 >= 0 && !s0) m = w0;
-                if (w1 >= 0 && !s1 && w1 < m) m = w1;
-                m = warp_min64(m);
-                if (lane == 0) {
-                    nxt[qq] = m;
-                    mins = m < mins ? m : mins;
-                }
-                const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
-                if (b0 | b1) {
-                    unsigned base = 0;
-                    if (lane == 0) base = atomicAdd(&acc.F, (unsigned)(__popc(b0) + __popc(b1)));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    const unsigned lt = (1u << lane) - 1u;
-                    unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
-                    if (s0) {
-                        w[p] = -i;
-                        add128(wlo, whi, (unsigned long long)w0, 0);
-                        J.front[slot] = (int)p;
-                        if (slot < TAIL_FAST) {
-                            s_fs[slot] = rp[p];
-                            s_fl[slot] = rp[p + 1] - rp[p];
-                        }
-                        slot++;
+    // the round loop in two forms: NARROW (f < 2^62, so every sum of a
+    // round fits 64 bits: 64-bit adds, 32-bit warp reductions) or wide
+    auto rounds = [&](auto narrow_tag) {
+        constexpr bool NARROW = decltype(narrow_tag)::value;
+        TailRound R = tail_plan<NARROW>(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, seg_global_min(first, nseg));
+        while (!R.done) {
+            if (R.i > J.max_rounds) {
+                err = DUPIN_ERR_NO_PROGRESS;
+                break;
+            }
+            const long long i = R.i;
+            const long long *cur = segbuf + (i & 1) * nseg;
+            long long *nxt = segbuf + ((i + 1) & 1) * nseg;
+            TailAcc<NT / 32> &acc = s_acc[i & 1];
+            // ---- select
+            unsigned long long wlo = 0, whi = 0;
+            long long mins = kMaxLL;  // new minimum over the segments this lane looked at
+            for (int q0 = wid * 32; q0 < nseg; q0 += NT) {
+                const int q = q0 + lane;
+                const long long sm = q < nseg ? cur[q] : kMaxLL;
+                if (q < nseg) nxt[q] = sm;
+                const bool cand = seg_candidate(sm, R);
+                if (!cand) mins = sm < mins ? sm : mins;  // untouched by the select
+                unsigned cm = __ballot_sync(0xffffffffu, cand);
+                __syncwarp();
+                while (cm) {
+                    const int qq = q0 + __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    const long long p = (long long)qq * TAIL_SEG + 2 * lane;
+                    const long long w0 = p < n ? w[p] : -1, w1 = p + 1 < n ? w[p + 1] : -1;
+                    bool s0, s1;
+                    if (R.minrule) {
+                        s0 = w0 >= 0 && w0 <= R.minw;
+                        s1 = w1 >= 0 && w1 <= R.minw;
+                    } else {
+                        s0 = w0 >= 0 && (w0 <= R.gle || mul_le(w0, R.Y, R.Xhi, R.Xlo));
+                        s1 = w1 >= 0 && (w1 <= R.gle || mul_le(w1, R.Y, R.Xhi, R.Xlo));
                     }
-                    if (s1) {
-                        w[p + 1] = -i;
-                        add128(wlo, whi, (unsigned long long)w1, 0);
-                        J.front[slot] = (int)(p + 1);
-                        if (slot < TAIL_FAST) {
-                            s_fs[slot] = rp[p + 1];
-                            s_fl[slot] = rp[p + 2] - rp[p + 1];
+                    long long m = kMaxLL;
+                    if (w0 >= 0 && !s0) m = w0;
+                    if (w1 >= 0 && !s1 && w1 < m) m = w1;
+                    m = warp_min64(m);
+                    if (lane == 0) {
+                        nxt[qq] = m;
+                        mins = m < mins ? m : mins;
+                    }
+                    const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
+                    if (b0 | b1) {
+                        unsigned base = 0;
+                        if (lane == 0) base = atomicAdd(&acc.F, (unsigned)(__popc(b0) + __popc(b1)));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        const unsigned lt = (1u << lane) - 1u;
+                        unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
+                        if (s0) {
+                            w[p] = -i;
+                            if (NARROW) wlo += (unsigned long long)w0;
+                            else add128(wlo, whi, (unsigned long long)w0, 0);
+                            J.front[slot] = (int)p;
+                            if (slot < TAIL_FAST) {
+                                s_fs[slot] = rp[p];
+                                s_fl[slot] = rp[p + 1] - rp[p];
+                            }
+                            slot++;
+                        }
+                        if (s1) {
+                            w[p + 1] = -i;
+                            if (NARROW) wlo += (unsigned long long)w1;
+                            else add128(wlo, whi, (unsigned long long)w1, 0);
+                            J.front[slot] = (int)(p + 1);
+                            if (slot < TAIL_FAST) {
+                                s_fs[slot] = rp[p + 1];
+                                s_fl[slot] = rp[p + 2] - rp[p + 1];
+                            }
                         }
                     }
                 }
             }
-        }
-        warp_sum128(wlo, whi);
-        mins = warp_min64(mins);
-        if (lane == 0) {
-            acc.wlo[wid] = wlo;
-            acc.whi[wid] = whi;
-            acc.mins[wid] = mins;
-        }
-        __syncthreads();
-        if (tid == 0) s_acc[(i + 1) & 1].F = 0;
-        const int F = (int)acc.F;
-        // ---- expand: every arc of the frontier (heads read from global memory)
-        unsigned long long ilo = 0, ihi = 0;
-        long long mind = kMaxLL;
-        auto arc = [&](long long pos) {
-            const int v = arc_head(col[pos], hubs);
-            const long long c = dg ? DUPIN_Q_ONE : cw[pos];
-            const long long wv = w[v];
-            if (wv >= 0) {
-                const long long old = (long long)atomicAdd((unsigned long long *)&w[v], (unsigned long long)(-c));
-                atomicMin(&nxt[v / TAIL_SEG], old - c);
-                mind = old - c < mind ? old - c : mind;
-            } else if (wv == -i) {
-                add128(ilo, ihi, (unsigned long long)c, 0);
+            if (NARROW) {
+                if (__any_sync(0xffffffffu, wlo != 0)) wlo = warp_sum64_redux(wlo);
+            } else if (__any_sync(0xffffffffu, (wlo | whi) != 0)) {
+                warp_sum128(wlo, whi);
             }
-        };
-        if (F <= TAIL_FAST) {
-            int q = 0;
-            long long qs = 0, ql = F > 0 ? s_fl[0] : 0;
-            for (long long x = tid;; x += NT) {
-                while (q < F && x >= qs + ql) {
-                    qs += ql;
-                    q++;
-                    if (q < F) ql = s_fl[q];
-                }
-                if (q >= F) break;
-                arc(s_fs[q] + (x - qs));
+            mins = warp_min64(mins);
+            if (lane == 0) {
+                acc.wlo[wid] = wlo;
+                acc.whi[wid] = whi;
+                acc.mins[wid] = mins;
             }
-        } else {
-            for (int c0 = 0; c0 < F; c0 += NT) {
-                const int qq = c0 + tid;
-                long long deg = 0;
-                if (qq < F) {
-                    const int p = J.front[qq];
-                    deg = rp[p + 1] - rp[p];
+            __syncthreads();
+            if (tid == 0) s_acc[(i + 1) & 1].F = 0;
+            const int F = (int)acc.F;
+            // ---- expand: every arc of the frontier (heads read from global memory)
+            unsigned long long ilo = 0, ihi = 0;
+            long long mind = kMaxLL;
+            auto arc = [&](long long pos) {
+                const int v = arc_head(col[pos], hubs);
+                const long long c = dg ? DUPIN_Q_ONE : cw[pos];
+                const long long wv = w[v];
+                if (wv >= 0) {
+                    const long long old = (long long)atomicAdd((unsigned long long *)&w[v], (unsigned long long)(-c));
+                    atomicMin(&nxt[v / TAIL_SEG], old - c);
+                    mind = old - c < mind ? old - c : mind;
+                } else if (wv == -i) {
+                    if (NARROW) ilo += (unsigned long long)c;
+                    else add128(ilo, ihi, (unsigned long long)c, 0);
                 }
-                long long tot;
-                long long ex = block_excl_scan<NT / 32>(deg, s_w, tot);
-                s_pref[tid] = ex;
-                const int nq = (F - c0) < NT ? (F - c0) : NT;
-                if (tid == 0) s_pref[nq] = tot;
-                __syncthreads();
-                for (long long x = tid; x < tot; x += NT) {
-                    const int e = smem_last_le(s_pref, nq, x);
-                    const int p = J.front[c0 + e];
-                    arc(rp[p] + (x - s_pref[e]));
+            };
+            if (F <= TAIL_FAST) {
+                // chunks of 32 consecutive arcs of one vertex, chunk c to warp
+                // c % (NT / 32); the walk is the same in every lane of a warp
+                int e = 0;
+                long long cbase = 0, c = wid;
+                long long a0 = F > 0 ? s_fs[0] : 0, ln = F > 0 ? s_fl[0] : 0;
+                while (e < F) {
+                    if (c >= cbase + ((ln + 31) >> 5)) {
+                        cbase += (ln + 31) >> 5;
+                        e++;
+                        if (e < F) {
+                            a0 = s_fs[e];
+                            ln = s_fl[e];
+                        }
+                        continue;
+                    }
+                    const long long off = (c - cbase) * 32 + lane;
+                    if (off < ln) arc(a0 + off);
+                    c += NT / 32;
                 }
-                __syncthreads();
+            } else {
+                for (int c0 = 0; c0 < F; c0 += NT) {
+                    const int qq = c0 + tid;
+                    long long deg = 0;
+                    if (qq < F) {
+                        const int p = J.front[qq];
+                        deg = rp[p + 1] - rp[p];
+                    }
+                    long long tot;
+                    long long ex = block_excl_scan<NT / 32>(deg, s_w, tot);
+                    s_pref[tid] = ex;
+                    const int nq = (F - c0) < NT ? (F - c0) : NT;
+                    if (tid == 0) s_pref[nq] = tot;
+                    __syncthreads();
+                    for (long long x = tid; x < tot; x += NT) {
+                        const int e = smem_last_le(s_pref, nq, x);
+                        const int p = J.front[c0 + e];
+                        arc(rp[p] + (x - s_pref[e]));
+                    }
+                    __syncthreads();
+                }
             }
+            if (NARROW) {
+                if (__any_sync(0xffffffffu, ilo != 0)) ilo = warp_sum64_redux(ilo);
+            } else if (__any_sync(0xffffffffu, (ilo | ihi) != 0)) {
+                warp_sum128(ilo, ihi);
+            }
+            mind = warp_min64(mind);
+            if (lane == 0) {
+                acc.ilo[wid] = ilo;
+                acc.ihi[wid] = ihi;
+                if (mind < acc.mins[wid]) acc.mins[wid] = mind;
+            }
+            __syncthreads();
+            // ---- every warp: close round i, plan round i + 1
+            u128 wsel, internal;
+            long long mins_all;
+            tail_acc_sum<NT / 32, NARROW>(acc, wsel, internal, mins_all);
+            st.f = st.f - (wsel - (internal >> 1));
+            st.size -= F;
+            st.round = i;
+            st.n_min_rule += R.minrule ? 1 : 0;
+            if (st.size > 0 && frac_gt<NARROW>(st.f, st.size, st.bf, st.best_size)) {
+                st.bf = st.f;
+                st.best_size = st.size;
+                st.best_round = i;
+            }
+            if (tid == 0 && i < J.tr_cap) {
+                J.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
+                J.tr_f_lo[i] = (unsigned long long)st.f;
+                J.tr_size[i] = st.size;
+                J.tr_peeled[i] = F;
+            }
+            if (F == 0) {
+                err = DUPIN_ERR_NO_PROGRESS;
+                break;
+            }
+            R = tail_plan<NARROW>(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, mins_all);
         }
-        warp_sum128(ilo, ihi);
-        mind = warp_min64(mind);
-        if (lane == 0) {
-            acc.ilo[wid] = ilo;
-            acc.ihi[wid] = ihi;
-            if (mind < acc.mins[wid]) acc.mins[wid] = mind;
-        }
-        __syncthreads();
-        // ---- every warp: close round i, plan round i + 1
-        u128 wsel, internal;
-        long long mins_all;
-        tail_acc_sum(acc, wsel, internal, mins_all);
-        st.f = st.f - (wsel - (internal >> 1));
-        st.size -= F;
-        st.round = i;
-        st.n_min_rule += R.minrule ? 1 : 0;
-        if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
-            st.bf = st.f;
-            st.best_size = st.size;
-            st.best_round = i;
-        }
-        if (tid == 0 && i < J.tr_cap) {
-            J.tr_f_hi[i] = (long long)(unsigned long long)(st.f >> 64);
-            J.tr_f_lo[i] = (unsigned long long)st.f;
-            J.tr_size[i] = st.size;
-            J.tr_peeled[i] = F;
-        }
-        if (F == 0) {
-            err = DUPIN_ERR_NO_PROGRESS;
-            break;
-        }
-        R = tail_plan(J.kD, J.D, J.use_min, J.gpo, J.lpo, st, mins_all);
-    }
+    };
+    // f only decreases and starts as the best f
+    if ((unsigned long long)(st.f >> 64) == 0 && (unsigned long long)st.f < (1ull << 62)) rounds(std::true_type{});
+    else rounds(std::false_type{});
     __syncthreads();
     for (long long u = tid; u < n; u += NT) {
         const long long wv = w[u];
