@@ -1079,17 +1079,8 @@ __device__ __forceinline__ void peel_tail_body(const PeelArgs &A, unsigned char 
                 }
             }
         }
-        if (NARROW) {
-            if (__any_sync(0xffffffffu, wlo != 0)) wlo = warp_sum64_redux(wlo);
-        } else if (__any_sync(0xffffffffu, (wlo | whi) != 0)) {
-            warp_sum128(wlo, whi);
-        }
-        mins = warp_min64(mins);
-        if (lane == 0) {
-            acc.wlo[wid] = wlo;
-            acc.whi[wid] = whi;
-            acc.mins[wid] = mins;
-        }
+        // the select's sums and minimum stay in registers: they are reduced
+        // with the expand's after it, off the path to the first barrier
         __syncthreads();
         // round i+1's counter was last read in round i-1: reset it now
         if (tid == 0) s_acc[(i + 1) & 1].F = 0;
@@ -1135,6 +1126,7 @@ __device__ __forceinline__ void peel_tail_body(const PeelArgs &A, unsigned char 
             int c = wid;
             while (e < F) {
                 long long pos[TAIL_ILP];
+                int got = 0;
 #pragma unroll
                 for (int u = 0; u < TAIL_ILP; u++) {
                     pos[u] = -1;
@@ -1151,9 +1143,14 @@ __device__ __forceinline__ void peel_tail_body(const PeelArgs &A, unsigned char 
                         const int a = a0 + (c - cbase) * 32 + lane;
                         if (a < a1) pos[u] = a;
                         c += TAIL_WARPS;
+                        got++;
                     }
                 }
-                arcs(pos);
+                if (got == 1) {  // one chunk: no predicated-off slots to issue
+                    if (pos[0] >= 0) apply(tcol[pos[0]], dg ? DUPIN_Q_ONE : tcw[pos[0]]);
+                } else {
+                    arcs(pos);
+                }
             }
         } else {
             for (int c0 = 0; c0 < F; c0 += TAIL_THREADS) {
@@ -1187,15 +1184,19 @@ __device__ __forceinline__ void peel_tail_body(const PeelArgs &A, unsigned char 
             }
         }
         if (NARROW) {
+            if (__any_sync(0xffffffffu, wlo != 0)) wlo = warp_sum64_redux(wlo);
             if (__any_sync(0xffffffffu, ilo != 0)) ilo = warp_sum64_redux(ilo);
-        } else if (__any_sync(0xffffffffu, (ilo | ihi) != 0)) {
-            warp_sum128(ilo, ihi);
+        } else {
+            if (__any_sync(0xffffffffu, (wlo | whi) != 0)) warp_sum128(wlo, whi);
+            if (__any_sync(0xffffffffu, (ilo | ihi) != 0)) warp_sum128(ilo, ihi);
         }
-        mind = warp_min64(mind);
+        mins = warp_min64(mind < mins ? mind : mins);
         if (lane == 0) {
+            acc.wlo[wid] = wlo;
+            acc.whi[wid] = whi;
             acc.ilo[wid] = ilo;
             acc.ihi[wid] = ihi;
-            if (mind < acc.mins[wid]) acc.mins[wid] = mind;
+            acc.mins[wid] = mins;
         }
         __syncthreads();
         // ---- every warp: close round i and plan round i + 1 (same values everywhere)
