@@ -236,17 +236,7 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
                     }
                 }
             }
-            if (NARROW) {
-                if (__any_sync(0xffffffffu, wlo != 0)) wlo = warp_sum64_redux(wlo);
-            } else if (__any_sync(0xffffffffu, (wlo | whi) != 0)) {
-                warp_sum128(wlo, whi);
-            }
-            mins = warp_min64(mins);
-            if (lane == 0) {
-                acc.wlo[wid] = wlo;
-                acc.whi[wid] = whi;
-                acc.mins[wid] = mins;
-            }
+            // the select's sums and minimum stay in registers until the expand's
             __syncthreads();
             if (tid == 0) s_acc[(i + 1) & 1].F = 0;
             const int F = (int)acc.F;
@@ -309,15 +299,19 @@ __device__ __forceinline__ void cta_peel_one(const CtaJob &J, long long *segbuf,
                 }
             }
             if (NARROW) {
+                if (__any_sync(0xffffffffu, wlo != 0)) wlo = warp_sum64_redux(wlo);
                 if (__any_sync(0xffffffffu, ilo != 0)) ilo = warp_sum64_redux(ilo);
-            } else if (__any_sync(0xffffffffu, (ilo | ihi) != 0)) {
-                warp_sum128(ilo, ihi);
+            } else {
+                if (__any_sync(0xffffffffu, (wlo | whi) != 0)) warp_sum128(wlo, whi);
+                if (__any_sync(0xffffffffu, (ilo | ihi) != 0)) warp_sum128(ilo, ihi);
             }
-            mind = warp_min64(mind);
+            mins = warp_min64(mind < mins ? mind : mins);
             if (lane == 0) {
+                acc.wlo[wid] = wlo;
+                acc.whi[wid] = whi;
                 acc.ilo[wid] = ilo;
                 acc.ihi[wid] = ihi;
-                if (mind < acc.mins[wid]) acc.mins[wid] = mind;
+                acc.mins[wid] = mins;
             }
             __syncthreads();
             // ---- every warp: close round i, plan round i + 1
