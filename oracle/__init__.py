@@ -4,7 +4,8 @@ Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this package.  It wraps ``dupin_oracle.c`` (plain
 single-threaded C, exact __int128 arithmetic) with ctypes and shares no code
 with the CUDA library.  See ``dupin_oracle.c`` for what each routine follows
-in the paper (Sec. 2 Eq. 1; Algorithms 1-4; Lemma 4.1/4.2; Thm 2.1/4.3).
+in the paper (Sec. 2 Eq. 1; Algorithms 1-4; Lemma 4.1/4.2; Thm 2.1/4.3; the
+clique metrics TDS and kCLiDS of Sec. 2.1).
 
 Pinning (tests/test_oracle.py): brute-force enumeration, exact max-flow DG,
 closed forms (cliques, stars, complete bipartite graphs), hand-derived
@@ -55,6 +56,10 @@ def lib():
         L.og_brute_force.argtypes = [P, P]
         L.og_exact_dg.restype = ctypes.c_int
         L.og_exact_dg.argtypes = [P, P, P]
+        L.og_peel_clique.restype = ctypes.c_int
+        L.og_peel_clique.argtypes = [P, i32, i32, i64, i64, u32, i64, P, P, P, P, P, P, P, i64, P]
+        L.og_brute_force_clique.restype = ctypes.c_int
+        L.og_brute_force_clique.argtypes = [P, i32, P]
         L.og_verify.restype = ctypes.c_int
         L.og_verify.argtypes = [P, i32, i64, i64, P, i64, P, P, P, P, i64, i64, u64, P, i64]
         _lib = L
@@ -122,6 +127,7 @@ class PeelResult:
     violations: int
     n_min_rule: int
     scan_volume: int
+    clique: int = 0  # q for the clique metrics (f = clique count), 0: Q32.32 weights
 
     @property
     def best_mask(self) -> np.ndarray:
@@ -129,7 +135,9 @@ class PeelResult:
 
     @property
     def best_density(self) -> float:
-        return self.best_f / self.best_size / 2**32 if self.best_size else 0.0
+        if not self.best_size:
+            return 0.0
+        return self.best_f / self.best_size / (1 if self.clique else 2**32)
 
 
 def peel_batch(g: Graph, k_mult: int = 1, eps=(1, 10), flags: int = 0, max_rounds: int = 0,
@@ -158,6 +166,46 @@ def peel_batch(g: Graph, k_mult: int = 1, eps=(1, 10), flags: int = 0, max_round
         trace_size=sz[: R + 1].copy(), trace_peeled=pe[: R + 1].copy(), trace_T=tt[: R + 1].copy(),
         trace_kind=kd[: R + 1].copy(), violations=int(out[5]), n_min_rule=int(out[6]), scan_volume=int(out[7]),
     )
+
+
+def peel_clique(g: Graph, q: int = 3, k_mult: int = 3, eps=(1, 10), flags: int = 0, max_rounds: int = 0,
+                trace_cap: Optional[int] = None) -> PeelResult:
+    """Algorithm 2 (3 / 4 by flag) for the q-clique metrics: TDS (q = 3) and
+    kCLiDS (Sec. 2.1); f and the weights are clique counts, recomputed from
+    scratch each round.  The paper's multiplier for these metrics is q."""
+    L = lib()
+    n = g.n
+    cap = trace_cap if trace_cap is not None else n + 2
+    pr = np.zeros(n, np.int32)
+    fh = np.zeros(cap, np.int64)
+    fl = np.zeros(cap, np.uint64)
+    sz = np.zeros(cap, np.int64)
+    pe = np.zeros(cap, np.int64)
+    tt = np.zeros(cap, np.int64)
+    kd = np.zeros(cap, np.int32)
+    out = np.zeros(8, np.int64)
+    rc = L.og_peel_clique(g._h, q, k_mult, eps[0], eps[1], flags, max_rounds, _p(pr), _p(fh), _p(fl), _p(sz),
+                          _p(pe), _p(tt), _p(kd), cap, _p(out))
+    if rc != 0:
+        raise OracleError(rc)
+    R = int(out[0])
+    return PeelResult(
+        peel_round=pr, n_rounds=R, best_round=int(out[1]), best_size=int(out[2]),
+        best_f=i128(out[3], np.uint64(out[4])),
+        trace_f=[i128(fh[i], fl[i]) for i in range(R + 1)],
+        trace_size=sz[: R + 1].copy(), trace_peeled=pe[: R + 1].copy(), trace_T=tt[: R + 1].copy(),
+        trace_kind=kd[: R + 1].copy(), violations=int(out[5]), n_min_rule=int(out[6]), scan_volume=int(out[7]),
+        clique=q,
+    )
+
+
+def brute_force_clique(g: Graph, q: int = 3):
+    """(best_size, cliques in the best set, mask) over all non-empty subsets (n <= 20)."""
+    out = np.zeros(3, np.int64)
+    rc = lib().og_brute_force_clique(g._h, q, _p(out))
+    if rc != 0:
+        raise OracleError(rc)
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def peel_serial(g: Graph):

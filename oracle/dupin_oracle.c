@@ -17,6 +17,9 @@
  *     w_u(S_{i-1}) <= k(1+eps) g(S_{i-1}) leaves in round i; the densest S_i
  *     is returned);
  *   - Algorithm 3 (global threshold tau_max) and Algorithm 4 (local trims);
+ *   - the same peel for the clique metrics TDS and kCLiDS (Sec. 2.1): f(S)
+ *     = number of q-cliques of G[S], w_u(S) = those through u, recomputed
+ *     from scratch every round, and their brute-force optimum;
  *   - brute-force densest subgraph (n <= 24) and exact DG densest subgraph
  *     by Goldberg's max-flow construction (cited in Sec. 2.3), the two
  *     independent pins for the approximation theorems (Thm 2.1, Thm 4.3);
@@ -390,6 +393,278 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
     free(w); free(in); free(rem); free(ulist);
     if (status == OG_OK && overflow_trace) return OG_ERR_BUFFER;
     return status;
+}
+
+/* ------------------------------------------ clique metrics (TDS, kCLiDS) */
+
+/*
+ * TDS and kCLiDS (Sec. 2.1): f(S) is the number of q-cliques of G[S] (q = 3
+ * for TDS), which Eq. 1 expresses with c = 0 and a_u = (q-cliques through
+ * u)/q.  The peeling weight w_u(S) is the number of q-cliques of G[S] that
+ * contain u -- the decrease of f when u leaves S -- so the weights of S sum
+ * to q f(S).  Weights and f are plain clique counts here: every test the
+ * peel makes compares ratios of integers, which a common scale does not
+ * change.  Algorithm 2 recomputes the weights of the remaining set every
+ * round (Sec. 4.1); so does this routine, by listing the cliques of G[S]
+ * from scratch, which is slow and plainly follows the definition.
+ */
+
+/* each vertex's neighbours in increasing order (a copy of g->nbr) */
+static int32_t *sorted_nbrs(const og_graph *g) {
+    int32_t *s = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * g->m + 1));
+    if (!s) return NULL;
+    for (int64_t u = 0; u < g->n; u++) {
+        int64_t b = g->off[u], e = g->off[u + 1];
+        for (int64_t p = b; p < e; p++) s[p] = g->nbr[p];
+        for (int64_t p = b + 1; p < e; p++) { /* insertion sort: lists are short in tests */
+            int32_t x = s[p];
+            int64_t q = p - 1;
+            while (q >= b && s[q] > x) { s[q + 1] = s[q]; q--; }
+            s[q + 1] = x;
+        }
+    }
+    return s;
+}
+
+/* is v a neighbour of u (binary search in u's sorted list) */
+static int adjacent(const og_graph *g, const int32_t *srt, int32_t u, int32_t v) {
+    int64_t lo = g->off[u], hi = g->off[u + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (srt[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < g->off[u + 1] && srt[lo] == v;
+}
+
+typedef struct {
+    const og_graph *g;
+    const int32_t *srt;
+    int q;
+    int32_t *chosen;  /* q vertices, increasing */
+    int32_t **level;  /* candidate lists per depth, each maxdeg long */
+    int64_t *w;       /* cliques through each vertex */
+    i128 count;       /* cliques listed */
+} clique_walk;
+
+/* extend the chosen vertices chosen[0..depth) by every candidate in turn;
+   cand holds the vertices after chosen[depth-1] that are adjacent to all of
+   them and in S, in increasing order */
+static void clique_extend(clique_walk *c, int depth, const int32_t *cand, int64_t nc) {
+    if (depth == c->q) {
+        c->count++;
+        for (int j = 0; j < c->q; j++) c->w[c->chosen[j]]++;
+        return;
+    }
+    int32_t *next = c->level[depth];
+    for (int64_t i = 0; i < nc; i++) {
+        int32_t v = cand[i];
+        c->chosen[depth] = v;
+        int64_t nn = 0;
+        if (depth + 1 < c->q)
+            for (int64_t j = i + 1; j < nc; j++)
+                if (adjacent(c->g, c->srt, v, cand[j])) next[nn++] = cand[j];
+        clique_extend(c, depth + 1, next, nn);
+    }
+}
+
+/* w_u(S) for every u (0 outside S) and f(S), by listing the q-cliques of G[S] */
+static i128 clique_weights(const og_graph *g, const int32_t *srt, const uint8_t *in, int q, int64_t *w,
+                           int32_t *chosen, int32_t **level) {
+    clique_walk c = {g, srt, q, chosen, level, w, 0};
+    for (int64_t u = 0; u < g->n; u++) w[u] = 0;
+    for (int64_t u = 0; u < g->n; u++) {
+        if (!in[u]) continue;
+        int64_t nc = 0;
+        for (int64_t p = g->off[u]; p < g->off[u + 1]; p++)
+            if (srt[p] > u && in[srt[p]]) level[0][nc++] = srt[p];
+        chosen[0] = (int32_t)u;
+        clique_extend(&c, 1, level[0], nc);
+    }
+    return c.count;
+}
+
+/*
+ * Algorithm 2 (and 3 / 4 by flag, as og_peel_batch) for the q-clique
+ * metrics, q >= 2 (q = 2 is DG with unscaled counts).  Same outputs as
+ * og_peel_batch; trace f is the clique count; out[5] counts rounds where
+ * the weights did not sum to q f.
+ */
+int og_peel_clique(const og_graph *g, int32_t q, int32_t k_mult, int64_t eps_num, int64_t eps_den,
+                   uint32_t flags, int64_t max_rounds, int32_t *peel_round,
+                   int64_t *tr_f_hi, uint64_t *tr_f_lo, int64_t *tr_size, int64_t *tr_peeled,
+                   int64_t *tr_T, int32_t *tr_kind, int64_t tr_cap, int64_t *out) {
+    const int64_t n = g->n;
+    if (q < 2 || q > 16 || k_mult < 1 || eps_num < 0 || eps_den < 1) return OG_ERR_ARG;
+    if (max_rounds <= 0) max_rounds = n + 1;
+    for (int i = 0; i < 8; i++) out[i] = 0;
+    if (flags & OG_FLAG_LPO) flags |= OG_FLAG_GPO;
+    if (tr_cap < 1) return OG_ERR_BUFFER;
+
+    int64_t maxdeg = 1;
+    for (int64_t u = 0; u < n; u++)
+        if (g->off[u + 1] - g->off[u] > maxdeg) maxdeg = g->off[u + 1] - g->off[u];
+    int64_t *w = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    uint8_t *in = (uint8_t *)malloc((size_t)n + 1);
+    int32_t *ulist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *chosen = (int32_t *)malloc(sizeof(int32_t) * (size_t)q);
+    int32_t **level = (int32_t **)calloc((size_t)q, sizeof(int32_t *));
+    int32_t *srt = sorted_nbrs(g);
+    int ok = w && in && ulist && chosen && level && srt;
+    for (int d = 0; ok && d < q; d++) ok = (level[d] = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxdeg)) != NULL;
+    if (!ok) {
+        if (level) for (int d = 0; d < q; d++) free(level[d]);
+        free(w); free(in); free(ulist); free(chosen); free(level); free(srt);
+        return OG_ERR_OOM;
+    }
+
+    for (int64_t u = 0; u < n; u++) { in[u] = 1; peel_round[u] = INT32_MAX; }
+    i128 f = clique_weights(g, srt, in, q, w, chosen, level);
+    int64_t size = n, viol = 0, nfallback = 0, scan = 0, R = 0;
+    int64_t best_round = 0, best_size = n;
+    i128 best_f = f;
+    tr_f_hi[0] = (int64_t)(f >> 64);
+    tr_f_lo[0] = (uint64_t)f;
+    tr_size[0] = n;
+    tr_peeled[0] = 0;
+    tr_T[0] = 0;
+    tr_kind[0] = 0;
+    int64_t gpo_le = 0, gpo_lt = -1;
+    const i128 kD = (i128)k_mult * (eps_den + eps_num);
+    int status = OG_OK, overflow_trace = 0;
+
+    /* remove ulist[0..nU) as round R+1 of the given kind, then recompute the
+       weights and f of the remaining set from scratch */
+#define CLIQUE_ROUND(TVAL, KIND)                                                       \
+    do {                                                                               \
+        R++;                                                                           \
+        for (int64_t j = 0; j < nU; j++) { in[ulist[j]] = 0; peel_round[ulist[j]] = (int32_t)R; } \
+        size -= nU;                                                                    \
+        f = clique_weights(g, srt, in, q, w, chosen, level);                           \
+        i128 s_ = 0;                                                                   \
+        for (int64_t u = 0; u < n; u++) if (in[u]) s_ += w[u];                         \
+        if (s_ != (i128)q * f) viol++;                                                 \
+        if (R < tr_cap) {                                                              \
+            tr_f_hi[R] = (int64_t)(f >> 64); tr_f_lo[R] = (uint64_t)f;                 \
+            tr_size[R] = size; tr_peeled[R] = nU; tr_T[R] = (TVAL); tr_kind[R] = (KIND); \
+        } else {                                                                       \
+            overflow_trace = 1;                                                        \
+        }                                                                              \
+        if (size > 0 && frac_gt(f, size, best_f, best_size)) {                         \
+            best_f = f; best_size = size; best_round = R;                              \
+        }                                                                              \
+    } while (0)
+
+    {
+        i128 s = 0;
+        for (int64_t u = 0; u < n; u++) s += w[u];
+        if (s != (i128)q * f) viol++;
+    }
+    while (size > 0) {
+        if (R + 1 > max_rounds) { status = OG_ERR_NO_PROGRESS; break; }
+        scan += size;
+        int64_t T = floor_div_sat(kD * f, (i128)eps_den * size);
+        if (flags & OG_FLAG_GPO) {
+            int64_t le = floor_div_sat((i128)eps_den * f, kD * size);
+            int64_t lt = below_div_sat((i128)eps_den * f, kD * size);
+            if (le > gpo_le) gpo_le = le;
+            if (lt > gpo_lt) gpo_lt = lt;
+            if (gpo_le > T) T = gpo_le;
+        }
+        int64_t nU = 0;
+        for (int64_t u = 0; u < n; u++)
+            if (in[u] && w[u] <= T) ulist[nU++] = (int32_t)u;
+        int kind = 0;
+        if (nU == 0) { /* minimum-weight rule, as for the other metrics */
+            int64_t mn = INT64_MAX;
+            for (int64_t u = 0; u < n; u++)
+                if (in[u] && w[u] < mn) mn = w[u];
+            T = mn;
+            for (int64_t u = 0; u < n; u++)
+                if (in[u] && w[u] <= T) ulist[nU++] = (int32_t)u;
+            kind = 1;
+            nfallback++;
+        }
+        if (nU == 0) { viol++; status = OG_ERR_NO_PROGRESS; break; }
+        CLIQUE_ROUND(T, kind);
+        if (flags & OG_FLAG_LPO) {
+            while (size > 0) {
+                int64_t below_g = below_div_sat(f, size);
+                int any = 0;
+                for (int64_t u = 0; u < n && !any; u++)
+                    if (in[u] && w[u] <= below_g) any = 1;
+                if (!any) break;
+                if (R + 1 > max_rounds) { status = OG_ERR_NO_PROGRESS; break; }
+                int64_t L = below_g > gpo_lt ? below_g : gpo_lt;
+                scan += size;
+                nU = 0;
+                for (int64_t u = 0; u < n; u++)
+                    if (in[u] && w[u] <= L) ulist[nU++] = (int32_t)u;
+                CLIQUE_ROUND(L, 2);
+            }
+            if (status != OG_OK) break;
+        }
+    }
+#undef CLIQUE_ROUND
+    if (status == OG_OK && f != 0) viol++;
+    out[0] = R;
+    out[1] = best_round;
+    out[2] = best_size;
+    out[3] = (int64_t)(best_f >> 64);
+    out[4] = (int64_t)(uint64_t)best_f;
+    out[5] = viol;
+    out[6] = nfallback;
+    out[7] = scan;
+    for (int d = 0; d < q; d++) free(level[d]);
+    free(w); free(in); free(ulist); free(chosen); free(level); free(srt);
+    if (status == OG_OK && overflow_trace) return OG_ERR_BUFFER;
+    return status;
+}
+
+/*
+ * max over non-empty S of (q-cliques of G[S]) / |S| by enumerating all
+ * 2^n - 1 subsets (n <= 20): the graph's cliques are listed once as vertex
+ * masks, and a subset counts those inside it.  Ties keep the first mask.
+ * out[0] = |S*|, out[1] = cliques in S*, out[2] = the mask of S*.
+ */
+int og_brute_force_clique(const og_graph *g, int32_t q, int64_t *out) {
+    const int64_t n = g->n;
+    if (n < 1 || n > 20 || q < 2 || q > 16) return OG_ERR_ARG;
+    /* list the cliques: choose q vertices in increasing order, all pairs adjacent */
+    int64_t cap = 1024, nk = 0;
+    uint32_t *km = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cap);
+    int32_t *srt = sorted_nbrs(g);
+    if (!km || !srt) { free(km); free(srt); return OG_ERR_OOM; }
+    for (uint32_t mask = 1; mask < (1u << n); mask++) {
+        if (__builtin_popcount(mask) != q) continue;
+        int clique = 1;
+        for (int64_t u = 0; u < n && clique; u++) {
+            if (!((mask >> u) & 1)) continue;
+            for (int64_t v = u + 1; v < n && clique; v++)
+                if (((mask >> v) & 1) && !adjacent(g, srt, (int32_t)u, (int32_t)v)) clique = 0;
+        }
+        if (!clique) continue;
+        if (nk == cap) {
+            cap *= 2;
+            uint32_t *t = (uint32_t *)realloc(km, sizeof(uint32_t) * (size_t)cap);
+            if (!t) { free(km); free(srt); return OG_ERR_OOM; }
+            km = t;
+        }
+        km[nk++] = mask;
+    }
+    int64_t bc = -1, bs = 1, bm = 0;
+    for (uint32_t mask = 1; mask < (1u << n); mask++) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < nk; j++) c += (km[j] & mask) == km[j];
+        int64_t s = __builtin_popcount(mask);
+        if (bc < 0 || frac_gt(c, s, bc, bs)) { bc = c; bs = s; bm = mask; }
+    }
+    out[0] = bs;
+    out[1] = bc;
+    out[2] = bm;
+    free(km);
+    free(srt);
+    return OG_OK;
 }
 
 /* --------------------------------------------------------- Algorithm 1 */
