@@ -53,6 +53,17 @@ def test_version_and_errors_without_gpu(libdupin):
     assert "NULL" in dupin.last_error()
 
 
+def test_batch_shape_arguments_without_gpu():
+    """The launch-shape entry points reject bad arguments before any device call."""
+    from paper_2504_09311_gb300 import dupin
+
+    L = dupin.lib()
+    assert L.dupin_batch_set_threads(64) == dupin.ERR_INVALID_ARG
+    assert L.dupin_batch_get_threads(None) == dupin.ERR_INVALID_ARG
+    assert L.dupin_batch_tune(None, None, -1, None, None) == dupin.ERR_INVALID_ARG
+    assert L.dupin_batch_tune(None, None, 2, None, None) == dupin.ERR_INVALID_ARG
+
+
 def test_struct_layouts_match_header():
     from paper_2504_09311_gb300 import dupin
 
