@@ -294,6 +294,28 @@ def measured_traffic(kernel: str) -> Optional[float]:
     return float(d["bytes_per_launch"])
 
 
+# Latencies measured on a GB300 (one thread, dependent chains): a global load
+# that hits L2 and a 64-bit shared-memory atomic add with its result used.
+L2_HIT_CYCLES = 311
+SMEM_ATOMIC64_CYCLES = 130
+
+
+def round_latency(tail_ms: float, tail_rounds: float, sm_mhz: float) -> Optional[dict]:
+    """The one-CTA tail's time per round against the latency every round pays
+    in sequence: the removed vertices' arcs are read from L2 and their
+    neighbours' weights updated by shared atomics whose results decide the
+    next round, so a round cannot take less than one L2 hit plus one
+    dependent shared atomic."""
+    if tail_rounds <= 0 or tail_ms <= 0 or sm_mhz <= 0:
+        return None
+    us = tail_ms * 1e3 / tail_rounds
+    floor_us = (L2_HIT_CYCLES + SMEM_ATOMIC64_CYCLES) / sm_mhz
+    return {"tail_rounds_per_peel": round(tail_rounds, 1), "us_per_round": round(us, 3),
+            "floor_us": round(floor_us, 3), "frac": round(floor_us / us, 3),
+            "floor": f"L2 hit {L2_HIT_CYCLES} + dependent 64-bit shared atomic {SMEM_ATOMIC64_CYCLES} cycles "
+                     f"at {sm_mhz:.0f} MHz"}
+
+
 def max_over_ranks(ms: float, dist) -> float:
     """The step time every rank reports is the slowest rank's (host tensors, so
     the gloo process group carries it)."""
@@ -452,6 +474,10 @@ def main():
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "phase_ms_per_peel": {names[i]: round(float(mean_phase[i]), 4) for i in range(4)},
                 "algorithmic_bytes_per_peel": {kk: int(np.mean([b[kk] for _, b in per_eps])) for kk in names}}
+    tail_rounds = float(np.mean([r[1] - r[2] for r in rec]))
+    lat = round_latency(float(mean_phase[3]), tail_rounds, clocks.summary().get("sm_mhz") or 2070.0)
+    if lat is not None:
+        roofline["round_latency"] = lat
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -75,3 +75,13 @@ def test_batched_leg_keys(monkeypatch):
     assert abs(r["graphs_per_s"] - 6 / (r["ms"] / 1e3)) < 1e-6 * r["graphs_per_s"]
     assert d.calls == {"tune": 1, "batch": 5, "single": 6}
     assert _Graph.freed == 6
+
+
+def test_round_latency_reading():
+    import bench
+
+    r = bench.round_latency(6.8, 3208.0, 2070.0)
+    assert r["us_per_round"] == round(6.8e3 / 3208, 3)
+    assert r["floor_us"] == round((bench.L2_HIT_CYCLES + bench.SMEM_ATOMIC64_CYCLES) / 2070.0, 3)
+    assert 0 < r["frac"] < 1
+    assert bench.round_latency(0.0, 10, 2070.0) is None and bench.round_latency(1.0, 0, 2070.0) is None
