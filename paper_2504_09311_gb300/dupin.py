@@ -254,6 +254,59 @@ class PeelOutput:
         return self._trace_f
 
 
+def _result_dtype() -> np.dtype:
+    """numpy view of dupin_result (same offsets and size as the ctypes Result)."""
+    fmt = {ctypes.c_void_p: "<u8", ctypes.c_int64: "<i8", ctypes.c_uint64: "<u8", ctypes.c_double: "<f8"}
+    names, formats, offsets = [], [], []
+    for name, ct in Result._fields_:
+        names.append(name)
+        offsets.append(getattr(Result, name).offset)
+        formats.append(fmt[ct] if ct in fmt else ("<f4", (ct._length_,)))
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(Result)})
+
+
+RESULT_DTYPE = _result_dtype()
+
+
+def _data_addr(x) -> int:
+    """Address of a numpy array or torch tensor, 0 for None."""
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.__array_interface__["data"][0]
+    return x.data_ptr()
+
+
+def _result_array(keep) -> np.ndarray:
+    """dupin_result[k] for per-graph (peel_round, best_mask, trace) buffers, filled column by column."""
+    RA = np.zeros(len(keep), RESULT_DTYPE)
+    RA["peel_round"] = [_data_addr(b[0]) for b in keep]
+    RA["best_mask"] = [_data_addr(b[1]) for b in keep]
+    if any(b[2] is not None for b in keep):
+        for name, q in (("trace_f_hi", 0), ("trace_f_lo", 1), ("trace_size", 2), ("trace_peeled", 3)):
+            RA[name] = [_data_addr(b[2][q]) if b[2] is not None else 0 for b in keep]
+        RA["trace_cap"] = [len(b[2][0]) if b[2] is not None else 0 for b in keep]
+    return RA
+
+
+def _outputs(RA: np.ndarray, keep) -> list:
+    """PeelOutput per graph from a filled dupin_result[k]."""
+    nr, br, bs = RA["n_rounds"].tolist(), RA["best_round"].tolist(), RA["best_size"].tolist()
+    fh, fl, dens = RA["best_f_hi"].tolist(), RA["best_f_lo"].tolist(), RA["best_density"].tolist()
+    nmr, nb, ta, ph = RA["n_min_rule"].tolist(), RA["n_bulk_rounds"].tolist(), RA["tail_arcs"].tolist(), \
+        RA["phase_ms"].tolist()
+    outs = []
+    for j, (pr, mk, trace) in enumerate(keep):
+        o = PeelOutput(nr[j], br[j], bs[j], (fh[j] << 64) + fl[j], dens[j], nmr[j], pr, mk, n_bulk_rounds=nb[j],
+                       phase_ms=ph[j], tail_arcs=ta[j])
+        if trace is not None and isinstance(trace[0], np.ndarray):
+            R = nr[j] + 1
+            o.trace_f_hi, o.trace_f_lo, o.trace_size, o.trace_peeled = (t[:R] for t in trace)
+        outs.append(o)
+    return outs
+
+
 def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> Result:
     r = Result()
     r.best_mask = _addr(best_mask)
@@ -339,23 +392,50 @@ def result_buffers(n: int, want_rounds=True, want_mask=False, want_trace=False, 
     return pr, mk, trace
 
 
+class BatchBuffers:
+    """Host result buffers for a batch, reusable across peel_batch calls: the
+    per-graph (peel_round, best_mask, trace) buffers and the result array with
+    their addresses filled in once."""
+
+    def __init__(self, keep):
+        self.keep = list(keep)
+        self.template = _result_array(self.keep)
+
+    @classmethod
+    def for_graphs(cls, graphs, want_rounds=True, want_mask=False, want_trace=False, pinned=False):
+        if not pinned or want_mask or want_trace:
+            return cls([result_buffers(g.n, want_rounds, want_mask, want_trace, pinned) for g in graphs])
+        # peel rounds only: one page-locked block sliced per graph
+        import torch
+
+        total = sum(g.n for g in graphs)
+        block = torch.empty(max(total, 1), dtype=torch.int32, pin_memory=True).numpy()
+        keep, at = [], 0
+        for g in graphs:
+            keep.append((block[at:at + g.n] if want_rounds else None, None, None))
+            at += g.n
+        bb = cls(keep)
+        bb._block = block  # keeps the page-locked memory alive
+        return bb
+
+
 def peel_batch(graphs: Sequence[Graph], params: Sequence[Params], want_rounds=True, want_trace=False, stream=None,
                want_mask=False, buffers=None):
     """dupin_peel_batch with host result buffers; returns a list of PeelOutput.
-    buffers: optional per-graph (peel_round, best_mask, trace) from result_buffers()."""
+    buffers: optional per-graph (peel_round, best_mask, trace) from result_buffers(),
+    or a BatchBuffers (reusable: addresses computed once)."""
     k = len(graphs)
-    G = (ctypes.c_void_p * k)(*[g.handle.value for g in graphs])
+    G = np.fromiter((g.handle.value for g in graphs), dtype=np.uint64, count=k)
     P = (Params * k)(*params)
-    R = (Result * k)()
-    keep = []
-    for j, g in enumerate(graphs):
-        pr, mk, trace = buffers[j] if buffers is not None else result_buffers(g.n, want_rounds, want_mask, want_trace)
-        cap = len(trace[0]) if trace is not None else 0
-        R[j] = _result_struct(pr, mk, trace, cap)
-        keep.append((pr, mk, trace))
-    check(lib().dupin_peel_batch(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p),
-                                 ctypes.cast(R, ctypes.c_void_p), k, _stream(stream)))
-    return [_output(R[j], keep[j][0], keep[j][1], keep[j][2]) for j in range(k)]
+    if isinstance(buffers, BatchBuffers):
+        keep, RA = buffers.keep, buffers.template.copy()
+    else:
+        keep = list(buffers) if buffers is not None else \
+            [result_buffers(g.n, want_rounds, want_mask, want_trace) for g in graphs]
+        RA = _result_array(keep)
+    check(lib().dupin_peel_batch(G.ctypes.data, ctypes.cast(P, ctypes.c_void_p), RA.ctypes.data, k,
+                                 _stream(stream)))
+    return _outputs(RA, keep)
 
 
 def batch_threads(threads=None) -> int:

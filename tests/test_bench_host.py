@@ -56,6 +56,7 @@ def _fake_dupin():
         return _Out(g.n)
 
     d.batch_tune, d.peel_batch, d.peel = batch_tune, peel_batch, peel
+    d.BatchBuffers = types.SimpleNamespace(for_graphs=lambda graphs, **kw: None)
     return d
 
 
