@@ -60,6 +60,8 @@ def lib():
         L.og_peel_clique.argtypes = [P, i32, i32, i64, i64, u32, i64, P, P, P, P, P, P, P, i64, P]
         L.og_brute_force_clique.restype = ctypes.c_int
         L.og_brute_force_clique.argtypes = [P, i32, P]
+        L.og_verify_clique.restype = ctypes.c_int
+        L.og_verify_clique.argtypes = [P, i32, i32, i64, i64, P, i64, P, P, P, P, i64, i64, u64, P, i64]
         L.og_verify.restype = ctypes.c_int
         L.og_verify.argtypes = [P, i32, i64, i64, P, i64, P, P, P, P, i64, i64, u64, P, i64]
         _lib = L
@@ -249,4 +251,18 @@ def verify(g: Graph, k_mult, eps, peel_round, n_rounds, trace_f_hi, trace_f_lo, 
     pe = np.ascontiguousarray(trace_peeled, np.int64)
     rc = lib().og_verify(g._h, k_mult, eps[0], eps[1], _p(pr), n_rounds, _p(fh), _p(fl), _p(sz), _p(pe),
                          best_round, nsample, seed, msg, 512)
+    return rc, msg.value.decode()
+
+
+def verify_clique(g: Graph, q, k_mult, eps, peel_round, n_rounds, trace_f_hi, trace_f_lo, trace_size,
+                  trace_peeled, best_round, nsample=4, seed=1):
+    """Check a plain clique-metric Algorithm 2 result against the definitions; returns (code, message)."""
+    msg = ctypes.create_string_buffer(512)
+    pr = np.ascontiguousarray(peel_round, np.int32)
+    fh = np.ascontiguousarray(trace_f_hi, np.int64)
+    fl = np.ascontiguousarray(trace_f_lo, np.uint64)
+    sz = np.ascontiguousarray(trace_size, np.int64)
+    pe = np.ascontiguousarray(trace_peeled, np.int64)
+    rc = lib().og_verify_clique(g._h, q, k_mult, eps[0], eps[1], _p(pr), n_rounds, _p(fh), _p(fl), _p(sz), _p(pe),
+                                best_round, nsample, seed, msg, 512)
     return rc, msg.value.decode()

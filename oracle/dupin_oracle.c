@@ -1095,3 +1095,102 @@ done:
     return rc;
 #undef FAIL
 }
+
+/*
+ * Check a plain Algorithm 2 result for the q-clique metrics (no GPO/LPO)
+ * against the definitions, for graphs too large to replay:
+ *   (1) every vertex has a round in [1, R], every round is non-empty, and
+ *       |S_i|, |U_i| from peel_round equal the trace;
+ *   (2) at 'nsample' sampled rounds plus the first and the last two, the
+ *       q-cliques of G[S_{i-1}] are listed afresh: f(S_{i-1}) equals the
+ *       trace, every vertex peeled in round i had w_u(S_{i-1}) <= T_i and
+ *       every survivor more (T_i from the trace by the k(1+eps)g rule, or
+ *       the minimum live weight when the rule selects nobody);
+ *   (3) the reported best round is the earliest argmax of f_i/|S_i| over
+ *       the trace.
+ * Returns 0 when every check holds, else a positive code; msg explains.
+ */
+int og_verify_clique(const og_graph *g, int32_t q, int32_t k_mult, int64_t eps_num, int64_t eps_den,
+                     const int32_t *peel_round, int64_t R, const int64_t *tr_f_hi, const uint64_t *tr_f_lo,
+                     const int64_t *tr_size, const int64_t *tr_peeled, int64_t best_round, int64_t nsample,
+                     uint64_t seed, char *msg, int64_t msg_cap) {
+    const int64_t n = g->n;
+#define FAILC(code, ...) do { if (msg && msg_cap > 0) snprintf(msg, (size_t)msg_cap, __VA_ARGS__); rc = (code); goto done; } while (0)
+    int rc = 0;
+    if (q < 2 || q > 16 || R < 0) return 100;
+    int64_t maxdeg = 1;
+    for (int64_t u = 0; u < n; u++)
+        if (g->off[u + 1] - g->off[u] > maxdeg) maxdeg = g->off[u + 1] - g->off[u];
+    int64_t *cnt = (int64_t *)calloc((size_t)R + 2, sizeof(int64_t));
+    int64_t *w = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    uint8_t *in = (uint8_t *)malloc((size_t)n + 1);
+    int32_t *chosen = (int32_t *)malloc(sizeof(int32_t) * (size_t)q);
+    int32_t **level = (int32_t **)calloc((size_t)q, sizeof(int32_t *));
+    int32_t *srt = sorted_nbrs(g);
+    const i128 kD = (i128)k_mult * (eps_den + eps_num);
+    if (!cnt || !w || !in || !chosen || !level || !srt) FAILC(101, "out of memory");
+    for (int d = 0; d < q; d++)
+        if (!(level[d] = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxdeg))) FAILC(101, "out of memory");
+    /* (1) */
+    for (int64_t u = 0; u < n; u++) {
+        int32_t r = peel_round[u];
+        if (r < 1 || r > R) FAILC(1, "vertex %lld has round %d outside [1,%lld]", (long long)u, r, (long long)R);
+        cnt[r]++;
+    }
+    {
+        int64_t sz = n;
+        if (tr_size[0] != n) FAILC(4, "trace entry 0 size mismatch");
+        for (int64_t i = 1; i <= R; i++) {
+            if (cnt[i] == 0) FAILC(2, "round %lld is empty", (long long)i);
+            sz -= cnt[i];
+            if (tr_size[i] != sz) FAILC(4, "size trace mismatch at round %lld", (long long)i);
+            if (tr_peeled[i] != cnt[i]) FAILC(5, "peeled-count mismatch at round %lld", (long long)i);
+        }
+    }
+    /* (2) */
+    {
+        uint64_t st = seed;
+        for (int64_t s = 0; s < nsample + 3 && R > 0; s++) {
+            int64_t i;
+            if (s == 0) i = 1;
+            else if (s == 1) i = R;
+            else if (s == 2) i = R > 1 ? R - 1 : 1;
+            else i = 1 + (int64_t)(v_mix(&st) % (uint64_t)R);
+            for (int64_t u = 0; u < n; u++) in[u] = peel_round[u] >= i;
+            const i128 f = clique_weights(g, srt, in, q, w, chosen, level);
+            const i128 ft = ((i128)tr_f_hi[i - 1] << 64) | (i128)tr_f_lo[i - 1];
+            if (f != ft) FAILC(3, "f trace mismatch at round %lld", (long long)(i - 1));
+            int64_t T = floor_div_sat(kD * f, (i128)eps_den * tr_size[i - 1]);
+            int64_t mn = INT64_MAX;
+            int any_le = 0;
+            for (int64_t u = 0; u < n; u++) {
+                if (!in[u]) continue;
+                if (w[u] < mn) mn = w[u];
+                if (w[u] <= T) any_le = 1;
+            }
+            if (!any_le) T = mn; /* the minimum rule */
+            for (int64_t u = 0; u < n; u++) {
+                if (!in[u]) continue;
+                if (peel_round[u] == i && w[u] > T)
+                    FAILC(6, "round %lld: vertex %lld peeled above the threshold", (long long)i, (long long)u);
+                if (peel_round[u] > i && w[u] <= T)
+                    FAILC(7, "round %lld: survivor %lld at or below the threshold", (long long)i, (long long)u);
+            }
+        }
+    }
+    /* (3) */
+    {
+        int64_t b = 0;
+        for (int64_t i = 1; i < R; i++) {
+            const i128 fi = ((i128)tr_f_hi[i] << 64) | (i128)tr_f_lo[i];
+            const i128 fb = ((i128)tr_f_hi[b] << 64) | (i128)tr_f_lo[b];
+            if (frac_gt(fi, tr_size[i], fb, tr_size[b])) b = i;
+        }
+        if (b != best_round) FAILC(11, "best round %lld, expected %lld", (long long)best_round, (long long)b);
+    }
+done:
+    if (level) for (int d = 0; d < q; d++) free(level[d]);
+    free(cnt); free(w); free(in); free(chosen); free(level); free(srt);
+    return rc;
+#undef FAILC
+}

@@ -14,6 +14,8 @@ oracle independently of itself:
     minimum rule keeps it for smaller k because min w <= q g);
   * Lemma 4.1's shrink |S_i| < |S_{i-1}| / (1 + eps) for k = q and eps > 0,
     and Lemma 4.2 (no empty round).
+The verifier for large results (og_verify_clique) accepts the oracle's runs
+and rejects planted mistakes.
 """
 import itertools
 import json
@@ -196,3 +198,31 @@ def test_clique_errors():
         oracle.peel_clique(g, 3, 0, (1, 10))
     with pytest.raises(oracle.OracleError):
         oracle.brute_force_clique(graph(21, []), 3)
+
+
+def _vc(g, q, k, eps, r, pr=None, fh=None, best=None, nsample=64):
+    fh_arr = np.array([x >> 64 for x in r.trace_f], np.int64) if fh is None else fh
+    fl_arr = np.array([x & ((1 << 64) - 1) for x in r.trace_f], np.uint64)
+    return oracle.verify_clique(g, q, k, eps, r.peel_round if pr is None else pr, r.n_rounds, fh_arr, fl_arr,
+                                r.trace_size, r.trace_peeled, r.best_round if best is None else best, nsample=nsample)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("q,k,eps", [(3, 3, (1, 10)), (3, 1, (0, 1)), (4, 4, (1, 5))])
+def test_clique_verifier_accepts_and_rejects(seed, q, k, eps):
+    n = 30
+    g = graph(n, random_edges(n, 0.35, 50 + seed))
+    r = oracle.peel_clique(g, q, k, eps)
+    assert _vc(g, q, k, eps, r) == (0, "")
+    if r.n_rounds >= 2:
+        # a vertex moved to the next round
+        pr = r.peel_round.copy()
+        u = int(np.flatnonzero(pr == 1)[0])
+        pr[u] = 2
+        assert _vc(g, q, k, eps, r, pr=pr)[0] != 0
+        # a wrong best round
+        assert _vc(g, q, k, eps, r, best=(r.best_round + 1) % r.n_rounds)[0] != 0
+    # a wrong f in the trace (high word)
+    fh = np.array([x >> 64 for x in r.trace_f], np.int64)
+    fh[0] += 1
+    assert _vc(g, q, k, eps, r, fh=fh)[0] != 0
