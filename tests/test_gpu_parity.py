@@ -66,7 +66,8 @@ def test_golden_examples(dupin, path, tail_cap):
                          np.array([x * Q for x in G["a"]], np.int64))
     dg = dupin.Graph.from_synth(g)
     for case in G["cases"]:
-        out = dupin.peel(dg, G["metric"], case["k"], tuple(case["eps"]), tail_cap=tail_cap)
+        flags = {"": 0, "gpo": dupin.GPO, "lpo": dupin.LPO}[case.get("flags", "")]
+        out = dupin.peel(dg, G["metric"], case["k"], tuple(case["eps"]), flags=flags, tail_cap=tail_cap)
         assert list(out.peel_round) == case["peel_round"]
         assert out.trace_f == [x * Q for x in case["trace_f"]]
         assert list(out.trace_size) == case["trace_size"]

@@ -53,6 +53,11 @@ def density(f, s):
 # ---------------------------------------------------------------- goldens
 
 
+def case_flags(case) -> int:
+    """A golden case's variant: "" Algorithm 2, "gpo" Algorithm 3, "lpo" Algorithm 4."""
+    return {"": 0, "gpo": oracle.FLAG_GPO, "lpo": oracle.FLAG_LPO}[case.get("flags", "")]
+
+
 def golden_files():
     return sorted(glob.glob(os.path.join(GOLDEN, "peel_*.json")))
 
@@ -62,7 +67,7 @@ def test_golden_batch_peel(path):
     G = json.load(open(path))
     g = graph_from_lists(G["n"], G["edges"], G["a"], G["metric"])
     for case in G["cases"]:
-        r = oracle.peel_batch(g, case["k"], tuple(case["eps"]), flags=oracle.FLAG_RECOMPUTE_F)
+        r = oracle.peel_batch(g, case["k"], tuple(case["eps"]), flags=case_flags(case) | oracle.FLAG_RECOMPUTE_F)
         assert r.violations == 0
         assert list(r.peel_round) == case["peel_round"], case
         assert r.trace_f == [x * Q for x in case["trace_f"]]
@@ -72,6 +77,9 @@ def test_golden_batch_peel(path):
         assert r.best_size == case["best_size"]
         assert r.best_f == case["best_f"] * Q
         assert r.n_min_rule == case["n_min_rule"]
+        if "trace_T" in case:  # the integer threshold and the kind of every round
+            assert [int(x) for x in r.trace_T] == case["trace_T"], case
+            assert list(r.trace_kind) == case["trace_kind"], case
     if "serial" in G:
         order, step, size, f = oracle.peel_serial(g)
         assert list(order) == G["serial"]["order"]
