@@ -215,10 +215,17 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
     uint8_t *in = (uint8_t *)malloc((size_t)n + 1);     /* u in current S */
     uint8_t *rem = (uint8_t *)calloc((size_t)n + 1, 1); /* u in removal set U */
     int32_t *ulist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
-    if (!w || !in || !rem || !ulist) { free(w); free(in); free(rem); free(ulist); return OG_ERR_OOM; }
+    /* the members of the current S as a list: every loop "for u in S_{i-1}"
+       of Algorithms 2-4 walks it; it is filtered after each removal */
+    int32_t *slist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    if (!w || !in || !rem || !ulist || !slist) {
+        free(w); free(in); free(rem); free(ulist); free(slist);
+        return OG_ERR_OOM;
+    }
 
     /* S_0 = V; initial peeling weights and f(S_0) */
-    for (int64_t u = 0; u < n; u++) { in[u] = 1; peel_round[u] = INT32_MAX; }
+    for (int64_t u = 0; u < n; u++) { in[u] = 1; peel_round[u] = INT32_MAX; slist[u] = (int32_t)u; }
+    int64_t ns = n; /* |S| as the list's length */
     for (int64_t u = 0; u < n; u++) w[u] = w_of(g, in, u);
     i128 f = f_of_set(g, in);
     int64_t size = n;
@@ -234,7 +241,7 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
     int64_t R = 0;
     int64_t best_round = 0, best_size = n;
     i128 best_f = f;
-    if (tr_cap < 1) { free(w); free(in); free(rem); free(ulist); return OG_ERR_BUFFER; }
+    if (tr_cap < 1) { free(w); free(in); free(rem); free(ulist); free(slist); return OG_ERR_BUFFER; }
     tr_f_hi[0] = (int64_t)(f >> 64);
     tr_f_lo[0] = (uint64_t)f;
     tr_size[0] = n;
@@ -263,17 +270,17 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
             if (gpo_le > T) T = gpo_le;
         }
         int64_t nU = 0;
-        for (int64_t u = 0; u < n; u++)
-            if (in[u] && w[u] <= T) ulist[nU++] = (int32_t)u;
+        for (int64_t j = 0; j < ns; j++)
+            if (w[slist[j]] <= T) ulist[nU++] = slist[j];
         int kind = 0;
         if (nU == 0) {
             /* minimum-weight rule when the threshold selects nobody */
             int64_t mn = INT64_MAX;
-            for (int64_t u = 0; u < n; u++)
-                if (in[u] && w[u] < mn) mn = w[u];
+            for (int64_t j = 0; j < ns; j++)
+                if (w[slist[j]] < mn) mn = w[slist[j]];
             T = mn;
-            for (int64_t u = 0; u < n; u++)
-                if (in[u] && w[u] <= T) ulist[nU++] = (int32_t)u;
+            for (int64_t j = 0; j < ns; j++)
+                if (w[slist[j]] <= T) ulist[nU++] = slist[j];
             kind = 1;
             nfallback++;
         }
@@ -298,8 +305,15 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
             }
         }
         for (int64_t j = 0; j < nU; j++) { in[ulist[j]] = 0; rem[ulist[j]] = 0; }
+        {
+            int64_t k2 = 0;
+            for (int64_t j = 0; j < ns; j++)
+                if (in[slist[j]]) slist[k2++] = slist[j];
+            ns = k2;
+        }
         f -= df;
         size -= nU;
+        if (ns != size) viol++;
         if (flags & OG_FLAG_RECOMPUTE_F) {
             i128 f2 = f_of_set(g, in);
             if (f2 != f) viol++;
@@ -330,16 +344,16 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
             while (size > 0) {
                 int64_t below_g = below_div_sat(f, size); /* w < g  <=>  w <= this */
                 int any = 0;
-                for (int64_t u = 0; u < n && !any; u++)
-                    if (in[u] && w[u] <= below_g) any = 1;
+                for (int64_t j = 0; j < ns && !any; j++)
+                    if (w[slist[j]] <= below_g) any = 1;
                 if (!any) break;
                 if (R + 1 > max_rounds) { status = OG_ERR_NO_PROGRESS; break; }
                 int64_t L = below_g;
                 if (gpo_lt > L) L = gpo_lt; /* tau_2 = max(tau_max, g) */
                 scan += size;
                 nU = 0;
-                for (int64_t u = 0; u < n; u++)
-                    if (in[u] && w[u] <= L) ulist[nU++] = (int32_t)u;
+                for (int64_t j = 0; j < ns; j++)
+                    if (w[slist[j]] <= L) ulist[nU++] = slist[j];
                 R++;
                 for (int64_t j = 0; j < nU; j++) { rem[ulist[j]] = 1; peel_round[ulist[j]] = (int32_t)R; }
                 df = 0;
@@ -358,8 +372,15 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
                     }
                 }
                 for (int64_t j = 0; j < nU; j++) { in[ulist[j]] = 0; rem[ulist[j]] = 0; }
+                {
+                    int64_t k2 = 0;
+                    for (int64_t j = 0; j < ns; j++)
+                        if (in[slist[j]]) slist[k2++] = slist[j];
+                    ns = k2;
+                }
                 f -= df;
                 size -= nU;
+                if (ns != size) viol++;
                 if (flags & OG_FLAG_RECOMPUTE_F) {
                     if (f_of_set(g, in) != f) viol++;
                 }
@@ -390,7 +411,7 @@ int og_peel_batch(const og_graph *g, int32_t k_mult, int64_t eps_num, int64_t ep
     out[5] = viol;
     out[6] = nfallback;
     out[7] = scan;
-    free(w); free(in); free(rem); free(ulist);
+    free(w); free(in); free(rem); free(ulist); free(slist);
     if (status == OG_OK && overflow_trace) return OG_ERR_BUFFER;
     return status;
 }
