@@ -1,23 +1,28 @@
 #!/usr/bin/env python
 """Benchmark: Dupin batch peeling (Algorithm 2) on one GB300, and replicas on N.
 
-Default workload (the single-GPU configuration the headline metric is quoted
-on): a Fraudar-weighted bipartite transaction graph, 2M users x 1M items,
-40M Zipf(1.8) background edges plus 5 camouflaged 500x500 blocks (p=0.3,
-150 camouflage draws per block user), peeled with the FD metric at
-eps in {0, 1/20, 1/5}, k_mult = 1.  One step = the three peels of the whole
-hot path (initial weights, grid-wide rounds, tail sub-graph, one-CTA rounds).
+Default workload (the largest single-GPU configuration): an undirected R-MAT
+graph of scale 24 (16,777,216 vertices, 16 * 2^24 draws with a = 0.57,
+b = c = 0.19, self-loops dropped and pairs merged: 260,377,346 edges) with
+Fraudar weights c = 1/ln(d_obj + 5) in Q32.32, peeled with the DG and the FD
+metric at the threshold (1 + eps) g(S) (k_mult = 1, eps = 1/10).  One step =
+the two peels of the whole hot path (initial weights, grid-wide rounds, tail
+sub-graph, tail rounds on one CTA or a thread-block cluster) in one batched
+call.  Beside it (not the headline): the same graph at k_mult = 2 and the DW
+metric (c uniform in 1..100, a uniform in 0..10) at k_mult = 1.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 
-value     edges peeled per second over all ranks (3 * m per step per rank),
+value     edges peeled per second over all ranks (2 * m per step per rank),
           graph resident in HBM, results left in device memory;
 e2e       the same metric through the C ABI with host buffers: each step
-          loads the graph from pinned host memory, peels three times and
-          copies every result (peel rounds, best mask, trace) back;
-roofline  the dominant phase's algorithmic bytes per launch / its CUDA-event
+          loads the graph from pinned host memory, validates it, peels it
+          with both metrics and copies every result (peel rounds, best mask,
+          trace) back;
+roofline  the dominant kernel's algorithmic bytes per launch / its CUDA-event
           time, against the measured HBM copy bandwidth;
-cpu_baseline  the single-threaded C oracle on one of the three peels.
+cpu_baseline  the single-threaded C oracle on one of the step's peels of the
+          full graph.
 Multi-GPU: replicas only (every rank peels its own copy; no collective on
 the data path), so scaling is weak.
 """
@@ -38,18 +43,20 @@ from typing import Optional
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# name -> the graph, the peels of one step (metric, eps) and k_mult
 WORKLOADS = {
-    "fd_2Mx1M_40M": dict(metric="fd", eps=[(0, 1), (1, 20), (1, 5)], k=1),
-    "rmat24_dw": dict(metric="dw", eps=[(1, 10)], k=1),
-    "rmat24_dg": dict(metric="dg", eps=[(1, 10)], k=1),
-    "rmat24_fd": dict(metric="fd", eps=[(1, 10)], k=1),
-    # R-MAT scale 22 (4.2M vertices, ~65M edges): the profiling case of the R-MAT runs
-    "rmat22_dg": dict(metric="dg", eps=[(1, 10)], k=1),
-    "rmat22_fd": dict(metric="fd", eps=[(1, 10)], k=1),
-    "dg_block_10kx5k": dict(metric="dg", eps=[(1, 10)], k=1),
-    # the FD generator at a quarter of the size: the profiling case (arcs still exceed L2)
-    "fd_500kx250k_8M": dict(metric="fd", eps=[(0, 1), (1, 20), (1, 5)], k=1),
+    "rmat24": dict(graph="rmat24_fd", peels=[("dg", (1, 10)), ("fd", (1, 10))], k=1),
+    "rmat24_dw": dict(graph="rmat24_dw", peels=[("dw", (1, 10))], k=1),
+    # R-MAT scale 22 (4.2M vertices, 64M edges): the profiling case of the R-MAT runs
+    "rmat22": dict(graph="rmat22_fd", peels=[("dg", (1, 10)), ("fd", (1, 10))], k=1),
+    "fd_2Mx1M_40M": dict(graph="fd_2Mx1M_40M", peels=[("fd", (0, 1)), ("fd", (1, 20)), ("fd", (1, 5))], k=1),
+    "dg_block_10kx5k": dict(graph="dg_block_10kx5k", peels=[("dg", (1, 10))], k=1),
+    # the FD generator at a quarter of the size: a profiling case (arcs still exceed L2)
+    "fd_500kx250k_8M": dict(graph="fd_500kx250k_8M", peels=[("fd", (0, 1)), ("fd", (1, 20)), ("fd", (1, 5))], k=1),
 }
+# the reference arm's per-step sample of each workload (the oracle on the full
+# R-MAT-24 graph takes tens of seconds per peel): the same generator at scale 22
+REFERENCE_SAMPLE = {"rmat24": "rmat22_fd", "rmat24_dw": "rmat22_dw"}
 
 
 def make_graph(name: str):
@@ -65,6 +72,15 @@ def make_graph(name: str):
     if name == "fd_500kx250k_8M":
         return synth.fd_camouflage(seed=1, nU=500_000, nI=250_000, m_bg=8_000_000)
     raise ValueError(name)
+
+
+def dw_copy(g):
+    """The same topology with DW weights (c uniform in 1..100, a in 0..10)."""
+    from paper_2504_09311_gb300 import synth
+
+    h = synth.SynthGraph(g.n_left, g.n_right, g.eu, g.ev)
+    synth.with_weights(h, "dw", 1, a_range=(0, 10), c_range=(1, 100))
+    return h
 
 
 def measured_peaks():
@@ -193,6 +209,18 @@ def bench_batched(dupin, stream, args):
     tl = time.perf_counter() - t0
     same = all(np.array_equal(a.peel_round, b.peel_round) and a.best_round == b.best_round and a.best_f == b.best_f
                for a, b in zip(outs, singles))
+    # a seeded sample of the windows against the CPU oracle
+    import oracle
+
+    sample = list(range(0, len(gs), max(1, len(gs) // 64)))[:64]
+    bad = 0
+    for j in sample:
+        og = oracle.Graph.from_synth(gs[j], "fd")
+        r = oracle.peel_batch(og, 1, (1, 10))
+        og.close()
+        o = outs[j]
+        bad += 0 if (np.array_equal(o.peel_round, r.peel_round) and o.best_round == r.best_round and
+                     o.best_f == r.best_f and o.n_rounds == r.n_rounds) else 1
     edges = int(sum(g.m for g in gs))
     for dg in dgs:
         dg.free()
@@ -200,16 +228,19 @@ def bench_batched(dupin, stream, args):
                         "eps=1/10, k=1", "graphs_per_s": args.windows / tb, "edges_per_s": edges / tb,
             "ms": tb * 1e3, "ms_best": min(times) * 1e3, "calls": reps,
             "one_launch_per_graph_graphs_per_s": args.windows / tl, "speedup": tl / tb,
-            "identical_to_single": bool(same), "generation_s": round(tgen, 1),
+            "identical_to_single": bool(same), "oracle_checked": len(sample), "oracle_mismatches": bad,
+            "oracle_sample": "every (count/64)-th window, peel rounds, rounds, best round and best f",
+            "generation_s": round(tgen, 1),
             "cta_threads": cta_threads, "one_cta_max_vertices": dupin.BATCH_CTA_MAX_N,
             "result_buffers": "peel rounds copied every call into page-locked host buffers allocated once"}
 
 
 def bench_serving(dupin, args, requests=2000, rate=2000.0):
     """Poisson stream (mean 2,000 req/s) of FD peels over resident graphs: the window mix plus
-    1% of requests on a few R-MAT scale-21 graphs (edge factor 10); p50/p99 from the server."""
-    import threading
-
+    1% of requests on a few R-MAT scale-21 graphs (edge factor 10); p50/p99 from the server.
+    Then the same requests submitted all at once (saturation graphs/s), and every distinct
+    graph's result against the CPU oracle."""
+    import oracle
     from paper_2504_09311_gb300 import synth
 
     pool = synth.transaction_windows(256, seed=7)
@@ -219,36 +250,50 @@ def bench_serving(dupin, args, requests=2000, rate=2000.0):
     p = dupin.make_params("fd", 1, (1, 10))
     arrivals = synth.poisson_arrivals(requests, rate, seed=3)
     pick = synth.uniform_ints(requests, 1_000_000, seed=4)
-    srv = dupin.Server(memory_budget=16 << 30, max_slots=8)
-    tickets = []
-    t0 = time.perf_counter()
-    for j in range(requests):
-        dt = arrivals[j] - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        if pick[j] % 100 == 0:
-            g = gbig[int(pick[j] // 100) % len(gbig)]
-        else:
-            g = gpool[int(pick[j]) % len(gpool)]
-        tickets.append((g, srv.submit(g, p, want_rounds=True)))
-    outs = [(g, srv.wait(t)) for g, t in tickets]
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    # every result equals the graph's own peel alone
-    ref = {}
-    mismatch = 0
-    for g, o in outs:
-        key = id(g)
-        if key not in ref:
-            ref[key] = dupin.peel(g, "fd", 1, (1, 10), want_mask=False, want_trace=False)
-        r = ref[key]
+    which = [("big", int(pick[j] // 100) % len(gbig)) if pick[j] % 100 == 0 else ("pool", int(pick[j]) % len(gpool))
+             for j in range(requests)]
+    graph_of = lambda w: gbig[w[1]] if w[0] == "big" else gpool[w[1]]
+
+    def run(paced: bool):
+        srv = dupin.Server(memory_budget=16 << 30, max_slots=8)
+        tickets = []
+        t0 = time.perf_counter()
+        for j in range(requests):
+            if paced:
+                dt = arrivals[j] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append((which[j], srv.submit(graph_of(which[j]), p, want_rounds=True)))
+        outs = [(w, srv.wait(t)) for w, t in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return outs, wall, st
+
+    outs, wall, st = run(True)
+    outs_sat, wall_sat, st_sat = run(False)
+    # every result equals the graph's own peel alone, and each distinct graph's equals the oracle's
+    ref, orc = {}, {}
+    mismatch = omis = 0
+    for w, o in outs + outs_sat:
+        if w not in ref:
+            ref[w] = dupin.peel(graph_of(w), "fd", 1, (1, 10), want_mask=False, want_trace=False)
+            sg = big[w[1]] if w[0] == "big" else pool[w[1]]
+            og = oracle.Graph.from_synth(sg, "fd")
+            orc[w] = oracle.peel_batch(og, 1, (1, 10))
+            og.close()
+        r, q = ref[w], orc[w]
         mismatch += 0 if (np.array_equal(o.peel_round, r.peel_round) and o.best_f == r.best_f) else 1
+        omis += 0 if (np.array_equal(o.peel_round, q.peel_round) and o.best_f == q.best_f and
+                      o.best_round == q.best_round) else 1
     for g in gpool + gbig:
         g.free()
     return {"workload": f"{requests} requests, Poisson {rate:.0f}/s, 256 windows + 1% on 2 R-MAT-21 (ef 10) graphs",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "graphs_per_s": requests / wall,
-            "completed": st["completed"], "mismatches_vs_alone": mismatch}
+            "completed": st["completed"], "mismatches_vs_alone": mismatch, "oracle_mismatches": omis,
+            "oracle_graphs_checked": len(orc),
+            "saturation": {"graphs_per_s": requests / wall_sat, "p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"],
+                           "how": "the same requests submitted at once"}}
 
 
 def cpu_baseline(g, metric, eps, k):
@@ -261,8 +306,8 @@ def cpu_baseline(g, metric, eps, k):
     t2 = time.perf_counter()
     og.close()
     return {"value": g.m / (t2 - t1), "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"one of the step's peels (eps={eps[0]}/{eps[1]}, k={k}) of the full graph, single-threaded C "
-                      f"oracle; {t2 - t1:.2f} s peel + {t1 - t0:.2f} s adjacency build (not counted)",
+            "sample": f"one of the step's peels ({metric.upper()}, eps={eps[0]}/{eps[1]}, k={k}) of the full graph, "
+                      f"single-threaded C oracle; {t2 - t1:.2f} s peel + {t1 - t0:.2f} s adjacency build (not counted)",
             "seconds": t2 - t1}
 
 
@@ -350,29 +395,85 @@ def cpu_parallel_baseline(g, metric, eps, k):
 
 
 def run_reference(args, wl, rank, world):
+    """The oracle as it stands, single-threaded, on this arm's workload: each
+    step peels the step's (metric, eps) list once.  For the R-MAT-24 workloads
+    a step peels the scale-22 graph of the same generator (a quarter of the
+    vertices and edges), so that 20 + 5 steps end within minutes."""
     if rank != 0:
         return
     import oracle
 
-    g = make_graph(args.workload)
-    og = oracle.Graph.from_synth(g, wl["metric"])
-    eps = wl["eps"][1] if len(wl["eps"]) > 1 else wl["eps"][0]
+    sample_graph = REFERENCE_SAMPLE.get(args.workload, wl["graph"])
+    g = make_graph(sample_graph)
+    ogs = {}
+    for metric, _ in wl["peels"]:
+        if metric not in ogs:
+            ogs[metric] = oracle.Graph.from_synth(g, metric)
+
+    def step():
+        for metric, eps in wl["peels"]:
+            oracle.peel_batch(ogs[metric], wl["k"], eps)
+
     for _ in range(args.warmup):
-        oracle.peel_batch(og, wl["k"], eps)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.peel_batch(og, wl["k"], eps)
+        step()
     dt = (time.perf_counter() - t0) / args.steps
-    value = g.m / dt
+    value = g.m * len(wl["peels"]) / dt
+    peels = ", ".join(f"{m.upper()} eps={e[0]}/{e[1]}" for m, e in wl["peels"])
+    sample = (f"each step peels the {sample_graph} graph ({g.n} vertices, {g.m} edges) once per ({peels}), "
+              f"k={wl['k']}" + ("; the same R-MAT generator at scale 22 stands in for scale 24" if
+                                sample_graph != wl["graph"] else ""))
     line = {"impl": "reference", "metric": "edges peeled/s", "value": value, "unit": "edges/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": args.workload, "k_mult": wl["k"], "eps": f"{eps[0]}/{eps[1]}",
-                       "n": g.n, "m": g.m, "sample": "one peel per step"},
-            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one peel (eps={eps[0]}/{eps[1]}) of the full graph per step"},
+            "config": {"workload": args.workload, "k_mult": wl["k"],
+                       "peels": [f"{m}:{e[0]}/{e[1]}" for m, e in wl["peels"]], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    for og in ogs.values():
+        og.close()
     print(json.dumps(line), flush=True)
+
+
+def kernel_of(phase: str, tail_ctas: int) -> str:
+    return {"init": "k_init_vertex+k_init_arcs+k_init_reduce", "bulk": "k_peel_bulk",
+            "build": "k_tail_prep+k_tail_scan+k_tail_arcs",
+            "tail": "k_peel_cluster" if tail_ctas > 1 else "k_peel_tail"}[phase]
+
+
+def side_runs(dupin, g, dg, stream, wl, reps=3):
+    """Beside the headline: the same graph at k_mult = 2, and the DW metric at
+    k_mult = 1 on the same topology (its own weights): per-peel device time."""
+    import torch
+
+    out = {}
+
+    def time_peel(graph, metric, k, eps):
+        dupin.peel(graph, metric, k, eps, want_rounds=False, want_mask=False, want_trace=False, stream=stream)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = dupin.peel(graph, metric, k, eps, flags=dupin.TIMING, want_rounds=False, want_mask=False,
+                           want_trace=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = float(np.median(ms))
+        return {"ms_per_peel": round(t, 3), "edges_per_s": g.m / (t / 1e3), "rounds": int(o.n_rounds),
+                "bulk_rounds": int(o.n_bulk_rounds), "tail_ctas": int(o.tail_ctas),
+                "phase_ms": [round(float(x), 3) for x in o.phase_ms]}
+
+    for metric, eps in wl["peels"]:
+        out[f"{metric}_k2"] = time_peel(dg, metric, 2, eps)
+    gw = dw_copy(g)
+    dw = dupin.Graph.from_synth(gw, stream=stream)
+    out["dw_k1"] = time_peel(dw, "dw", 1, (1, 10))
+    out["dw_k1"]["weights"] = "c uniform 1..100, a uniform 0..10 (Q32.32), same topology"
+    dw.free()
+    return out
 
 
 def main():
@@ -381,12 +482,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dupin", choices=["dupin", "reference"])
-    ap.add_argument("--workload", default="fd_2Mx1M_40M", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="rmat24", choices=list(WORKLOADS))
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-side", action="store_true")
     ap.add_argument("--windows", type=int, default=4096)
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
@@ -416,22 +518,24 @@ def main():
     torch.cuda.set_device(local)
     dupin.lib()  # the CUDA library must be present: no fallback
     stream = torch.cuda.current_stream()
-    g = make_graph(args.workload)
-    metric, epss, k = wl["metric"], wl["eps"], wl["k"]
+    t0 = time.perf_counter()
+    g = make_graph(wl["graph"])
+    gen_s = time.perf_counter() - t0
+    peels, k = wl["peels"], wl["k"]
     dg = dupin.Graph.from_synth(g)
-    pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
-    mk = torch.empty(g.n, dtype=torch.uint8, device="cuda")
-    params = [dupin.make_params(metric, k, e, flags=dupin.TIMING) for e in epss]
+    params = [dupin.make_params(metric, k, e, flags=dupin.TIMING) for metric, e in peels]
     # one output pair per peel: the step's peels run together (grid-wide
-    # stages in turn, one-CTA tails side by side) through dupin_peel_batch
-    prs = [pr] + [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in epss[1:]]
-    mks = [mk] + [torch.empty(g.n, dtype=torch.uint8, device="cuda") for _ in epss[1:]]
+    # stages in turn, tails side by side) through dupin_peel_batch
+    prs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in peels]
+    mks = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for _ in peels]
+    # a peel whose (graph, metric) came earlier in the step copies that peel's initial weights
+    follower = [any(peels[q][0] == peels[j][0] for q in range(j)) for j in range(len(peels))]
 
     def step(record=None):
         R = dupin.peel_batch_device([dg] * len(params), params, prs, mks, stream=stream)
         if record is not None:
             for j in range(len(params)):
-                record.append((j, R[j].n_rounds, R[j].n_bulk_rounds, list(R[j].phase_ms)))
+                record.append((j, R[j].n_rounds, R[j].n_bulk_rounds, list(R[j].phase_ms), R[j].tail_ctas))
 
     for _ in range(args.warmup):
         step()
@@ -454,33 +558,58 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
     edges_per_step = g.m * len(params)
     value = world * edges_per_step / (ms / 1e3)
+    sm_mhz = clocks.summary().get("sm_mhz") or 2070.0
 
-    # phase breakdown and roofline of the dominant phase (per launch = one peel)
-    phases = np.array([r[3] for r in rec], np.float64)  # (steps*len(params), 4)
-    mean_phase = phases.mean(axis=0)
+    # per peel: phase times (mean over the timed steps) and algorithmic bytes
+    # from the peel's own output
     names = ["init", "bulk", "build", "tail"]
-    dom = int(np.argmax(mean_phase))
-    # algorithmic bytes per launch from one peel's own output
-    per_eps = []
-    for j, e in enumerate(epss):
+    per_peel = []
+    for j, (metric, e) in enumerate(peels):
+        ph = np.mean(np.array([r[3] for r in rec if r[0] == j], np.float64), axis=0)
+        nb = [r[2] for r in rec if r[0] == j][0]
+        tc = [r[4] for r in rec if r[0] == j][0]
         out = dupin.peel(dg, metric, k, e, flags=dupin.TIMING)
-        per_eps.append((out, algorithmic_bytes(g, out.peel_round, np.asarray(out.trace_size), rec[j][2], metric)))
-    bytes_dom = float(np.mean([b[names[dom]] for _, b in per_eps]))
-    # per-launch time of the dominant phase, averaged over the timed launches
+        b = algorithmic_bytes(g, out.peel_round, np.asarray(out.trace_size), nb, metric)
+        if follower[j]:  # its initial weights are a copy (w, round, live list: 24 B per vertex)
+            b["init"] = 24 * g.n
+        per_peel.append({"metric": metric, "eps": f"{e[0]}/{e[1]}", "rounds": int(out.n_rounds), "bulk_rounds": int(nb),
+                         "tail_ctas": int(tc), "init_copied": bool(follower[j]),
+                         "ms": {names[q]: round(float(ph[q]), 4) for q in range(4)},
+                         "algorithmic_bytes": {kk: int(b[kk]) for kk in names}})
+    # the dominant kernel: the largest total device time over the step's peels
+    # (a follower's copied initial weights are another kernel and left out)
+    tot = {}
+    for p in per_peel:
+        for q in names:
+            if q == "init" and p["init_copied"]:
+                continue
+            key = kernel_of(q, p["tail_ctas"])
+            t_, b_ = tot.get(key, (0.0, 0))
+            tot[key] = (t_ + p["ms"][q], b_ + p["algorithmic_bytes"][q])
+    kernel = max(tot, key=lambda kk: tot[kk][0])
+    t_dom, b_dom = tot[kernel]
+    launches = sum(1 for p in per_peel for q in names if kernel_of(q, p["tail_ctas"]) == kernel and
+                   not (q == "init" and p["init_copied"]))
     peak, peak_kind = measured_peaks()
-    achieved = bytes_dom / (mean_phase[dom] / 1e3) / 1e9 if mean_phase[dom] > 0 else 0.0
-    kernel = {"init": "k_init_vertex+k_init_arcs+k_init_reduce", "bulk": "k_peel_bulk",
-              "build": "k_tail_prep+k_tail_scan+k_tail_arcs", "tail": "k_peel_tail"}[names[dom]]
+    achieved = b_dom / (t_dom / 1e3) / 1e9 if t_dom > 0 else 0.0
     traffic = measured_traffic(kernel) if args.workload == "fd_2Mx1M_40M" else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "phase_ms_per_peel": {names[i]: round(float(mean_phase[i]), 4) for i in range(4)},
-                "algorithmic_bytes_per_peel": {kk: int(np.mean([b[kk] for _, b in per_eps])) for kk in names}}
-    tail_rounds = float(np.mean([r[1] - r[2] for r in rec]))
-    lat = round_latency(float(mean_phase[3]), tail_rounds, clocks.summary().get("sm_mhz") or 2070.0)
-    if lat is not None:
-        roofline["round_latency"] = lat
+                "launches_per_step": launches, "ms_per_step": round(t_dom, 4),
+                "algorithmic_bytes_per_step": int(b_dom),
+                "peak_source": f"{peak_kind} hbm_gbs", "per_peel": per_peel}
+    # the whole step against the same roofline: every phase's algorithmic bytes over the step time
+    step_bytes = sum(p["algorithmic_bytes"][q] for p in per_peel for q in names)
+    roofline["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_bytes / (ms / 1e3) / 1e9, 2),
+                        "frac": round(step_bytes / (ms / 1e3) / 1e9 / peak, 4)}
+    one_cta = [(p["ms"]["tail"], p["rounds"] - p["bulk_rounds"]) for p in per_peel if p["tail_ctas"] == 1]
+    if one_cta:
+        lat = round_latency(sum(t for t, _ in one_cta), sum(r for _, r in one_cta), sm_mhz)
+        if lat is not None:
+            roofline["round_latency"] = lat
+    cl = [(p["ms"]["tail"], p["rounds"] - p["bulk_rounds"]) for p in per_peel if p["tail_ctas"] > 1]
+    if cl and sum(r for _, r in cl) > 0:
+        roofline["cluster_tail_us_per_round"] = round(sum(t for t, _ in cl) * 1e3 / sum(r for _, r in cl), 3)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -495,10 +624,11 @@ def main():
                             pin_memory=True)
             t.numpy()[:] = a
             pinned.append(t.numpy())
+        del csr
         h2d = sum(a.nbytes for a in pinned if a is not None)
         d2h = 0
         # the results land in page-locked host buffers (allocated once)
-        res_bufs = [dupin.result_buffers(g.n, True, True, True, pinned=True) for _ in epss]
+        res_bufs = [dupin.result_buffers(g.n, True, True, True, pinned=True) for _ in peels]
 
         def e2e_step():
             nonlocal d2h
@@ -507,7 +637,7 @@ def main():
             else:
                 gg = dupin.Graph.load_symmetric(g.n, *pinned, g.a, stream=stream)
             d2h = 0
-            ps = [dupin.make_params(metric, k, e) for e in epss]
+            ps = [dupin.make_params(metric, k, e) for metric, e in peels]
             for o in dupin.peel_batch([gg] * len(ps), ps, want_rounds=True, want_trace=True, want_mask=True,
                                       stream=stream, buffers=res_bufs):
                 d2h += o.peel_round.nbytes + o.best_mask.nbytes + 32 * (o.n_rounds + 1)
@@ -523,28 +653,30 @@ def main():
         dt = (time.perf_counter() - t0) / ksteps
         e2e = {"value": world * edges_per_step / dt, "unit": "edges/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
-               "includes": "graph load from pinned host memory + validation + one batched call of the 3 peels "
+               "includes": "graph load from pinned host memory + validation + one batched call of the step's peels "
                            "(peel workspaces from the cache of freed graphs' workspaces) + result copies + free"}
+        del pinned
 
+    side = None if args.no_side or not args.workload.startswith("rmat") else side_runs(dupin, g, dg, stream, wl)
     batched = None if args.no_batch else bench_batched(dupin, stream, args)
     serving = None if args.no_serve else bench_serving(dupin, args)
 
     cpu = cpu_par = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, metric, epss[1] if len(epss) > 1 else epss[0], k)
-        cpu["unit"] = "edges/s"
-        cpu_par = cpu_parallel_baseline(g, metric, epss[1] if len(epss) > 1 else epss[0], k)
+        metric_b, eps_b = peels[-1] if len(peels) < 3 else peels[1]
+        cpu = cpu_baseline(g, metric_b, eps_b, k)
+        cpu_par = cpu_parallel_baseline(g, metric_b, eps_b, k)
 
-    launches_per_peel = 13  # reset, init x4, bulk, tail build x5, tail, mask
+    launches_per_peel = 14  # reset, init x4, bulk, tail build x5, one-CTA tail, cluster tail
     line = {
         "metric": "edges peeled/s", "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "metric": metric, "k_mult": k,
-                   "eps": [f"{a}/{b}" for a, b in epss], "n": g.n, "m": g.m, "arcs": 2 * g.m,
-                   "rounds": [int(o.n_rounds) for o, _ in per_eps],
-                   "bulk_rounds": [int(rec[j][2]) for j in range(len(epss))],
-                   "l2": "inputs larger than L2 (graph arrays ~1 GB vs 129 MB L2)",
+        "config": {"workload": args.workload, "graph": wl["graph"], "k_mult": k,
+                   "peels": [f"{m}:{e[0]}/{e[1]}" for m, e in peels], "n": g.n, "m": g.m, "arcs": 2 * g.m,
+                   "rounds": [p["rounds"] for p in per_peel], "bulk_rounds": [p["bulk_rounds"] for p in per_peel],
+                   "tail_ctas": [p["tail_ctas"] for p in per_peel], "generation_s": round(gen_s, 1),
+                   "l2": "inputs larger than L2 (graph arrays several GB vs 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -552,6 +684,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches_per_peel * len(params) * args.steps,
         "clocks": clocks.summary(),
+        "side": side,
         "batched": batched,
         "serving": serving,
     }

@@ -88,7 +88,8 @@ typedef struct dupin_graph dupin_graph;
  *
  * csr_w / csc_w may be NULL (all c = 1.0); vertex_w (length n) may be NULL
  * (all a = 0).  The edge set must be simple: no self-loops, no repeated
- * pairs.  Offsets are int64 and start at 0; ids are int32.
+ * pairs.  Every row lists its neighbour ids in strictly increasing order.
+ * Offsets are int64 and start at 0; ids are int32.
  */
 typedef struct {
     int64_t n_left, n_right;
@@ -105,10 +106,17 @@ typedef struct {
 /*
  * Copy a graph to the current CUDA device as one symmetric adjacency
  * (int64 row offsets, int32 neighbour ids, int64 Q32.32 arc weights) and
- * validate it (offsets monotone, ids in range, weights >= 0, every initial
- * peeling weight a_u + sum_v c_uv < 2^63, fewer than 2^40 arcs).  On
- * success *out owns the device copy until dupin_graph_free.  Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
- * Synchronises 'stream'.
+ * validate it on the device: offsets monotone from 0, ids in range, no
+ * self-loops, weights >= 0, every initial peeling weight a_u + sum_v c_uv <
+ * 2^63, fewer than 2^40 arcs, every row strictly increasing (no repeated
+ * pair), and symmetry -- every arc u -> v has the reverse arc v -> u with
+ * the same weight; for form (a), the CSC holds exactly the CSR's edges and
+ * weights.  Symmetry is checked by comparing a keyed 64-bit fingerprint of
+ * the arcs with that of the reversed arcs (the key is drawn once per
+ * process), so an asymmetric input is rejected except with probability
+ * about 2^-64.  On success *out owns the device copy until
+ * dupin_graph_free.  Errors: INVALID_ARG (any check above), OVERFLOW, OOM,
+ * CUDA.  Synchronises 'stream'.
  */
 int dupin_graph_load(const dupin_graph_desc *desc, void *stream, dupin_graph **out);
 
@@ -135,6 +143,8 @@ int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs
                                   w_u < g(S) (Sec. 5.2); implies DUPIN_GPO */
 #define DUPIN_RESULT_DEVICE 8u /* best_mask / peel_round / trace_* are device pointers */
 #define DUPIN_TIMING 16u       /* fill the phase_ms[] durations (CUDA events on 'stream') */
+#define DUPIN_TAIL_ONE_CTA 32u /* every tail runs in the one-CTA kernel (no cluster tail) */
+#define DUPIN_TAIL_CLUSTER 64u /* every tail runs in the cluster kernel (never one CTA) */
 
 typedef struct {
     int32_t metric;     /* DUPIN_DG, DUPIN_DW or DUPIN_FD */
@@ -143,12 +153,13 @@ typedef struct {
     int64_t eps_den;    /* 1 .. 2^24 */
     int64_t max_rounds; /* <= 0: n + 1 */
     uint32_t flags;
-    int32_t tail_cap;   /* <= 0: automatic; else live-set size below which one CTA finishes */
-    int64_t tail_arc_cap; /* <= 0: automatic (2^16); else, once |S| <= tail_cap, the
-                             one CTA takes over when the live sub-graph has at most
+    int32_t tail_cap;   /* <= 0: automatic; else the live-set size at or below which
+                           a tail (one CTA or a cluster) may finish the peel */
+    int64_t tail_arc_cap; /* <= 0: automatic (2^16); else, once |S| fits a tail, the
+                             tail takes over when the live sub-graph has at most
                              this many arcs (2 |E(S)|) or after a round that removed
-                             at most 64 vertices (if it has at most 2^27 arcs),
-                             whichever comes first */
+                             at most 64 vertices or expanded at most 2^18 arcs (if the
+                             sub-graph has at most 2^27 arcs), whichever comes first */
 } dupin_params;
 
 /*
@@ -161,10 +172,19 @@ typedef struct {
  * Scalars (always host): n_rounds R, best_round b (S_b = {u : peel_round[u]
  * > b}), |S_b|, f(S_b) as (hi, lo), g(S_b) as a double (value, not Q32.32),
  * how many rounds used the minimum-weight rule, how many rounds ran in the
- * grid-wide kernel (the rest ran in the one-CTA tail), the tail's arc
- * count (0 when the grid-wide rounds emptied S), and with DUPIN_TIMING
- * the device time of each phase: [0] initial weights, [1] grid-wide rounds,
- * [2] tail sub-graph build, [3] one-CTA rounds.
+ * grid-wide kernel (the rest ran in a tail), the tail's arc count (0 when
+ * the grid-wide rounds emptied S), with DUPIN_TIMING the device time of
+ * each phase: [0] initial weights, [1] grid-wide rounds, [2] tail sub-graph
+ * build, [3] tail rounds; and the CTAs of the tail that ran (1: the one-CTA
+ * tail, 8 or 16: the cluster tail, 0: no tail).
+ *
+ * The tail: once the live set is small, one of two kernels finishes the
+ * peel on the live sub-graph -- one CTA with the state in its shared memory
+ * (live sets of at most about 14,900 vertices whose sub-graph has at most
+ * 2^20 arcs), or a thread-block cluster of 8 or 16 CTAs with the state
+ * spread over their shared memory (live sets of up to about 160,000
+ * vertices).  Both give identical results; the flags DUPIN_TAIL_ONE_CTA and
+ * DUPIN_TAIL_CLUSTER force one of them.
  */
 typedef struct {
     uint8_t *best_mask;
@@ -182,8 +202,9 @@ typedef struct {
     double best_density;
     int64_t n_min_rule;
     int64_t n_bulk_rounds;
-    int64_t tail_arcs;  /* arcs of the live sub-graph the one-CTA tail started on */
+    int64_t tail_arcs;  /* arcs of the live sub-graph the tail started on */
     float phase_ms[4];
+    int64_t tail_ctas;  /* CTAs of the tail that ran: 1, 8 or 16 (0: none) */
 } dupin_result;
 
 /*

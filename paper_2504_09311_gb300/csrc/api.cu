@@ -5,6 +5,8 @@
 
 #include <string>
 
+#include <chrono>
+
 #include "dupin_internal.h"
 
 static thread_local std::string t_last_error;
@@ -40,4 +42,14 @@ extern "C" int64_t dupin_struct_size(const char *name) {
     if (n == "dupin_serve_config") return (int64_t)sizeof(dupin_serve_config);
     if (n == "dupin_serve_stats_t") return (int64_t)sizeof(dupin_serve_stats_t);
     return -1;
+}
+
+// The key of the arc fingerprints that the symmetry checks sum (sym_mix): one
+// per process, drawn at first use from the clock and an address, so that no
+// fixed input can be built to cancel a missing reverse arc.
+unsigned long long fingerprint_key() {
+    static const unsigned long long key = fmix64(
+        (unsigned long long)std::chrono::steady_clock::now().time_since_epoch().count() ^
+        (unsigned long long)(uintptr_t)&key ^ 0x5bd1e9955bd1e995ULL);
+    return key;
 }

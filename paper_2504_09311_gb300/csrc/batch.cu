@@ -713,10 +713,17 @@ static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params 
         if (rc) return fail_at(q, rc);
     }
     // With few peels, peel q's grid-wide stage runs beside the tails of peels
-    // 0 .. q-1 on one block per SM fewer per running tail (each tail holds one
-    // SM), so that its cooperative grid always fits; with many peels every
-    // grid-wide stage runs first, on all SMs, and the tails after them.
-    const bool overlap = k <= TAIL_OVERLAP_MAX;
+    // 0 .. q-1 on one block per SM fewer per SM a running tail may hold (one
+    // for the one-CTA tail, the cluster's CTAs for the cluster tail), so that
+    // its cooperative grid always fits; with many peels every grid-wide stage
+    // runs first, on all SMs, and the tails after them.
+    const int cl_sms = cluster_ctas();
+    bool overlap = k <= TAIL_OVERLAP_MAX;
+    {
+        long long held = 0;
+        for (size_t q = 0; q + 1 < k; q++) held += plans[q].cl_cap > 0 ? cl_sms : 1;
+        if (overlap && ws[0] && held > ws[0]->grid / 2) overlap = false;
+    }
     if (!overlap) {
         for (size_t q = 0; q < k; q++) {
             int rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s);
@@ -725,9 +732,10 @@ static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params 
     }
     std::vector<cudaEvent_t> ev(2 * k, nullptr);
     int rc = DUPIN_OK;
+    int held = 0;  // SMs the tails queued so far may hold
     for (size_t q = 0; q < k && rc == DUPIN_OK; q++) {
         if (overlap) {
-            const int grid = ws[q]->grid - (int)q;
+            const int grid = ws[q]->grid - held;
             rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s, nullptr,
                                      grid > 0 ? grid : 1);
             if (rc) break;
@@ -749,6 +757,7 @@ static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params 
         }
         rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_TAIL, t);
         if (rc) break;
+        held += plans[q].cl_cap > 0 ? cl_sms : 1;
         e = cudaEventRecord(ev[2 * q + 1], t);
         if (e != cudaSuccess) rc = dupin_cuda_fail(e, "tail stream join");
     }

@@ -23,17 +23,23 @@ typedef unsigned __int128 u128;
 // back-off below) and report DUPIN_ERR_TIMEOUT instead of hanging.
 #define DUPIN_SPIN_LIMIT (1ll << 21)
 
-// A grid-wide round that removed at most this many vertices is "small":
-// once S fits the one-CTA tail, the tail takes over after such a round
-// whatever the live arc count.
+// A grid-wide round that removed at most this many vertices, or expanded at
+// most DUPIN_TAIL_SMALL_ARCS arcs, is "small": once S fits a tail, the tail
+// takes over after such a round whatever the live arc count.
 #define DUPIN_TAIL_SMALL_ROUND 64
+#define DUPIN_TAIL_SMALL_ARCS (1LL << 18)
+// The one-CTA tail takes a live set of at most tail_cap vertices only when
+// its sub-graph has at most this many arcs (one SM fetches them); larger
+// ones go to the cluster tail.
+#define DUPIN_ONE_CTA_ARCS (1LL << 20)
 // ... provided its live sub-graph fits the tail's arc buffer (2^27 arcs)
 #define DUPIN_TAIL_BUF_ARCS (1LL << 27)
 
 // Peeling phases recorded in PeelCtl::status
 #define ST_RUNNING 0
 #define ST_DONE 1
-#define ST_TAIL 2
+#define ST_TAIL 2     // the one-CTA tail finishes the peel
+#define ST_CLUSTER 3  // the cluster tail finishes the peel
 
 // Device-resident control block of one peel.  'bar_*' is the grid barrier;
 // the rest is the state after the last completed round.
@@ -61,7 +67,7 @@ struct PeelCtl {
     unsigned long long init_lo, init_hi;  // sum over u of (w_u + a_u) = 2 f(V)
     long long init_min;
     int init_overflow;
-    int pad1;
+    int tail_ctas;  // CTAs of the tail that finished the peel (0: none ran)
 };
 
 // Per-block partial results of one bulk round (one 128-byte line each)
@@ -123,8 +129,11 @@ struct PeelArgs {
     int gpo;            // Algorithm 3
     int lpo;            // Algorithm 4 (with gpo)
     long long max_rounds;
-    long long tail_cap;     // the tail takes over once |S| <= tail_cap ...
-    long long tail_arcs;    // ... and 2 |E(S)| <= tail_arcs
+    long long tail_cap;     // the one-CTA tail takes |S| <= tail_cap ...
+    long long one_arcs;     // ... with 2 |E(S)| <= one_arcs; otherwise the cluster tail
+    long long cl_cap;       // the cluster tail takes |S| <= cl_cap (0: no cluster tail)
+    long long hcap;         // max(tail_cap, cl_cap): the grid-wide rounds hand over below it ...
+    long long tail_arcs;    // ... once 2 |E(S)| <= tail_arcs or after a small round
     // tail sub-graph
     int *loc;           // global id -> local id (valid for live vertices)
     long long *tdeg;    // tail: full degree prefix [L+1]
@@ -293,6 +302,26 @@ __device__ __forceinline__ long long warp_incl_scan64(long long x) {
         if (lane >= d) x += o;
     }
     return x;
+}
+
+// A keyed 64-bit fingerprint of an arc (u -> v, weight c) for symmetry
+// checks: summed over all arcs with a wrapping add, sym_mix(u, v, c) and
+// sym_mix(v, u, c) give the same total when every arc has a reverse arc of
+// the same weight (the multiset of arcs equals its reverse); a missing or
+// re-weighted reverse arc leaves the totals different except with
+// probability about 2^-64 over the key.  (SplitMix64's finaliser.)
+__host__ __device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ULL;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebULL;
+    x ^= x >> 31;
+    return x;
+}
+__host__ __device__ __forceinline__ unsigned long long sym_mix(unsigned long long key, long long u, long long v,
+                                                               long long c) {
+    const unsigned long long h = fmix64(key ^ (((unsigned long long)u << 32) | (unsigned long long)(unsigned)v));
+    return fmix64(h + (unsigned long long)c * 0x9e3779b97f4a7c15ULL + key);
 }
 
 __device__ __forceinline__ void set_error(PeelCtl *ctl, int code) { atomicCAS(&ctl->error, 0, code); }

@@ -14,6 +14,8 @@ void dupin_set_error(const std::string &msg);
 int dupin_fail(int code, const std::string &msg);
 // CUDA error -> DUPIN_ERR_CUDA with the runtime's text
 int dupin_cuda_fail(cudaError_t e, const char *what);
+// the per-process key of the symmetry fingerprints (sym_mix)
+unsigned long long fingerprint_key();
 
 #define DUPIN_CUDA_TRY(expr)                                   \
     do {                                                       \
@@ -70,6 +72,9 @@ struct dupin_graph {
 // takes over once |S| <= tail_cap and 2 |E(S)| <= tail_arcs.
 struct PeelPlan {
     long long tail_cap = 0, tail_arcs = 0, max_rounds = 0, tr_cap = 0;
+    long long cl_cap = 0;    // cluster tail capacity (0: none)
+    long long one_arcs = 0;  // the one-CTA tail's live-arc limit
+    long long hcap() const { return tail_cap > cl_cap ? tail_cap : cl_cap; }
 };
 
 DevGraph dev_graph(const dupin_graph *g, int metric);
@@ -121,6 +126,13 @@ void launch_mask(const int *pr, long long n, long long best_round, uint8_t *mask
 
 // a whole peel of a small graph with caller-supplied buffers (no allocation)
 int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStream_t s);
+
+// the cluster tail (cluster.cu): its live-set capacity on the current device,
+// its CTAs per cluster, and its launch (the kernel returns at once unless the
+// peel's status says the cluster finishes it)
+long long cluster_cap_limit();
+int cluster_ctas();
+int launch_cluster_tail(const PeelArgs &A, cudaStream_t s);
 
 // the largest live set the single-CTA tail accepts, and the default caps
 long long tail_cap_limit();

@@ -6,9 +6,14 @@
 // vertices: rows [0, n_left) are users whose neighbour ids are shifted by
 // n_left (items become vertices n_left + i), rows [n_left, n) are items.
 // Validation runs on the device: offsets monotone and starting at 0, ids in
-// range, no self-loops, weights >= 0 (Property 3.1), and every initial
-// peeling weight a_u + sum_v c_uv below 2^63 (checked with the same
-// segmented-sum kernel the peel uses).
+// range, no self-loops, weights >= 0 (Property 3.1), every initial peeling
+// weight a_u + sum_v c_uv below 2^63 (checked with the same segmented-sum
+// kernel the peel uses), every row's neighbour ids strictly increasing (so
+// no pair repeats), and the adjacency symmetric with equal weights on an
+// arc and its reverse -- for a bipartite graph, the CSC holds exactly the
+// CSR's edges -- by a keyed fingerprint of the arc multiset against its
+// reverse (a missing or re-weighted reverse arc passes with probability
+// about 2^-64).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -137,6 +142,31 @@ __global__ void k_encode_hub_arcs(int *col, long long arcs, const int *slot_of) 
         const int h = slot_of[col[p]];
         if (h >= 0) col[p] = -(h + 1);
     }
+}
+
+// Every row strictly increasing (flags[0] = 1 otherwise) and the symmetry
+// fingerprint sum over arcs u -> v of sym_mix(u, v, c) - sym_mix(v, u, c)
+// (flags + 2, a wrapping 64-bit sum: 0 for a symmetric adjacency).  One warp
+// per row, lanes striding over its arcs.
+__global__ void k_check_rows(const long long *rp, const int *col, const long long *cw, long long n,
+                             unsigned long long key, int *flags) {
+    const int lane = threadIdx.x & 31;
+    const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long fp = 0;
+    bool bad = false;
+    for (long long u = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += W) {
+        const long long b = rp[u], e = rp[u + 1];
+        for (long long p = b + lane; p < e; p += 32) {
+            const int v = col[p];
+            if (p + 1 < e && col[p + 1] <= v) bad = true;
+            const long long c = cw ? cw[p] : DUPIN_Q_ONE;
+            fp += sym_mix(key, u, v, c) - sym_mix(key, v, u, c);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&flags[0], 1);
+    // wrapping sum over the warp, then one atomic per warp
+    for (int d = 16; d > 0; d >>= 1) fp += __shfl_down_sync(0xffffffffu, fp, d);
+    if (lane == 0 && fp) atomicAdd((unsigned long long *)(flags + 2), fp);
 }
 
 __global__ void k_fill_i32(int *x, long long n, int v) {
@@ -369,6 +399,34 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
             return dupin_fail(has_w ? DUPIN_ERR_OVERFLOW : DUPIN_ERR_INVALID_ARG,
                               "invalid graph: a neighbour id out of range, a self-loop, a negative weight, or a "
                               "peeling weight >= 2^63");
+        }
+    }
+    // sorted rows without repeats, and symmetry (ids are in range by now)
+    if (arcs > 0) {
+        int *fl = nullptr;
+        TRY(galloc((void **)&fl, 16, s));
+        e = cudaMemsetAsync(fl, 0, 16, s);
+        if (e == cudaSuccess) {
+            k_check_rows<<<sms * 8, 256, 0, s>>>(g->rp, g->col, g->cw, n, fingerprint_key(), fl);
+            e = cudaGetLastError();
+        }
+        int hf[4] = {0, 0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hf, fl, 16, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        gfree(fl, s);
+        TRY(e);
+        unsigned long long fp = 0;
+        memcpy(&fp, hf + 2, sizeof(fp));
+        if (hf[0] || fp) {
+            graph_release(g);
+            gfree(bad, s);
+            if (hf[0])
+                return dupin_fail(DUPIN_ERR_INVALID_ARG, "invalid graph: a row's neighbour ids are not strictly "
+                                                         "increasing (unsorted, or a repeated pair)");
+            return dupin_fail(DUPIN_ERR_INVALID_ARG,
+                              bip ? "invalid graph: the CSC does not hold the CSR's edges with the same weights"
+                                  : "invalid graph: the CSR is not symmetric (an arc without a reverse arc of "
+                                    "equal weight)");
         }
     }
 #undef TRY

@@ -77,15 +77,24 @@ __global__ void k_noalloc_check(const long long *rp, const int *col, const long 
     (void)cw;
 }
 
-// ids in range, no self-loops, weights >= 0 (run only after the offsets passed)
+// ids in range, no self-loops, weights >= 0 (run only after the offsets
+// passed); flags[4..5] accumulate the symmetry fingerprint (sum over arcs of
+// sym_mix(u, v, c) - sym_mix(v, u, c), zero for a symmetric CSR)
 __global__ void k_noalloc_check_arcs(const long long *rp, const int *col, const long long *cw, long long n,
-                                     int *flags) {
+                                     unsigned long long key, int *flags) {
+    unsigned long long fp = 0;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
         for (long long p = rp[u]; p < rp[u + 1]; p++) {
             const int v = col[p];
-            if (v < 0 || v >= n || v == u || (cw && cw[p] < 0)) atomicExch(&flags[0], 1);
+            const long long c = cw ? cw[p] : DUPIN_Q_ONE;
+            if (v < 0 || v >= n || v == u || c < 0) {
+                atomicExch(&flags[0], 1);
+                continue;
+            }
+            fp += sym_mix(key, u, v, c) - sym_mix(key, v, u, c);
         }
     }
+    if (fp) atomicAdd((unsigned long long *)(flags + 4), fp);
 }
 
 __global__ void k_noalloc_mask(const int *pr, long long n, long long best_round, uint8_t *mask) {
@@ -132,17 +141,23 @@ extern "C" int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32
     // validate the caller's CSR before any kernel indexes through it
     DUPIN_CUDA_TRY(cudaMemsetAsync(flags, 0, NOALLOC_FLAG_BYTES, s));
     k_noalloc_check<<<32, 256, 0, s>>>(rp, col, cw, a, n, flags);
-    int hflags[4] = {0, 0, 0, 0};
+    DUPIN_CUDA_TRY(cudaGetLastError());
+    int hflags[6] = {0, 0, 0, 0, 0, 0};
     DUPIN_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
     DUPIN_CUDA_TRY(cudaStreamSynchronize(s));
     long long arcs = 0;
     memcpy(&arcs, hflags + 2, sizeof(arcs));
     if (hflags[0] || arcs < 0) return dupin_fail(DUPIN_ERR_INVALID_ARG, "invalid CSR offsets or vertex weights");
+    if (arcs & 1) return dupin_fail(DUPIN_ERR_INVALID_ARG, "a symmetric CSR has an even arc count");
     if (arcs > 0 && !col) return dupin_fail(DUPIN_ERR_INVALID_ARG, "col_idx is NULL");
-    k_noalloc_check_arcs<<<32, 256, 0, s>>>(rp, col, cw, n, flags);
-    DUPIN_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    k_noalloc_check_arcs<<<32, 256, 0, s>>>(rp, col, cw, n, fingerprint_key(), flags);
+    DUPIN_CUDA_TRY(cudaGetLastError());
+    DUPIN_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
     DUPIN_CUDA_TRY(cudaStreamSynchronize(s));
     if (hflags[0]) return dupin_fail(DUPIN_ERR_INVALID_ARG, "invalid CSR: neighbour id out of range, self-loop or negative weight");
+    unsigned long long fp = 0;
+    memcpy(&fp, hflags + 4, sizeof(fp));
+    if (fp) return dupin_fail(DUPIN_ERR_INVALID_ARG, "the CSR is not symmetric (an arc without a reverse arc of equal weight)");
 
     PeelArgs A;
     memset(&A, 0, sizeof(A));
@@ -169,7 +184,11 @@ extern "C" int dupin_peel_noalloc(int64_t n, const int64_t *row_ptr, const int32
     A.gpo = (p.flags & (DUPIN_GPO | DUPIN_LPO)) ? 1 : 0;
     A.lpo = (p.flags & DUPIN_LPO) ? 1 : 0;
     A.max_rounds = p.max_rounds > 0 ? p.max_rounds : n + 1;
-    A.tail_cap = DUPIN_NOALLOC_MAX_N;
+    // the one-CTA kernel's shared memory follows the graph's size
+    A.tail_cap = n;
+    A.hcap = n;
+    A.cl_cap = 0;
+    A.one_arcs = 0x7fffffffffffffffLL;
     A.tail_arcs = arcs;
     // the graph itself is the one-CTA kernel's sub-graph (local ids = ids)
     A.tlrp = (long long *)rp;

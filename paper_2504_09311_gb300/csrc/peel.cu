@@ -302,7 +302,11 @@ __global__ void k_init_finish(PeelArgs A, long long n) {
     c->elive = A.g.arcs / 2;
     c->tail_arcs = 0;
     if (c->init_overflow) c->error = DUPIN_ERR_OVERFLOW;
-    c->status = n == 0 ? ST_DONE : (n <= A.tail_cap && A.g.arcs <= A.tail_arcs ? ST_TAIL : ST_RUNNING);
+    c->tail_ctas = 0;
+    if (n == 0) c->status = ST_DONE;
+    else if (n <= A.hcap && A.g.arcs <= A.tail_arcs)
+        c->status = n <= A.tail_cap && A.g.arcs <= A.one_arcs ? ST_TAIL : ST_CLUSTER;
+    else c->status = ST_RUNNING;
     if (A.tr_cap > 0) {
         A.tr_f_hi[0] = (long long)c->f_hi;
         A.tr_f_lo[0] = c->f_lo;
@@ -355,6 +359,7 @@ __device__ __forceinline__ void peel_bulk_body(const PeelArgs &A, const int b, c
     __shared__ struct {
         unsigned long long wlo, whi;  // sum of the selected vertices' weights
         long long U_sel, newSize;
+        long long arcs;     // arcs the round expanded
         long long minsurv;  // minimum weight of this round's survivors before its decrements
         int minrule, compact;
     } s_rd;
@@ -389,17 +394,19 @@ __device__ __forceinline__ void peel_bulk_body(const PeelArgs &A, const int b, c
         st.scan = ctl->scan_volume;
         s_elive = ctl->elive;
         s_rd.U_sel = kMaxLL;  // no round yet
+        s_rd.arcs = kMaxLL;
     }
     __syncthreads();
     if (ctl->status != ST_RUNNING || ctl->error) return;
 
     for (;;) {
         const long long size = s_st.size;
-        // the one-CTA tail takes over once S fits it and either its arcs are
-        // few or the rounds have become small (a round of few vertices costs
-        // the tail microseconds and the grid-wide kernel its barriers)
-        if (size == 0 || (size <= A.tail_cap && (2 * s_elive <= A.tail_arcs ||
-                                                  (s_rd.U_sel <= DUPIN_TAIL_SMALL_ROUND && 2 * s_elive <= A.tarc_cap))))
+        // a tail (one CTA or a cluster) takes over once S fits it and either
+        // its arcs are few or the rounds have become small (a round of few
+        // vertices or arcs costs a tail microseconds and the grid-wide kernel
+        // its barriers)
+        const bool small_round = s_rd.U_sel <= DUPIN_TAIL_SMALL_ROUND || s_rd.arcs <= DUPIN_TAIL_SMALL_ARCS;
+        if (size == 0 || (size <= A.hcap && (2 * s_elive <= A.tail_arcs || (small_round && 2 * s_elive <= A.tarc_cap))))
             break;
         if (s_st.round >= A.max_rounds) {
             if (b == 0 && tid == 0) set_error(ctl, DUPIN_ERR_NO_PROGRESS);
@@ -627,9 +634,10 @@ __device__ __forceinline__ void peel_bulk_body(const PeelArgs &A, const int b, c
             __syncthreads();
         }
         const long long newSize = size - U_sel;
-        const bool compact = newSize > 0 && (2 * newSize <= L || newSize <= A.tail_cap);
+        const bool compact = newSize > 0 && (2 * newSize <= L || newSize <= A.hcap);
         if (tid == 0) {
             s_rd.U_sel = U_sel;
+            s_rd.arcs = totArcs;
             s_rd.newSize = newSize;
             s_rd.minrule = minrule ? 1 : 0;
             s_rd.compact = compact ? 1 : 0;
@@ -868,7 +876,9 @@ __device__ __forceinline__ void peel_bulk_body(const PeelArgs &A, const int b, c
         ctl->scan_volume = st.scan;
         ctl->bulk_rounds = st.round;
         ctl->elive = s_elive;
-        if (ctl->error == 0) ctl->status = st.size == 0 ? ST_DONE : ST_TAIL;
+        if (ctl->error == 0)
+            ctl->status = st.size == 0 ? ST_DONE
+                          : (st.size <= A.tail_cap && 2 * s_elive <= A.one_arcs ? ST_TAIL : ST_CLUSTER);
     }
 }
 
@@ -879,7 +889,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) { pee
 // local ids and full degrees of the live vertices
 __global__ void k_tail_prep(PeelArgs A) {
     const PeelCtl *c = A.ctl;
-    if (c->status != ST_TAIL || c->error) return;
+    if ((c->status != ST_TAIL && c->status != ST_CLUSTER) || c->error) return;
     const long long L = c->live_len;
     const int *live = c->live_sel ? A.live1 : A.live0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L; p += (long long)gridDim.x * blockDim.x) {
@@ -893,7 +903,7 @@ __global__ void k_tail_prep(PeelArgs A) {
 __global__ void __launch_bounds__(SCAN_THREADS) k_tail_scan(PeelArgs A, long long *x, const int *cnt) {
     __shared__ long long s_w[SCAN_THREADS / 32];
     const PeelCtl *c = A.ctl;
-    if (c->status != ST_TAIL || c->error) return;
+    if ((c->status != ST_TAIL && c->status != ST_CLUSTER) || c->error) return;
     const long long L = c->live_len;
     long long carry = 0;
     for (long long b0 = 0; b0 < L; b0 += SCAN_THREADS) {
@@ -920,7 +930,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
     __shared__ long long s_start[WALK_WIN + 1];
     __shared__ long long s_k0;
     const PeelCtl *c = A.ctl;
-    if (c->status != ST_TAIL || c->error) return;
+    if ((c->status != ST_TAIL && c->status != ST_CLUSTER) || c->error) return;
     const long long L = c->live_len;
     const int *live = c->live_sel ? A.live1 : A.live0;
     const long long tot = A.tdeg[L];
@@ -1255,6 +1265,7 @@ __device__ __forceinline__ void peel_tail_body(const PeelArgs &A, unsigned char 
         ctl->gpo_lt = st.gpo_lt;
         ctl->n_min_rule = st.n_min_rule;
         ctl->scan_volume = st.scan;
+        ctl->tail_ctas = 1;
         if (!err) ctl->status = ST_DONE;
     }
 }
@@ -1321,11 +1332,16 @@ int peel_grid_size() {
     return std::min(sms * occ, WALK_WIN);
 }
 
+// raise k_peel_tail's dynamic shared-memory limit, once per device (the
+// limit is a per-device attribute of the function)
 static int set_tail_smem() {
-    static int done = -1;
-    if (done == 0) return DUPIN_OK;
+    static std::mutex mu;
+    static bool done[64] = {false};
     int dev = 0, smem = 0;
     cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return dupin_fail(DUPIN_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return DUPIN_OK;
     cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, k_peel_tail);
@@ -1333,7 +1349,7 @@ static int set_tail_smem() {
     int dyn = smem - (int)fa.sharedSizeBytes;
     e = cudaFuncSetAttribute(k_peel_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return dupin_cuda_fail(e, "cudaFuncSetAttribute(k_peel_tail)");
-    done = 0;
+    done[dev] = true;
     return DUPIN_OK;
 }
 
@@ -1348,8 +1364,11 @@ static int check_params(const dupin_graph *g, const dupin_params *p) {
     if (p->k_mult < 1 || p->k_mult > 64) return dupin_fail(DUPIN_ERR_INVALID_ARG, "k_mult must be in 1..64");
     if (p->eps_den < 1 || p->eps_den > (1LL << 24) || p->eps_num < 0 || p->eps_num > (1LL << 30))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "eps must be eps_num/eps_den with 0 <= eps_num <= 2^30, 1 <= eps_den <= 2^24");
-    if (p->flags & ~(uint32_t)(DUPIN_GPO | DUPIN_LPO | DUPIN_RESULT_DEVICE | DUPIN_TIMING))
+    if (p->flags & ~(uint32_t)(DUPIN_GPO | DUPIN_LPO | DUPIN_RESULT_DEVICE | DUPIN_TIMING | DUPIN_TAIL_ONE_CTA |
+                               DUPIN_TAIL_CLUSTER))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown flag");
+    if ((p->flags & DUPIN_TAIL_ONE_CTA) && (p->flags & DUPIN_TAIL_CLUSTER))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TAIL_ONE_CTA and DUPIN_TAIL_CLUSTER exclude each other");
     if (p->metric != DUPIN_DG && g->cw == nullptr)
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "DW/FD need edge weights; the graph was loaded without them");
     return DUPIN_OK;
@@ -1372,12 +1391,12 @@ DevGraph dev_graph(const dupin_graph *g, int metric) {
 // min(all arcs, |S| (|S| - 1)) arcs, and the grid-wide rounds go on while it
 // has more than DUPIN_TAIL_BUF_ARCS.
 static long long tail_arc_buffer(long long arcs, const PeelPlan &plan) {
-    const long long tc = plan.tail_cap;
+    const long long tc = plan.hcap();
     return std::min<long long>(std::min<long long>(arcs, tc * (tc > 0 ? tc - 1 : 0)), DUPIN_TAIL_BUF_ARCS);
 }
 
 long long workspace_bytes(long long n, long long arcs, bool has_cw, const PeelPlan &plan, int grid) {
-    const long long tail_cap = plan.tail_cap, tr_cap = plan.tr_cap;
+    const long long tail_cap = plan.hcap(), tr_cap = plan.tr_cap;
     const long long tarc = tail_arc_buffer(arcs, plan);
     long long b = 0;
     // w, pr, live0, live1, stage_id, stage_start, stage_off, fstart, loc, mask; fbase
@@ -1409,7 +1428,7 @@ void workspace_free(PeelWorkspace *ws) { workspace_free(ws, 0); }
 
 PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const PeelPlan &plan, bool async,
                                 cudaStream_t s, int *rc) {
-    const long long tail_cap = plan.tail_cap, tr_cap = plan.tr_cap;
+    const long long tail_cap = plan.hcap(), tr_cap = plan.tr_cap;
     PeelWorkspace *ws = new PeelWorkspace();
     cudaGetDevice(&ws->device);
     ws->n = n;
@@ -1470,7 +1489,7 @@ static std::vector<PeelWorkspace *> g_pool;
 
 static bool workspace_fits(const PeelWorkspace *ws, int dev, long long n, long long tarc, bool has_cw,
                            const PeelPlan &plan) {
-    return ws->device == dev && !ws->async && ws->n >= n && ws->tarc_cap >= tarc && ws->tail_cap >= plan.tail_cap &&
+    return ws->device == dev && !ws->async && ws->n >= n && ws->tarc_cap >= tarc && ws->tail_cap >= plan.hcap() &&
            ws->tr_cap >= plan.tr_cap && (ws->tcw != nullptr || !has_cw);
 }
 
@@ -1524,7 +1543,7 @@ static int workspace_ensure_ref(dupin_graph *g, PeelWorkspace *&slot, const Peel
     if (ws && workspace_fits(ws, g->device, g->n, tarc, has_cw, plan)) return DUPIN_OK;
     PeelPlan big = plan;
     if (ws) {  // grow to cover both the old and the new caps
-        big.tail_cap = std::max(plan.tail_cap, ws->tail_cap);
+        big.cl_cap = std::max(plan.hcap(), ws->tail_cap);
         big.tr_cap = std::max(plan.tr_cap, ws->tr_cap);
         workspace_release(ws);
         slot = nullptr;
@@ -1576,6 +1595,9 @@ static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const d
     A.lpo = (p->flags & DUPIN_LPO) ? 1 : 0;
     A.max_rounds = plan.max_rounds;
     A.tail_cap = plan.tail_cap;
+    A.one_arcs = plan.one_arcs;
+    A.cl_cap = plan.cl_cap;
+    A.hcap = plan.hcap();
     A.tail_arcs = std::min<long long>(plan.tail_arcs, ws->tarc_cap);
     A.loc = ws->loc;
     A.tdeg = ws->tdeg;
@@ -1617,7 +1639,7 @@ __global__ void k_init_follow_ctl(const PeelCtl *src, PeelCtl *dst) {
 int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, const PeelPlan &plan,
                         int stages, cudaStream_t s, const PeelWorkspace *init_from, int bulk_grid) {
     PeelArgs A = make_args(g, ws, p, plan);
-    const long long tail_cap = plan.tail_cap;
+    const long long tail_cap = plan.hcap();  // tail buffers hold this many vertices
     const bool timing = (p->flags & DUPIN_TIMING) != 0;
     if (timing && !ws->ev[0]) {
         for (int j = 0; j < 7; j++) DUPIN_CUDA_TRY(cudaEventCreate(&ws->ev[j]));
@@ -1641,7 +1663,7 @@ int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_par
     }
     if (stages & PEEL_BULK) {
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[2], s));
-        if (g->n > tail_cap || g->arcs > A.tail_arcs) {
+        if (g->n > A.hcap || g->arcs > A.tail_arcs) {
             const int grid = bulk_grid > 0 && bulk_grid < ws->grid ? bulk_grid : ws->grid;
             void *args[] = {&A};
             cudaError_t e =
@@ -1667,9 +1689,17 @@ int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_par
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[5], s));
     }
     if (stages & PEEL_TAIL) {
-        rc = set_tail_smem();
-        if (rc) return rc;
-        k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(tail_cap), s>>>(A);
+        // the status the grid-wide stage (or the set-up) left picks one of
+        // the two tails; the other returns at once
+        if (plan.tail_cap > 0) {
+            rc = set_tail_smem();
+            if (rc) return rc;
+            k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(plan.tail_cap), s>>>(A);
+        }
+        if (plan.cl_cap > 0) {
+            rc = launch_cluster_tail(A, s);
+            if (rc) return rc;
+        }
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[6], s));
     }
     cudaError_t e = cudaGetLastError();
@@ -1685,8 +1715,22 @@ int enqueue_peel(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p,
 int peel_resolve(const dupin_graph *g, const dupin_params *p, PeelPlan *plan) {
     int rc = check_params(g, p);
     if (rc) return rc;
-    long long lim = tail_cap_limit();
-    plan->tail_cap = p->tail_cap > 0 ? std::min<long long>(p->tail_cap, lim) : tail_cap_default();
+    const long long lim = tail_cap_limit();
+    const long long user = p->tail_cap > 0 ? p->tail_cap : 0;
+    plan->tail_cap = user ? std::min<long long>(user, lim) : tail_cap_default();
+    plan->cl_cap = 0;
+    plan->one_arcs = DUPIN_ONE_CTA_ARCS;
+    if (!(p->flags & DUPIN_TAIL_ONE_CTA)) {
+        const long long climit = cluster_cap_limit();
+        if (climit <= 0) {
+            if (p->flags & DUPIN_TAIL_CLUSTER) return dupin_fail(DUPIN_ERR_CUDA, "no cluster tail on this device");
+        } else {
+            plan->cl_cap = user ? std::min<long long>(user, climit) : climit;
+        }
+    }
+    if (p->flags & DUPIN_TAIL_ONE_CTA) plan->one_arcs = 0x7fffffffffffffffLL;  // every tail on one CTA
+    if (plan->cl_cap == 0) plan->one_arcs = 0x7fffffffffffffffLL;
+    if (p->flags & DUPIN_TAIL_CLUSTER) plan->tail_cap = 0;  // every tail on the cluster
     plan->tail_arcs = p->tail_arc_cap > 0 ? p->tail_arc_cap : DUPIN_TAIL_ARCS_DEFAULT;
     plan->max_rounds = p->max_rounds > 0 ? p->max_rounds : g->n + 1;
     plan->tr_cap = std::min<long long>(plan->max_rounds, g->n) + 1;
@@ -1701,6 +1745,7 @@ int peel_finish(const dupin_graph *g, PeelWorkspace *ws, const dupin_params *p, 
     r->n_min_rule = c.n_min_rule;
     r->n_bulk_rounds = c.bulk_rounds;
     r->tail_arcs = c.tail_arcs;
+    r->tail_ctas = c.tail_ctas;
     for (int j = 0; j < 4; j++) r->phase_ms[j] = 0.f;
     if ((p->flags & DUPIN_TIMING) && ws->ev[0]) {
         // init, grid-wide rounds, tail build, tail (the stages of several peels

@@ -1,18 +1,21 @@
 // serve.cu -- continuous batching of peel requests over resident graphs.
 //
 // A worker thread owns 'max_slots' non-blocking CUDA streams.  Requests wait
-// in a FIFO queue.  Whenever a slot is free, the worker takes the queued
-// requests for graphs small enough for one CTA (as many as the device-memory
-// budget admits, in arrival order) and launches them together as one
-// persistent one-CTA-per-graph peel on that slot's stream; it does not wait
-// for it, so requests arriving meanwhile go into the next launch on another
-// slot and the launches run side by side on the GPU.  A graph that needs the
-// grid-wide persistent kernel runs alone (admitted only when no slot is busy,
-// nothing admitted beside it), so its cooperative grid never competes for
-// SMs.  Graphs stay resident and shared; only per-request state is allocated
-// (stream-ordered, counted against the budget).  Every request's arithmetic
-// is the same exact integer peel, so a result is identical whether it ran
-// alone or in a mix.
+// in a queue.  Whenever a slot is free, the worker takes the queued requests
+// for graphs small enough for one CTA (as many as the device-memory budget
+// admits, in arrival order, passing over large requests that cannot start
+// yet) and launches them together as one persistent one-CTA-per-graph peel
+// on that slot's stream; it does not wait for it, so requests arriving
+// meanwhile go into the next launch on another slot and the launches run side
+// by side on the GPU.  A graph that needs the grid-wide persistent kernel
+// starts as soon as a slot and the budget allow and no other large request
+// is running: on a high-priority stream (its blocks are placed first as SMs
+// free up) with a cooperative grid smaller than the GPU by a reserve of SMs,
+// so the small requests admitted before and after it keep running beside
+// it, and its tail (one CTA or a cluster) runs beside them too.  Graphs stay
+// resident and shared; only per-request state is allocated (stream-ordered,
+// counted against the budget).  Every request's arithmetic is the same exact
+// integer peel, so a result is identical whether it ran alone or in a mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +49,9 @@ struct Request {
     bool done = false;
 };
 
+// SMs a running large request leaves to the small requests' launches
+#define SERVE_SMALL_RESERVE 32
+
 // what one slot is running: a batch of small requests, or one large request
 struct Slot {
     std::vector<Request *> reqs;
@@ -54,6 +60,8 @@ struct Slot {
     long long bytes = 0;
     bool busy = false;
     bool large = false;
+    cudaStream_t st = nullptr;  // the stream its work runs on
+    cudaEvent_t ev = nullptr;   // recorded after it
     // the batch entry point wants arrays indexed by position
     std::vector<dupin_graph *> gs;
     std::vector<dupin_params> ps;
@@ -73,10 +81,12 @@ struct dupin_server {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
     std::vector<Slot> slots;
+    cudaStream_t large_stream = nullptr;  // high priority, for the one running large request
+    cudaEvent_t large_event = nullptr;
     long long used_bytes = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
-    bool exclusive = false;
+    bool large_running = false;
     long long submitted = 0, completed = 0, rejected = 0, launches = 0;
     std::vector<double> lat_ms;
     double first_submit = -1, last_done = 0;
@@ -94,7 +104,7 @@ static const size_t kMaxBatch = 4096;
 static bool admit(dupin_server *s, std::unique_lock<std::mutex> &lk) {
     bool progress = false;
     for (;;) {
-        if (s->queue.empty() || s->exclusive) return progress;
+        if (s->queue.empty()) return progress;
         int slot = -1;
         for (int i = 0; i < (int)s->slots.size(); i++)
             if (!s->slots[i].busy) {
@@ -103,40 +113,60 @@ static bool admit(dupin_server *s, std::unique_lock<std::mutex> &lk) {
             }
         if (slot < 0) return progress;
         Slot &sl = s->slots[slot];
-        Request *front = s->queue.front();
         sl.reqs.clear();
         sl.bytes = 0;
-        if (front->large) {
-            if (n_busy(s) > 0) return progress;  // waits for an idle GPU
-            if (s->used_bytes + front->bytes > s->cfg.memory_budget) return progress;
-            s->queue.pop_front();
-            sl.reqs.push_back(front);
-            sl.bytes = front->bytes;
+        // the first large request in arrival order starts once none is running
+        // and the budget admits it
+        Request *big = nullptr;
+        if (!s->large_running) {
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                if (!(*it)->large) continue;
+                if (s->used_bytes + (*it)->bytes <= s->cfg.memory_budget) {
+                    big = *it;
+                    s->queue.erase(it);
+                }
+                break;
+            }
+        }
+        if (big) {
+            sl.reqs.push_back(big);
+            sl.bytes = big->bytes;
             sl.large = true;
-            s->exclusive = true;
+            sl.st = s->large_stream;
+            sl.ev = s->large_event;
+            s->large_running = true;
         } else {
-            // consecutive small requests from the front, within the budget
-            while (!s->queue.empty() && sl.reqs.size() < kMaxBatch) {
-                Request *q = s->queue.front();
-                if (q->large) break;
+            // small requests in arrival order (large ones that cannot start are
+            // passed over), within the budget
+            for (auto it = s->queue.begin(); it != s->queue.end() && sl.reqs.size() < kMaxBatch;) {
+                Request *q = *it;
+                if (q->large) {
+                    ++it;
+                    continue;
+                }
                 if (s->used_bytes + sl.bytes + q->bytes > s->cfg.memory_budget) break;
-                s->queue.pop_front();
+                it = s->queue.erase(it);
                 sl.reqs.push_back(q);
                 sl.bytes += q->bytes;
             }
             if (sl.reqs.empty()) return progress;
             sl.large = false;
+            sl.st = s->streams[slot];
+            sl.ev = s->events[slot];
         }
         s->used_bytes += sl.bytes;
         sl.busy = true;
         s->launches++;
         lk.unlock();
-        cudaStream_t st = s->streams[slot];
+        cudaStream_t st = sl.st;
         int rc = DUPIN_OK;
         if (sl.large) {
             Request *q = sl.reqs[0];
             sl.ws = workspace_create(q->g->n, q->g->arcs, q->g->cw != nullptr, q->plan, true, st, &rc);
-            if (rc == DUPIN_OK) rc = enqueue_peel(q->g, sl.ws, &q->p, q->plan, st);
+            if (rc == DUPIN_OK) {
+                const int grid = sl.ws->grid - SERVE_SMALL_RESERVE;
+                rc = enqueue_peel_stages(q->g, sl.ws, &q->p, q->plan, PEEL_ALL, st, nullptr, grid > 16 ? grid : 16);
+            }
         } else {
             const size_t k = sl.reqs.size();
             sl.gs.resize(k);
@@ -152,7 +182,7 @@ static bool admit(dupin_server *s, std::unique_lock<std::mutex> &lk) {
             rc = cta_batch_enqueue(sl.gs.data(), sl.ps.data(), sl.rs.data(), idx, st, &sl.batch);
         }
         if (rc == DUPIN_OK) {
-            cudaError_t e = cudaEventRecord(s->events[slot], st);
+            cudaError_t e = cudaEventRecord(sl.ev, st);
             if (e != cudaSuccess) rc = dupin_cuda_fail(e, "cudaEventRecord");
         }
         lk.lock();
@@ -164,7 +194,7 @@ static bool admit(dupin_server *s, std::unique_lock<std::mutex> &lk) {
 
 static void finish_slot(dupin_server *s, int i) {
     Slot &sl = s->slots[i];
-    cudaStream_t st = s->streams[i];
+    cudaStream_t st = sl.st;
     const bool launched_ok = sl.reqs.empty() || sl.reqs[0]->status == DUPIN_OK;
     if (sl.large) {
         Request *q = sl.reqs[0];
@@ -190,7 +220,7 @@ static void finish_slot(dupin_server *s, int i) {
     }
     s->last_done = t;
     s->used_bytes -= sl.bytes;
-    if (sl.large) s->exclusive = false;
+    if (sl.large) s->large_running = false;
     sl.busy = false;
     sl.reqs.clear();
     s->done_cv.notify_all();
@@ -214,7 +244,7 @@ static void serve_loop(dupin_server *s) {
             if (!busy) continue;
             const bool failed = !s->slots[i].reqs.empty() && s->slots[i].reqs[0]->status != DUPIN_OK;
             if (!failed) {
-                cudaError_t e = cudaEventQuery(s->events[i]);
+                cudaError_t e = cudaEventQuery(s->slots[i].ev);
                 if (e == cudaErrorNotReady) continue;
                 if (e != cudaSuccess) {
                     const int rc = dupin_cuda_fail(e, "request kernels");
@@ -246,6 +276,17 @@ extern "C" int dupin_serve_create(const dupin_serve_config *cfg, dupin_server **
     s->streams.resize(cfg->max_slots);
     s->events.resize(cfg->max_slots);
     s->slots.resize(cfg->max_slots);
+    {
+        int lo = 0, hi = 0;  // numerically lower is higher priority
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->large_stream, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->large_event, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (s->large_stream) cudaStreamDestroy(s->large_stream);
+            delete s;
+            return dupin_cuda_fail(e, "serving stream for large requests");
+        }
+    }
     for (int i = 0; i < cfg->max_slots; i++) {
         cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
@@ -254,6 +295,8 @@ extern "C" int dupin_serve_create(const dupin_serve_config *cfg, dupin_server **
                 cudaStreamDestroy(s->streams[j]);
                 cudaEventDestroy(s->events[j]);
             }
+            cudaStreamDestroy(s->large_stream);
+            cudaEventDestroy(s->large_event);
             delete s;
             return dupin_cuda_fail(e, "serving streams");
         }
@@ -361,6 +404,8 @@ extern "C" int dupin_serve_destroy(dupin_server *s) {
         cudaStreamDestroy(s->streams[i]);
         cudaEventDestroy(s->events[i]);
     }
+    cudaStreamDestroy(s->large_stream);
+    cudaEventDestroy(s->large_event);
     delete s;
     return DUPIN_OK;
 }

@@ -24,6 +24,8 @@ GPO = 1
 LPO = 2  # Algorithm 4 (implies GPO)
 RESULT_DEVICE = 8
 TIMING = 16
+TAIL_ONE_CTA = 32  # every tail on one CTA
+TAIL_CLUSTER = 64  # every tail on the thread-block cluster
 
 OK = 0
 ERR_INVALID_ARG, ERR_OVERFLOW, ERR_OOM, ERR_BUFFER_TOO_SMALL = -1, -2, -3, -4
@@ -55,7 +57,8 @@ class Result(ctypes.Structure):
                 ("trace_peeled", ctypes.c_void_p), ("trace_cap", ctypes.c_int64), ("n_rounds", ctypes.c_int64),
                 ("best_round", ctypes.c_int64), ("best_size", ctypes.c_int64), ("best_f_hi", ctypes.c_int64),
                 ("best_f_lo", ctypes.c_uint64), ("best_density", ctypes.c_double), ("n_min_rule", ctypes.c_int64),
-                ("n_bulk_rounds", ctypes.c_int64), ("tail_arcs", ctypes.c_int64), ("phase_ms", ctypes.c_float * 4)]
+                ("n_bulk_rounds", ctypes.c_int64), ("tail_arcs", ctypes.c_int64), ("phase_ms", ctypes.c_float * 4),
+                ("tail_ctas", ctypes.c_int64)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -242,6 +245,7 @@ class PeelOutput:
     n_bulk_rounds: int = 0
     phase_ms: Optional[list] = None
     tail_arcs: int = 0
+    tail_ctas: int = 0  # 1: the one-CTA tail ran, 8 or 16: the cluster tail, 0: none
 
     @property
     def trace_f(self) -> Optional[list]:
@@ -296,10 +300,11 @@ def _outputs(RA: np.ndarray, keep) -> list:
     fh, fl, dens = RA["best_f_hi"].tolist(), RA["best_f_lo"].tolist(), RA["best_density"].tolist()
     nmr, nb, ta, ph = RA["n_min_rule"].tolist(), RA["n_bulk_rounds"].tolist(), RA["tail_arcs"].tolist(), \
         RA["phase_ms"].tolist()
+    tc = RA["tail_ctas"].tolist()
     outs = []
     for j, (pr, mk, trace) in enumerate(keep):
         o = PeelOutput(nr[j], br[j], bs[j], (fh[j] << 64) + fl[j], dens[j], nmr[j], pr, mk, n_bulk_rounds=nb[j],
-                       phase_ms=ph[j], tail_arcs=ta[j])
+                       phase_ms=ph[j], tail_arcs=ta[j], tail_ctas=tc[j])
         if trace is not None and isinstance(trace[0], np.ndarray):
             R = nr[j] + 1
             o.trace_f_hi, o.trace_f_lo, o.trace_size, o.trace_peeled = (t[:R] for t in trace)
@@ -320,7 +325,8 @@ def _result_struct(peel_round=None, best_mask=None, trace=None, trace_cap=0) -> 
 def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
     out = PeelOutput(r.n_rounds, r.best_round, r.best_size, (int(r.best_f_hi) << 64) + int(r.best_f_lo),
                      r.best_density, r.n_min_rule, peel_round, best_mask, n_bulk_rounds=int(r.n_bulk_rounds),
-                     phase_ms=[float(x) for x in r.phase_ms], tail_arcs=int(r.tail_arcs))
+                     phase_ms=[float(x) for x in r.phase_ms], tail_arcs=int(r.tail_arcs),
+                     tail_ctas=int(r.tail_ctas))
     if trace is not None:
         R = r.n_rounds + 1
         fh, fl, sz, pe = trace

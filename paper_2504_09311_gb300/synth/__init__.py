@@ -120,9 +120,25 @@ class SynthGraph:
             return self.eu, (self.ev.astype(np.int64) + self.n_left).astype(np.int32)
         return self.eu, self.ev
 
+    def _sorted(self) -> "SynthGraph":
+        """This graph with its edge list in increasing (eu, ev) order (so every
+        CSR row comes out strictly increasing, as the loader requires); self
+        when it already is."""
+        eu, ev = np.asarray(self.eu), np.asarray(self.ev)
+        if eu.size < 2:
+            return self
+        key = (eu.astype(np.int64) << 32) | ev.astype(np.int64)
+        if np.all(key[1:] > key[:-1]):
+            return self
+        order = np.argsort(key, kind="stable")
+        return SynthGraph(self.n_left, self.n_right, eu[order].copy(), ev[order].copy(),
+                          None if self.c is None else np.asarray(self.c)[order].copy(), self.a, self.name)
+
     def bipartite_csr(self):
         """(csr_ptr, csr_idx, csr_w, csc_ptr, csc_idx, csc_w); weights None when c is None."""
         assert self.bipartite
+        if self._sorted() is not self:
+            return self._sorted().bipartite_csr()
         L = lib()
         nU, nI, m = self.n_left, self.n_right, self.m
         csr_ptr = np.empty(nU + 1, np.int64)
@@ -144,6 +160,8 @@ class SynthGraph:
             u, v = self.global_edges()
             g = SynthGraph(self.n, 0, u, v, self.c, self.a)
             return g.symmetric_csr()
+        if self._sorted() is not self:
+            return self._sorted().symmetric_csr()
         ptr = np.empty(self.n + 1, np.int64)
         idx = np.empty(2 * self.m, np.int32)
         w = np.empty(2 * self.m, np.int64) if self.c is not None else None

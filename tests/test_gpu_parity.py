@@ -115,6 +115,16 @@ def live_arcs_after(g, peel_round, r):
     return 2 * int(np.count_nonzero(np.minimum(peel_round[u], peel_round[v]) > r))
 
 
+def small_round(g, ref, r):
+    """Round r removed at most 64 vertices or expanded at most 2^18 arcs (the
+    removed vertices' degrees in the whole graph)."""
+    if ref.trace_peeled[r] <= 64:
+        return True
+    ptr, _, _ = g.symmetric_csr()
+    deg = np.diff(ptr)
+    return int(deg[np.asarray(ref.peel_round) == r].sum()) <= (1 << 18)
+
+
 @pytest.mark.parametrize("tail_arc_cap", [1, 700, 20000])
 def test_tail_waits_for_few_arcs(dupin, tail_arc_cap):
     """The tail starts once S fits it and either 2|E(S)| <= tail_arc_cap or the
@@ -134,14 +144,14 @@ def test_tail_waits_for_few_arcs(dupin, tail_arc_cap):
                 exact = live_arcs_after(g, ref.peel_round, nb)
                 assert out.tail_arcs == exact, ctx
                 # the tail starts once S fits and either its arcs are few or the
-                # last grid-wide round was small (<= 64 vertices) ...
+                # last grid-wide round was small (<= 64 vertices or <= 2^18 arcs) ...
                 if out.tail_arcs > 0:
                     assert ref.trace_size[nb] <= tail_cap, ctx
-                    assert out.tail_arcs <= tail_arc_cap or (nb > 0 and ref.trace_peeled[nb] <= 64), ctx
+                    assert out.tail_arcs <= tail_arc_cap or (nb > 0 and small_round(g, ref, nb)), ctx
                 # ... and not later
                 if nb > 0:
                     r = nb - 1
-                    small = r > 0 and ref.trace_peeled[r] <= 64
+                    small = r > 0 and small_round(g, ref, r)
                     assert ref.trace_size[r] > tail_cap or (live_arcs_after(g, ref.peel_round, r) > tail_arc_cap
                                                             and not small), ctx
 
@@ -253,6 +263,46 @@ def test_errors(dupin):
         dupin.peel(dgu, "dw", 1, (1, 10))
     dgu.free()
     dg.free()
+
+
+def test_loader_rejects_malformed_adjacency(dupin):
+    """dupin_graph_load: unsorted rows, a repeated pair, a missing or
+    re-weighted reverse arc, and a CSC that does not hold the CSR's edges are
+    INVALID_ARG; the well-formed versions load."""
+    sym = lambda n, rp, col, w=None: dupin.Graph.load_symmetric(n, np.array(rp, np.int64), np.array(col, np.int32),
+                                                                None if w is None else np.array(w, np.int64))
+    # path 0-1-2 loads
+    sym(3, [0, 1, 3, 4], [1, 0, 2, 1]).free()
+    cases = [
+        ("unsorted row", (3, [0, 1, 3, 4], [1, 2, 0, 1])),
+        ("repeated pair", (2, [0, 2, 4], [1, 1, 0, 0])),
+        ("missing reverse arc", (3, [0, 1, 2, 4], [1, 2, 0, 1])),
+        ("re-weighted reverse arc", (3, [0, 1, 3, 4], [1, 0, 2, 1], [Q, Q, 2 * Q, 3 * Q])),
+    ]
+    for name, args in cases:
+        with pytest.raises(dupin.DupinError) as e:
+            sym(*args)
+        assert e.value.code == dupin.ERR_INVALID_ARG, name
+    # bipartite: 2 users x 2 items, edges (0,0), (1,1)
+    cp, ci, cw = np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), np.array([Q, 2 * Q], np.int64)
+    dupin.Graph.load_bipartite(2, 2, cp, ci, cw, np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32),
+                               np.array([Q, 2 * Q], np.int64)).free()
+    bad_cscs = [("CSC names another user", np.array([1, 1], np.int32), np.array([Q, 2 * Q], np.int64)),
+                ("CSC weight differs", np.array([0, 1], np.int32), np.array([Q, 3 * Q], np.int64))]
+    for name, idx, w in bad_cscs:
+        with pytest.raises(dupin.DupinError) as e:
+            dupin.Graph.load_bipartite(2, 2, cp, ci, cw, np.array([0, 1, 2], np.int64), idx, w)
+        assert e.value.code == dupin.ERR_INVALID_ARG, name
+    # a large synthetic graph with one reverse arc re-weighted
+    g = synth.random_general(5000, 40000, seed=4)
+    synth.with_weights(g, "dw", seed=4)
+    ptr, idx, w = g.symmetric_csr()
+    dupin.Graph.load_symmetric(g.n, ptr, idx, w).free()
+    w2 = w.copy()
+    w2[len(w2) // 2] += Q
+    with pytest.raises(dupin.DupinError) as e:
+        dupin.Graph.load_symmetric(g.n, ptr, idx, w2)
+    assert e.value.code == dupin.ERR_INVALID_ARG
 
 
 def test_device_results(dupin):

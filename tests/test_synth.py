@@ -98,3 +98,38 @@ def test_layouts():
         for p in range(ptr[u], ptr[u + 1]):
             v = int(idx[p])
             assert (min(u, v), max(u, v)) in s
+
+
+def _rows_sorted_and_symmetric(ptr, idx, w):
+    n = len(ptr) - 1
+    row = np.repeat(np.arange(n, dtype=np.int64), np.diff(ptr))
+    # strictly increasing within each row
+    same_row = row[1:] == row[:-1]
+    assert np.all(idx[1:][same_row] > idx[:-1][same_row])
+    # the arc multiset equals its reverse, weights included
+    fwd = np.lexsort((idx, row))
+    rev = np.lexsort((row, idx.astype(np.int64)))
+    assert np.array_equal(row[fwd], idx[rev]) and np.array_equal(idx[fwd], row[rev])
+    if w is not None:
+        assert np.array_equal(w[fwd], w[rev])
+
+
+def test_csrs_meet_the_loader_preconditions():
+    """The loader rejects rows that are not strictly increasing and asymmetric
+    adjacencies; every CSR the generator hands it satisfies both."""
+    g = synth.rmat_weighted(12, 16, "dw", seed=2)
+    _rows_sorted_and_symmetric(*g.symmetric_csr())
+    b = synth.bipartite_zipf(3000, 1500, 30000, 1.8, 1, 50, 50, 0.3, 10, seed=5)
+    b.c = synth.fd_weights(b)
+    _rows_sorted_and_symmetric(*b.symmetric_csr())
+    cp, ci, cw, kp, ki, kw = b.bipartite_csr()
+    for ptr, idx in ((cp, ci), (kp, ki)):
+        r = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+        same = r[1:] == r[:-1]
+        assert np.all(idx[1:][same] > idx[:-1][same])
+    # CSR and CSC hold the same (user, item, weight) triples
+    u1 = np.repeat(np.arange(len(cp) - 1), np.diff(cp))
+    i2 = np.repeat(np.arange(len(kp) - 1), np.diff(kp))
+    a = sorted(zip(u1.tolist(), ci.tolist(), cw.tolist()))
+    bb = sorted(zip(ki.tolist(), i2.tolist(), kw.tolist()))
+    assert a == bb
