@@ -9,39 +9,47 @@
 // the live sub-graph's vertex state is spread over the cluster's shared
 // memory: local vertex p (0 <= p < L, the tail sub-graph's numbering) is
 // owned by CTA p mod C at slot p / C, which holds its peeling weight (>= 0
-// while live, -i once removed in round i) and its arc range.  A round:
+// while live, -i once removed in round i), its arc range and, per 64 slots,
+// the segment's exact minimum.  Every CTA also keeps its own copy of two
+// bitmaps over all local ids: the vertices removed through the previous round
+// and through the current one.  A round:
 //
-//   S  every CTA selects from its own slots (64-slot segments with an exact
-//      minimum each, double-buffered by round parity, so only segments that
-//      can hold a selected vertex are scanned), lists the selected slots and
-//      the prefix of their arc counts, and publishes its partial results;
+//   S  every CTA selects from its own slots (only segments whose minimum can
+//      pass the round's threshold are scanned), lists the selected slots with
+//      the prefix of their arc counts, prefetches their arcs into L2 (one bulk
+//      request per vertex), and pushes its count, arcs, weight sum and
+//      survivors' minimum into every CTA's inbox;
 //   -- cluster barrier --
-//   E  the round's arcs, concatenated over the CTAs' lists, are split evenly
-//      over the CTAs; each arc u -> v reads v's state in its owner's shared
-//      memory, subtracts c_uv with a returning 64-bit atomic add there when v
-//      survives (and marks v's segment dirty with a 32-bit atomic OR), or adds
-//      c_uv to the sum over arcs inside U_i when v left in this round;
+//   E  every CTA reads all CTAs' lists once: it extends its bitmap with U_i
+//      and, when the lists are short (the common case), builds the window of
+//      all listed vertices' arc ranges in the same pass; it walks an equal
+//      share of the round's arcs: an arc into an earlier round's removals is
+//      skipped, one into U_i adds c to the sum over arcs inside U_i, and one
+//      into a survivor subtracts c in its owner's shared memory with a
+//      returning 64-bit atomic add and lowers the owner's segment minimum by
+//      compare-and-swap; it pushes that sum and the smallest decremented
+//      weight into every CTA's inbox;
 //   -- cluster barrier --
-//   C  every CTA reads all partials and closes the round identically:
-//      f_i = f_{i-1} - (sum_{u in U_i} w_u - internal/2), |S_i|, the best prefix,
-//      the exact minimum live weight (survivors' minima before the round and
-//      every decrement's result), and plans round i+1.
+//   C  every CTA closes the round from its inbox, identically:
+//      f_i = f_{i-1} - (sum_{u in U_i} w_u - internal/2), |S_i|, the best
+//      prefix, the exact minimum live weight (survivors' minima before the
+//      round and every decrement's result) and the plan of round i+1.
 //
-// Before its next select every CTA recomputes the exact minimum of each of
-// its dirty segments.  (A 64-bit atomic minimum on another CTA's shared
-// memory was measured to lose updates when several SMs hit one word; 64-bit
-// adds and 32-bit ORs there stay atomic, so only those are used remotely.)
-//
-// Partials are double-buffered by round parity: round i+2 writes a buffer
-// only after the barrier that every CTA reaches after closing round i.
-// Every decision that ends the loop is taken from cluster-wide totals, so all
-// CTAs leave together; a last barrier keeps every CTA's shared memory alive
-// until no other CTA can read it.  All arithmetic is exact integer
-// arithmetic, identical to the one-CTA tail's.
+// A 64-bit atomic minimum on another CTA's shared memory was measured to lose
+// updates when several SMs hit one word, while 64-bit adds and
+// compare-and-swap there stay atomic: so the segment minima are lowered by a
+// compare-and-swap loop.  The selection inbox is double-buffered by round
+// parity; lists, prefixes and bitmaps are rewritten only after the barrier
+// that follows every CTA's last read of them.  Every decision that ends the
+// loop is taken from cluster-wide values, so all CTAs leave together; a last
+// barrier keeps every CTA's shared memory alive until no other CTA can read
+// it.  All arithmetic is exact integer arithmetic, identical to the one-CTA
+// tail's.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -50,10 +58,9 @@
 
 #define CL_THREADS 256
 #define CL_WARPS (CL_THREADS / 32)
-#define CL_SEG 64
-#define CL_WIN 512  // frontier entries per expand window
+#define CL_WIN 512  // list entries per expand window
 #define CL_ILP 4    // arcs in flight per thread in the expand
-#define CL_MAXSEG 1024  // segments per CTA (slots are 16-bit: at most 65,536 per CTA)
+#define CL_MAXC 16
 static const long long kPad = (long long)0x8000000000000000ULL;  // slots past the owned ones
 
 // ------------------------------------------------------------- cluster PTX
@@ -114,15 +121,6 @@ __device__ __forceinline__ unsigned long long cl_atom_add_u64(uint32_t a, unsign
     return v;
 }
 
-// an empty instruction that reads x: the thread waits for x's producer here
-__device__ __forceinline__ void consume(unsigned x) { asm volatile("" ::"r"(x)); }
-
-__device__ __forceinline__ unsigned cl_atom_or_b32(uint32_t a, unsigned x) {
-    unsigned v;
-    asm volatile("atom.shared::cluster.or.b32 %0, [%1], %2;" : "=r"(v) : "r"(a), "r"(x) : "memory");
-    return v;
-}
-
 // Largest k in [0, U] with le(k) true, for a predicate that is true on a
 // prefix of [0, U] and at k = 0.  One warp, 32 probes per step.
 template <class LeF>
@@ -153,39 +151,45 @@ __device__ __forceinline__ long long warp_search_last_le_fn(long long U, LeF le)
 
 // ------------------------------------------------------------ shared state
 
-// One CTA's partial results of a round (written by its thread 0).
-struct ClPart {
-    unsigned cnt;                    // vertices selected
-    unsigned arcs;                   // their arcs
-    unsigned long long wlo, whi;     // sum of their peeling weights
-    long long mins;                  // minimum over the CTA's survivors before the decrements
-    unsigned long long ilo, ihi;     // expand: sum of c over arcs inside U
-    long long mind;                  // expand: minimum weight after a decrement
+// One CTA's selection of a round, pushed into every CTA's inbox before the
+// first barrier (double-buffered by round parity).
+struct ClSel {
+    unsigned cnt;                 // vertices selected
+    unsigned arcs;                // their arcs
+    unsigned long long w_lo, w_hi;  // sum of their weights
+    long long mins;               // minimum over the CTA's survivors before the decrements
+};
+
+// One CTA's expand results, pushed into every CTA's inbox before the second barrier.
+struct ClRes {
+    unsigned long long i_lo, i_hi;  // sum of c over the arcs it expanded that end inside U_i
+    long long mind;                 // minimum weight after one of its decrements
 };
 
 struct ClShared {
-    ClPart part[2];                 // by round parity
-    unsigned F[2];                  // frontier counter, by round parity
-    long long initmin;              // the CTA's minimum live weight at the start
+    ClSel sel[2][CL_MAXC];  // [parity][CTA]
+    ClRes res[CL_MAXC];     // [CTA]
+    unsigned F[2];          // list counter, by round parity
+    long long initmin;
     long long red_mn[CL_WARPS];
     unsigned long long red_lo[CL_WARPS], red_hi[CL_WARPS];
     long long scan[CL_WARPS];
-    unsigned wbase[CL_WIN + 1];     // expand window: arc prefix of entries e0 ..
-    unsigned wstart[CL_WIN + 1];    // ... and their first arcs in the sub-graph
+    unsigned qcnt[CL_MAXC], qarc[CL_MAXC];  // the round: per CTA selected vertices and arcs ...
+    unsigned qcex[CL_MAXC], qaex[CL_MAXC];  // ... and their exclusive prefixes
+    unsigned wbase[CL_WIN + 1];             // expand window: arc prefix of its entries ...
+    unsigned wstart[CL_WIN + 1];            // ... and their first arcs in the sub-graph
     long long win_e0;
-    unsigned dirty[CL_MAXSEG / 32];  // segments whose vertices lost weight in the last expand
     int err;
 };
 
-// Dynamic shared memory per CTA for P slots (P a multiple of CL_SEG):
-// tw (8 B), arc start and degree (4 + 4 B), frontier slot (2 B), frontier
-// arc prefix (4 B) per slot, two segment minima per segment.
-__host__ __device__ __forceinline__ long long cl_smem_bytes(long long P) {
-    const long long nseg = P / CL_SEG;
-    return 8 * P + 4 * P + 4 * P + 16 * nseg + 4 * (P + 1) + 2 * P + 16;
+// Dynamic shared memory per CTA for P slots (P a multiple of 64) in a cluster
+// of C CTAs: tw (8 B), arc start and degree (4 + 4 B), the list entry (2 B),
+// its arc prefix (4 B) and first arc (4 B) per slot, one exact minimum per
+// 64-slot segment, and two bitmaps over all C P local ids.
+__host__ __device__ __forceinline__ long long cl_smem_bytes(long long P, long long C) {
+    const long long nw = (C * P + 31) / 32;
+    return 8 * P + 4 * P + 4 * P + 8 * (P / 64) + 4 * (P + 1) + 4 * P + 2 * P + 32 + 8 * nw;
 }
-
-// ------------------------------------------------------------------ kernel
 
 __device__ __forceinline__ long long block_min64(long long x, long long *s) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -198,30 +202,59 @@ __device__ __forceinline__ long long block_min64(long long x, long long *s) {
     return m;
 }
 
-__global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ ClShared S;
+__device__ __forceinline__ long long cl_cas_b64(uint32_t a, long long cmp, long long x) {
+    long long v;
+    asm volatile("atom.shared::cluster.cas.b64 %0, [%1], %2, %3;" : "=l"(v) : "r"(a), "l"(cmp), "l"(x) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void cl_st_u32(uint32_t a, unsigned x) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(x) : "memory");
+}
+
+__device__ __forceinline__ void cl_st_u64(uint32_t a, unsigned long long x) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(x) : "memory");
+}
+
+// L2 prefetch of bytes [off, off + len) of an array of 'total' bytes, in
+// 16-byte granules inside the array (one bulk request, no data returned)
+__device__ __forceinline__ void prefetch_l2(const void *base, unsigned long long total, unsigned long long off,
+                                            unsigned long long len) {
+    const unsigned long long a = off & ~15ull;
+    unsigned long long b = (off + len + 15) & ~15ull;
+    const unsigned long long end = total & ~15ull;
+    if (b > end) b = end;
+    if (b > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char *)base + a), "r"((unsigned)(b - a))
+                     : "memory");
+}
+
+// NARROW: f < 2^62 and the best f < 2^64 when the cluster starts, so every
+// sum a round forms fits 64 bits and the products are 64 x 64 -> 128-bit.
+template <bool NARROW>
+__device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, unsigned char *smem, ClShared &S) {
     PeelCtl *ctl = A.ctl;
-    if (ctl->status != ST_CLUSTER || ctl->error) return;  // identical in every CTA
     const unsigned C = cl_size(), r = cl_rank();
     const int lg = C == 16 ? 4 : (C == 8 ? 3 : (C == 4 ? 2 : (C == 2 ? 1 : 0)));
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long L = ctl->live_len;
     const int *live = ctl->live_sel ? A.live1 : A.live0;
     const long long nown = L > (long long)r ? (L - (long long)r + C - 1) / C : 0;
-    const int nseg = P / CL_SEG;                      // segment minima buffers hold nseg entries
-    const int nsl = (int)((nown + CL_SEG - 1) / CL_SEG);  // segments that hold this CTA's vertices
-    long long *tw = (long long *)smem;                           // [P]
-    unsigned *tst = (unsigned *)(smem + 8 * (size_t)P);          // [P] first arc
-    unsigned *tdg = tst + P;                                     // [P] arcs
-    long long *segbuf = (long long *)(tdg + P);                  // [2 nseg]
-    unsigned *fpre = (unsigned *)(segbuf + 2 * nseg);            // [P + 1]
-    unsigned short *fl = (unsigned short *)(fpre + P + 1);       // [P]
+    const int nsl = (int)((nown + 63) / 64);           // segments that hold this CTA's vertices
+    const long long NW = ((long long)C * P + 31) / 32;  // bitmap words
+    const int nwl = (int)((L + 31) / 32);               // ... that cover the live set
+    long long *tw = (long long *)smem;                         // [P]
+    unsigned *tst = (unsigned *)(smem + 8 * (size_t)P);        // [P] first arc
+    unsigned *tdg = tst + P;                                   // [P] arcs
+    long long *segmin = (long long *)(tdg + P);                // [P / 64]
+    unsigned *pre = (unsigned *)(segmin + P / 64);             // [P + 1] list arc prefix
+    unsigned *first = pre + P + 1;                             // [P] first arc of each list entry
+    unsigned short *lst = (unsigned short *)(first + P);       // [P] list of selected slots
+    unsigned *bm = (unsigned *)(((uintptr_t)(lst + P) + 15) & ~(uintptr_t)15);  // [2][NW]
     const bool dg = A.tcw == nullptr;
     const int *tcol = A.tcol;
     const long long *tcw = A.tcw;
 
-    // this CTA's slots: weights, arc ranges
     for (long long s = tid; s < P; s += CL_THREADS) {
         if (s < nown) {
             const long long p = s * C + r;
@@ -253,19 +286,20 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
         S.F[1] = 0;
         S.err = 0;
     }
-    for (int k = tid; k < CL_MAXSEG / 32; k += CL_THREADS) S.dirty[k] = 0;
+    {  // nothing of the live set is removed before the first round
+        unsigned *b0 = bm + (st.round & 1) * NW;
+        for (int k = tid; k < nwl; k += CL_THREADS) b0[k] = 0;
+    }
     __syncthreads();
-    // round i reads the minima in buffer (i & 1)
     {
-        long long *first = segbuf + ((st.round + 1) & 1) * nseg;
         long long mn = kMaxLL;
         for (int q = wid; q < nsl; q += CL_WARPS) {
-            const longlong2 v = *(const longlong2 *)&tw[(long long)q * CL_SEG + 2 * lane];
+            const longlong2 v = *(const longlong2 *)&tw[(long long)q * 64 + 2 * lane];
             long long m = kMaxLL;
             if (v.x >= 0) m = v.x;
             if (v.y >= 0 && v.y < m) m = v.y;
             m = warp_min64(m);
-            if (lane == 0) first[q] = m;
+            if (lane == 0) segmin[q] = m;
             mn = m < mn ? m : mn;
         }
         mn = block_min64(mn, S.red_mn);
@@ -275,7 +309,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
     long long m0 = kMaxLL;
     if (lane < (int)C) m0 = cl_ld_s64(cl_map(&S.initmin, lane));
     m0 = warp_min64(m0);
-    TailRound R = tail_plan<false>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, m0);
+    TailRound R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, m0);
     int err = 0;
     while (!R.done) {
         if (R.i > A.max_rounds) {
@@ -284,35 +318,22 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
         }
         const long long i = R.i;
         const int par = (int)(i & 1);
-        long long *cur = segbuf + par * nseg;
-        long long *nxt = segbuf + (par ^ 1) * nseg;
-        // ---- the exact minimum of every segment the last expand touched
-        for (int q = wid; q < nsl; q += CL_WARPS) {
-            if (!((S.dirty[q >> 5] >> (q & 31)) & 1u)) continue;  // warp-uniform
-            const longlong2 v = *(const longlong2 *)&tw[(long long)q * CL_SEG + 2 * lane];
-            long long m = kMaxLL;
-            if (v.x >= 0) m = v.x;
-            if (v.y >= 0 && v.y < m) m = v.y;
-            m = warp_min64(m);
-            if (lane == 0) cur[q] = m;
-        }
-        __syncthreads();
-        for (int k = tid; k < (nsl + 31) / 32; k += CL_THREADS) S.dirty[k] = 0;
-        // ---- S: select this CTA's slots
+        unsigned *bmc = bm + par * NW;              // removed through round i (built below)
+        const unsigned *bmp = bm + (par ^ 1) * NW;  // removed through round i-1
+        // ---- S: select this CTA's slots (segments that may hold selected vertices)
         unsigned long long wlo = 0, whi = 0;
         long long mins = kMaxLL;  // survivors' minimum over the segments this lane looked at
         for (int q0 = wid * 32; q0 < nsl; q0 += CL_THREADS) {
             const int q = q0 + lane;
-            const long long sm = q < nsl ? cur[q] : kMaxLL;
-            if (q < nsl) nxt[q] = sm;
+            const long long sm = q < nsl ? segmin[q] : kMaxLL;
             const bool cand = seg_candidate(sm, R);
             if (!cand) mins = sm < mins ? sm : mins;
             unsigned cm = __ballot_sync(0xffffffffu, cand);
-            __syncwarp();  // every lane's copy above lands before lane 0 overwrites a scanned segment's minimum
+            __syncwarp();
             while (cm) {
                 const int qq = q0 + __ffs(cm) - 1;
                 cm &= cm - 1;
-                const long long p = (long long)qq * CL_SEG + 2 * lane;
+                const long long p = (long long)qq * 64 + 2 * lane;
                 const longlong2 v = *(const longlong2 *)&tw[p];
                 bool s0, s1;
                 if (R.minrule) {
@@ -327,7 +348,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
                 if (v.y >= 0 && !s1 && v.y < m) m = v.y;
                 m = warp_min64(m);
                 if (lane == 0) {
-                    nxt[qq] = m;
+                    segmin[qq] = m;  // the survivors' minimum; the expand lowers it further
                     mins = m < mins ? m : mins;
                 }
                 const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
@@ -339,34 +360,21 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
                     unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
                     if (s0) {
                         tw[p] = -i;
-                        add128(wlo, whi, (unsigned long long)v.x, 0);
-                        fl[slot++] = (unsigned short)p;
+                        if (NARROW) wlo += (unsigned long long)v.x;
+                        else add128(wlo, whi, (unsigned long long)v.x, 0);
+                        lst[slot++] = (unsigned short)p;
                     }
                     if (s1) {
                         tw[p + 1] = -i;
-                        add128(wlo, whi, (unsigned long long)v.y, 0);
-                        fl[slot] = (unsigned short)(p + 1);
+                        if (NARROW) wlo += (unsigned long long)v.y;
+                        else add128(wlo, whi, (unsigned long long)v.y, 0);
+                        lst[slot] = (unsigned short)(p + 1);
                     }
                 }
             }
         }
-        __syncthreads();
-        const unsigned F = S.F[par];
-        if (tid == 0) S.F[par ^ 1] = 0;  // round i+1's counter (last read in round i-1)
-        // the frontier's arc prefix
-        {
-            unsigned carry = 0;
-            for (unsigned e0 = 0; e0 < F; e0 += CL_THREADS) {
-                const unsigned e = e0 + tid;
-                const long long d = e < F ? (long long)tdg[fl[e]] : 0;
-                long long tot;
-                const long long ex = block_excl_scan<CL_WARPS>(d, S.scan, tot);
-                if (e < F) fpre[e] = carry + (unsigned)ex;
-                carry += (unsigned)tot;
-            }
-            if (tid == 0) fpre[F] = carry;
-        }
-        warp_sum128(wlo, whi);
+        if (NARROW) wlo = warp_sum64_redux(wlo);
+        else warp_sum128(wlo, whi);
         mins = warp_min64(mins);
         if (lane == 0) {
             S.red_lo[wid] = wlo;
@@ -374,78 +382,171 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
             S.red_mn[wid] = mins;
         }
         __syncthreads();
-        if (wid == 0) {
+        const unsigned F = S.F[par];
+        if (tid == 0) S.F[par ^ 1] = 0;  // round i+1's counter (last read in round i-1)
+        // the list's arc prefix and first arcs; each listed vertex's arcs are
+        // prefetched into L2 now (the expand reads them after the barrier)
+        if (F <= 32) {
+            if (wid == 0) {
+                unsigned d = 0;
+                if (lane < (int)F) {
+                    const unsigned sl = lst[lane];
+                    d = tdg[sl];
+                    first[lane] = tst[sl];
+                    prefetch_l2(tcol, 4ull * A.tarc_cap, 4ull * tst[sl], 4ull * d);
+                    if (!dg) prefetch_l2(tcw, 8ull * A.tarc_cap, 8ull * tst[sl], 8ull * d);
+                }
+                unsigned incl = d;
+#pragma unroll
+                for (int k = 1; k < 32; k <<= 1) {
+                    const unsigned o = __shfl_up_sync(0xffffffffu, incl, k);
+                    if (lane >= k) incl += o;
+                }
+                if (lane < (int)F) pre[lane] = incl - d;
+                if (lane == 31) pre[F] = incl;
+            }
+        } else {
+            unsigned carry = 0;
+            for (unsigned e0 = 0; e0 < F; e0 += CL_THREADS) {
+                const unsigned e = e0 + tid;
+                unsigned d = 0;
+                if (e < F) {
+                    const unsigned sl = lst[e];
+                    d = tdg[sl];
+                    first[e] = tst[sl];
+                    prefetch_l2(tcol, 4ull * A.tarc_cap, 4ull * tst[sl], 4ull * d);
+                    if (!dg) prefetch_l2(tcw, 8ull * A.tarc_cap, 8ull * tst[sl], 8ull * d);
+                }
+                long long tot;
+                const long long ex = block_excl_scan<CL_WARPS>((long long)d, S.scan, tot);
+                if (e < F) pre[e] = carry + (unsigned)ex;
+                carry += (unsigned)tot;
+            }
+            if (tid == 0) pre[F] = carry;
+        }
+        if (wid == 0) {  // the CTA's totals, pushed into every CTA's inbox
             unsigned long long l = lane < CL_WARPS ? S.red_lo[lane] : 0, h = lane < CL_WARPS ? S.red_hi[lane] : 0;
             long long m = lane < CL_WARPS ? S.red_mn[lane] : kMaxLL;
             warp_sum128(l, h);
             m = warp_min64(m);
-            if (lane == 0) {
-                ClPart &pp = S.part[par];
-                pp.cnt = F;
-                pp.arcs = fpre[F];
-                pp.wlo = l;
-                pp.whi = h;
-                pp.mins = m;
+            l = __shfl_sync(0xffffffffu, l, 0);
+            h = __shfl_sync(0xffffffffu, h, 0);
+            m = __shfl_sync(0xffffffffu, m, 0);
+            __syncwarp();
+            const unsigned arcs = pre[F];
+            if (lane < (int)C) {
+                const uint32_t b = cl_map(&S.sel[par][r], lane);
+                cl_st_u32(b + offsetof(ClSel, cnt), F);
+                cl_st_u32(b + offsetof(ClSel, arcs), arcs);
+                cl_st_u64(b + offsetof(ClSel, w_lo), l);
+                cl_st_u64(b + offsetof(ClSel, w_hi), h);
+                cl_st_u64(b + offsetof(ClSel, mins), (unsigned long long)m);
             }
         }
-        cl_sync();  // A: every CTA's selection, list and partials are visible
-        // ---- E: expand the round's arcs, split evenly over the CTAs
+        cl_sync();  // A: every CTA's selection, list and prefix are visible
+        // ---- E: the removed set U_i and the round's arcs
+        if (wid == 0) {  // per CTA: selected vertices and arcs, and their prefixes
+            unsigned c = 0, a = 0;
+            if (lane < (int)C) {
+                c = S.sel[par][lane].cnt;
+                a = S.sel[par][lane].arcs;
+            }
+            unsigned ic = c, ia = a;
+#pragma unroll
+            for (int k = 1; k < 32; k <<= 1) {
+                const unsigned oc = __shfl_up_sync(0xffffffffu, ic, k), oa = __shfl_up_sync(0xffffffffu, ia, k);
+                if (lane >= k) {
+                    ic += oc;
+                    ia += oa;
+                }
+            }
+            if (lane < (int)C) {
+                S.qcnt[lane] = c;
+                S.qarc[lane] = a;
+                S.qcex[lane] = ic - c;
+                S.qaex[lane] = ia - a;
+            }
+        }
+        // removed through round i = removed through round i-1, plus U_i
+        for (int k = tid; k < nwl; k += CL_THREADS) bmc[k] = bmp[k];
+        __syncthreads();
+        const unsigned Ltot = S.qcex[C - 1] + S.qcnt[C - 1];
+        const unsigned Atot = S.qaex[C - 1] + S.qarc[C - 1];
+        // A short round (its lists fit one window): the window over all CTAs'
+        // lists is built here, in the same pass that extends the bitmap
+        const bool gwin = Ltot <= CL_WIN;
+        for (unsigned g = tid; g < Ltot; g += CL_THREADS) {
+            int q = 0;  // the last CTA whose entries start at or before g
+            for (int step = 8; step > 0; step >>= 1)
+                if (q + step < (int)C && S.qcex[q + step] <= g) q += step;
+            const unsigned e = g - S.qcex[q];
+            const unsigned sl = cl_ld_u16(cl_map(lst, q) + 2 * e);
+            if (gwin) {
+                S.wbase[g] = S.qaex[q] + cl_ld_u32(cl_map(pre, q) + 4 * e);
+                S.wstart[g] = cl_ld_u32(cl_map(first, q) + 4 * e);
+            }
+            const unsigned p = sl * C + q;
+            atomicOr(&bmc[p >> 5], 1u << (p & 31));
+        }
+        if (gwin)
+            for (unsigned t = Ltot + tid; t <= CL_WIN; t += CL_THREADS) S.wbase[t] = t == Ltot ? Atot : 0xffffffffu;
+        __syncthreads();
         unsigned long long ilo = 0, ihi = 0;
         long long mind = kMaxLL;
-        {
-            // per-CTA arc counts -> exclusive prefix (every warp holds it in lanes 0..C-1)
-            unsigned a = 0;
-            if (lane < (int)C) a = cl_ld_u32(cl_map(&S.part[par].arcs, lane));
-            unsigned incl = a;
+        // one arc: a survivor loses c in its owner's shared memory (returning
+        // 64-bit add; the owner's segment minimum lowered by compare-and-swap),
+        // an arc into U_i adds c to 'internal', an arc into an earlier round's
+        // removals is skipped (the bitmaps are local copies)
+        auto arcs = [&](const long long (&pos)[CL_ILP]) {
+            int cv[CL_ILP];
+            long long cc[CL_ILP];
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned o = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += o;
+            for (int u = 0; u < CL_ILP; u++) {
+                if (pos[u] >= 0) {
+                    cv[u] = tcol[pos[u]];
+                    cc[u] = dg ? DUPIN_Q_ONE : tcw[pos[u]];
+                }
             }
-            const unsigned Atot = __shfl_sync(0xffffffffu, incl, 31);
-            const unsigned excl = incl - a;
+            uint32_t sa[CL_ILP];
+            long long nv[CL_ILP], sm[CL_ILP];
+#pragma unroll
+            for (int u = 0; u < CL_ILP; u++) {
+                nv[u] = kMaxLL;
+                if (pos[u] < 0) continue;
+                const unsigned v = (unsigned)cv[u];
+                if (!((bmc[v >> 5] >> (v & 31)) & 1u)) {
+                    const unsigned o = v & (C - 1), sl = v >> lg;
+                    sa[u] = cl_map(&segmin[sl >> 6], o);
+                    sm[u] = cl_ld_s64(sa[u]);
+                    nv[u] = (long long)cl_atom_add_u64(cl_map(&tw[sl], o), (unsigned long long)(-cc[u])) - cc[u];
+                    mind = nv[u] < mind ? nv[u] : mind;
+                } else if (!((bmp[v >> 5] >> (v & 31)) & 1u)) {
+                    if (NARROW) ilo += (unsigned long long)cc[u];
+                    else add128(ilo, ihi, (unsigned long long)cc[u], 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CL_ILP; u++) {
+                if (nv[u] == kMaxLL) continue;
+                long long cur = sm[u];
+                while (nv[u] < cur) {
+                    const long long prev = cl_cas_b64(sa[u], cur, nv[u]);
+                    if (prev == cur) break;
+                    cur = prev;
+                }
+            }
+        };
+        {
             const unsigned E0 = (unsigned)split_at(Atot, r, C), E1 = (unsigned)split_at(Atot, r + 1, C);
-            unsigned x = E0;
-            while (x < E1) {  // block-uniform
-                // owner CTA q of global arc x and its local arc index
-                const unsigned m = __ballot_sync(0xffffffffu, lane < (int)C && excl <= x && a > 0 && x < excl + a);
-                if (m == 0) {  // cannot happen for x < Atot; leave the expand rather than map rank -1
-                    if (tid == 0) S.err = DUPIN_ERR_CUDA;
-                    break;
-                }
-                const int q = __ffs(m) - 1;
-                const unsigned qbase = __shfl_sync(0xffffffffu, excl, q), qcnt = __shfl_sync(0xffffffffu, a, q);
-                const unsigned lo = x - qbase;
-                const unsigned hi = (E1 - qbase < qcnt ? E1 - qbase : qcnt);
-                const unsigned Fq = cl_ld_u32(cl_map(&S.part[par].cnt, q));
-                const uint32_t rfpre = cl_map(fpre, q), rfl = cl_map(fl, q), rtst = cl_map(tst, q);
-                // the window's first entry: the last e with fpre_q[e] <= lo
-                // (fpre_q[0] = 0 <= lo < fpre_q[Fq]); warp 0, 32 probes a step
-                if (wid == 0) {
-                    const long long e = warp_search_last_le_fn(
-                        (long long)Fq - 1, [&](long long k) { return cl_ld_u32(rfpre + 4 * (uint32_t)k) <= lo; });
-                    if (lane == 0) S.win_e0 = e;
-                }
-                __syncthreads();
-                const long long e0 = S.win_e0;
-                for (int t = tid; t <= CL_WIN; t += CL_THREADS) {
-                    const long long e = e0 + t;
-                    unsigned b = 0xffffffffu, s0 = 0;
-                    if (e <= (long long)Fq) b = cl_ld_u32(rfpre + 4 * (uint32_t)e);
-                    if (e < (long long)Fq) s0 = cl_ld_u32(rtst + 4 * cl_ld_u16(rfl + 2 * (uint32_t)e));
-                    S.wbase[t] = e <= (long long)Fq ? b : 0xffffffffu;
-                    S.wstart[t] = s0;
-                }
-                __syncthreads();
-                const unsigned wend = S.wbase[CL_WIN] < hi ? S.wbase[CL_WIN] : hi;
-                for (unsigned xb = lo + tid; xb < wend; xb += CL_ILP * CL_THREADS) {
+            if (gwin) {
+                for (unsigned xb = E0 + tid; xb < E1; xb += CL_ILP * CL_THREADS) {
                     long long pos[CL_ILP];
 #pragma unroll
                     for (int u = 0; u < CL_ILP; u++) {
                         const unsigned xx = xb + u * CL_THREADS;
                         pos[u] = -1;
-                        if (xx < wend) {
-                            int lo2 = 0, hi2 = CL_WIN;  // last t with wbase[t] <= xx
+                        if (xx < E1) {
+                            int lo2 = 0, hi2 = (int)Ltot;  // last t with wbase[t] <= xx
                             while (lo2 < hi2) {
                                 const int mid = (lo2 + hi2 + 1) >> 1;
                                 if (S.wbase[mid] <= xx) lo2 = mid;
@@ -454,52 +555,63 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
                             pos[u] = (long long)S.wstart[lo2] + (xx - S.wbase[lo2]);
                         }
                     }
-                    int cv[CL_ILP];
-                    long long cc[CL_ILP];
-#pragma unroll
-                    for (int u = 0; u < CL_ILP; u++) {
-                        if (pos[u] >= 0) {
-                            cv[u] = tcol[pos[u]];
-                            cc[u] = dg ? DUPIN_Q_ONE : tcw[pos[u]];
-                        }
-                    }
-                    long long wv[CL_ILP];
-                    uint32_t wa[CL_ILP];
-#pragma unroll
-                    for (int u = 0; u < CL_ILP; u++) {
-                        if (pos[u] >= 0) {
-                            wa[u] = cl_map(&tw[cv[u] >> lg], (unsigned)cv[u] & (C - 1));
-                            wv[u] = cl_ld_s64(wa[u]);
-                        }
-                    }
-                    long long nv[CL_ILP];
-#pragma unroll
-                    for (int u = 0; u < CL_ILP; u++) {
-                        nv[u] = kMaxLL;
-                        if (pos[u] < 0) continue;
-                        if (wv[u] >= 0) {
-                            nv[u] = (long long)cl_atom_add_u64(wa[u], (unsigned long long)(-cc[u])) - cc[u];
-                            mind = nv[u] < mind ? nv[u] : mind;
-                        } else if (wv[u] == -i) {
-                            add128(ilo, ihi, (unsigned long long)cc[u], 0);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < CL_ILP; u++) {
-                        if (nv[u] != kMaxLL) {
-                            const int sg = (cv[u] >> lg) / CL_SEG;
-                            // the returned word is consumed, so the OR has been
-                            // performed at its target before this thread reaches
-                            // the next cluster barrier
-                            consume(cl_atom_or_b32(cl_map(&S.dirty[sg >> 5], (unsigned)cv[u] & (C - 1)), 1u << (sg & 31)));
-                        }
-                    }
+                    arcs(pos);
                 }
-                x = qbase + wend;
-                __syncthreads();  // the window is reused
+            } else {
+                unsigned x = E0;
+                int q = 0;
+                while (x < E1) {  // block-uniform: a window of one CTA's list at a time
+                    while (q + 1 < (int)C && (S.qaex[q + 1] <= x || S.qarc[q] == 0)) q++;
+                    if (!(S.qaex[q] <= x && x < S.qaex[q] + S.qarc[q])) {  // cannot happen for x < Atot
+                        if (tid == 0) S.err = DUPIN_ERR_CUDA;
+                        break;
+                    }
+                    const unsigned qbase = S.qaex[q], qcnt = S.qarc[q], Fq = S.qcnt[q];
+                    const unsigned lo = x - qbase;
+                    const unsigned hi = (E1 - qbase < qcnt ? E1 - qbase : qcnt);
+                    const uint32_t rpre = cl_map(pre, q), rfirst = cl_map(first, q);
+                    if (wid == 0) {  // the window's first entry: the last e with pre_q[e] <= lo
+                        const long long e = warp_search_last_le_fn(
+                            (long long)Fq - 1, [&](long long k) { return cl_ld_u32(rpre + 4 * (uint32_t)k) <= lo; });
+                        if (lane == 0) S.win_e0 = e;
+                    }
+                    __syncthreads();
+                    const long long e0 = S.win_e0;
+                    for (int t = tid; t <= CL_WIN; t += CL_THREADS) {
+                        const long long e = e0 + t;
+                        unsigned b = 0xffffffffu, s0 = 0;
+                        if (e <= (long long)Fq) b = cl_ld_u32(rpre + 4 * (uint32_t)e);
+                        if (e < (long long)Fq) s0 = cl_ld_u32(rfirst + 4 * (uint32_t)e);
+                        S.wbase[t] = b;
+                        S.wstart[t] = s0;
+                    }
+                    __syncthreads();
+                    const unsigned wend = S.wbase[CL_WIN] < hi ? S.wbase[CL_WIN] : hi;
+                    for (unsigned xb = lo + tid; xb < wend; xb += CL_ILP * CL_THREADS) {
+                        long long pos[CL_ILP];
+#pragma unroll
+                        for (int u = 0; u < CL_ILP; u++) {
+                            const unsigned xx = xb + u * CL_THREADS;
+                            pos[u] = -1;
+                            if (xx < wend) {
+                                int lo2 = 0, hi2 = CL_WIN;  // last t with wbase[t] <= xx
+                                while (lo2 < hi2) {
+                                    const int mid = (lo2 + hi2 + 1) >> 1;
+                                    if (S.wbase[mid] <= xx) lo2 = mid;
+                                    else hi2 = mid - 1;
+                                }
+                                pos[u] = (long long)S.wstart[lo2] + (xx - S.wbase[lo2]);
+                            }
+                        }
+                        arcs(pos);
+                    }
+                    x = qbase + wend;
+                    __syncthreads();  // the window is reused
+                }
             }
         }
-        warp_sum128(ilo, ihi);
+        if (NARROW) ilo = warp_sum64_redux(ilo);
+        else warp_sum128(ilo, ihi);
         mind = warp_min64(mind);
         if (lane == 0) {
             S.red_lo[wid] = ilo;
@@ -507,39 +619,50 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
             S.red_mn[wid] = mind;
         }
         __syncthreads();
-        if (wid == 0) {
+        if (wid == 0) {  // this CTA's results, pushed into every CTA's inbox
             unsigned long long l = lane < CL_WARPS ? S.red_lo[lane] : 0, h = lane < CL_WARPS ? S.red_hi[lane] : 0;
             long long m = lane < CL_WARPS ? S.red_mn[lane] : kMaxLL;
             warp_sum128(l, h);
             m = warp_min64(m);
-            if (lane == 0) {
-                S.part[par].ilo = l;
-                S.part[par].ihi = h;
-                S.part[par].mind = m;
+            l = __shfl_sync(0xffffffffu, l, 0);
+            h = __shfl_sync(0xffffffffu, h, 0);
+            m = __shfl_sync(0xffffffffu, m, 0);
+            if (lane < (int)C) {
+                const uint32_t b = cl_map(&S.res[r], lane);
+                cl_st_u64(b + offsetof(ClRes, i_lo), l);
+                cl_st_u64(b + offsetof(ClRes, i_hi), h);
+                cl_st_u64(b + offsetof(ClRes, mind), (unsigned long long)m);
             }
         }
-        cl_sync();  // B: every decrement and partial of round i is visible
-        // ---- C: close round i and plan round i+1 (every warp, same values)
+        cl_sync();  // B: every decrement and every CTA's results of round i are visible
+        // ---- C: close round i and plan round i+1 (every warp, same values, local reads)
         unsigned long long Wl = 0, Wh = 0, Il = 0, Ih = 0;
-        long long Un = 0, Mn = kMaxLL;
+        unsigned Uq = 0;
+        long long Mn = kMaxLL;
         if (lane < (int)C) {
-            const uint32_t pa = cl_map(&S.part[par], lane);
-            Un = cl_ld_u32(pa + offsetof(ClPart, cnt));
-            Wl = cl_ld_u64(pa + offsetof(ClPart, wlo));
-            Wh = cl_ld_u64(pa + offsetof(ClPart, whi));
-            Il = cl_ld_u64(pa + offsetof(ClPart, ilo));
-            Ih = cl_ld_u64(pa + offsetof(ClPart, ihi));
-            const long long m1 = cl_ld_s64(pa + offsetof(ClPart, mins)), m2 = cl_ld_s64(pa + offsetof(ClPart, mind));
-            Mn = m1 < m2 ? m1 : m2;
+            const ClSel &x = S.sel[par][lane];
+            const ClRes &y = S.res[lane];
+            Uq = x.cnt;
+            Wl = x.w_lo;
+            Wh = x.w_hi;
+            Il = y.i_lo;
+            Ih = y.i_hi;
+            Mn = x.mins < y.mind ? x.mins : y.mind;
         }
-        Un = warp_sum64(Un);
-        Un = __shfl_sync(0xffffffffu, Un, 0);
-        warp_sum128(Wl, Wh);
-        warp_sum128(Il, Ih);
-        Wl = __shfl_sync(0xffffffffu, Wl, 0);
-        Wh = __shfl_sync(0xffffffffu, Wh, 0);
-        Il = __shfl_sync(0xffffffffu, Il, 0);
-        Ih = __shfl_sync(0xffffffffu, Ih, 0);
+        const long long Un = (long long)__reduce_add_sync(0xffffffffu, Uq);
+        if (NARROW) {
+            Wl = warp_sum64_redux(Wl);
+            Il = warp_sum64_redux(Il);
+            Wh = 0;
+            Ih = 0;
+        } else {
+            warp_sum128(Wl, Wh);
+            warp_sum128(Il, Ih);
+            Wl = __shfl_sync(0xffffffffu, Wl, 0);
+            Wh = __shfl_sync(0xffffffffu, Wh, 0);
+            Il = __shfl_sync(0xffffffffu, Il, 0);
+            Ih = __shfl_sync(0xffffffffu, Ih, 0);
+        }
         Mn = warp_min64(Mn);
         const u128 wsel = mk128(Wl, Wh), internal = mk128(Il, Ih);
         st.f = st.f - (wsel - (internal >> 1));
@@ -547,7 +670,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
         st.size -= Un;
         st.round = i;
         st.n_min_rule += R.minrule ? 1 : 0;
-        if (st.size > 0 && frac_gt(st.f, st.size, st.bf, st.best_size)) {
+        if (st.size > 0 && frac_gt<NARROW>(st.f, st.size, st.bf, st.best_size)) {
             st.bf = st.f;
             st.best_size = st.size;
             st.best_round = i;
@@ -562,7 +685,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
-        R = tail_plan<false>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, Mn);
+        R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, Mn);
     }
     if (tid == 0 && S.err) set_error(ctl, S.err);
     // peel rounds of this CTA's vertices
@@ -590,6 +713,15 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int 
     if (r == 0 && tid == 0 && !err) ctl->status = ST_DONE;
 }
 
+__global__ void __launch_bounds__(CL_THREADS, 1) k_peel_cluster(PeelArgs A, int P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ClShared S;
+    const PeelCtl *ctl = A.ctl;
+    if (ctl->status != ST_CLUSTER || ctl->error) return;  // identical in every CTA
+    if (ctl->f_hi == 0 && ctl->f_lo < (1ull << 62) && ctl->bf_hi == 0) cluster_body<true>(A, P, smem, S);
+    else cluster_body<false>(A, P, smem, S);
+}
+
 // ------------------------------------------------------------------- host
 
 namespace {
@@ -604,8 +736,14 @@ ClConfig g_cl[64];
 
 // The cluster shape for the current device, set up once per device: 16 CTAs
 // where a cluster that large can be resident, else 8; P slots per CTA as the
-// shared memory allows (a multiple of 64, at most 65,536 so that a slot fits
-// 16 bits).
+// shared memory allows (a multiple of 64, at most 65,536).
+static long long slots_for(int C, int dyn) {
+    long long P = (long long)dyn / (26 + C / 4);
+    P = (P / 64) * 64;
+    while (P > 0 && cl_smem_bytes(P, C) > dyn) P -= 64;
+    return P > 65536 ? 65536 : P;  // a list entry keeps the slot in 16 bits
+}
+
 static int cluster_config(ClConfig *out) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -622,22 +760,22 @@ static int cluster_config(ClConfig *out) {
             return c.rc;
         }
         const int dyn = smem - (int)fa.sharedSizeBytes;
-        long long P = (dyn - 16) / 22;
-        P = (P / CL_SEG) * CL_SEG;
-        while (P > 0 && cl_smem_bytes(P) > dyn) P -= CL_SEG;
-        if (P > 65536) P = 65536;
-        e = cudaFuncSetAttribute(k_peel_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem_bytes(P));
+        const long long P16 = slots_for(16, dyn), P8 = slots_for(8, dyn);
+        const long long most = std::max(cl_smem_bytes(P16, 16), cl_smem_bytes(P8, 8));
+        e = cudaFuncSetAttribute(k_peel_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_peel_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess || P <= 0) {
+        if (e != cudaSuccess || P8 <= 0) {
             c.rc = dupin_cuda_fail(e, "cudaFuncSetAttribute(k_peel_cluster)");
             return c.rc;
         }
         int best = 0;
+        long long bestP = 0;
         for (int C : {16, 8}) {
+            const long long P = C == 16 ? P16 : P8;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);
             cfg.blockDim = dim3(CL_THREADS);
-            cfg.dynamicSmemBytes = (size_t)cl_smem_bytes(P);
+            cfg.dynamicSmemBytes = (size_t)cl_smem_bytes(P, C);
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeClusterDimension;
             at[0].val.clusterDim.x = C;
@@ -646,8 +784,9 @@ static int cluster_config(ClConfig *out) {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int nc = 0;
-            if (cudaOccupancyMaxActiveClusters(&nc, (void *)k_peel_cluster, &cfg) == cudaSuccess && nc > 0) {
+            if (P > 0 && cudaOccupancyMaxActiveClusters(&nc, (void *)k_peel_cluster, &cfg) == cudaSuccess && nc > 0) {
                 best = C;
+                bestP = P;
                 break;
             }
             cudaGetLastError();
@@ -657,7 +796,7 @@ static int cluster_config(ClConfig *out) {
             return c.rc;
         }
         c.C = best;
-        c.P = (int)P;
+        c.P = (int)bestP;
     }
     if (c.rc) return c.rc;
     *out = c;
@@ -683,7 +822,7 @@ int launch_cluster_tail(const PeelArgs &A, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.C);
     cfg.blockDim = dim3(CL_THREADS);
-    cfg.dynamicSmemBytes = (size_t)cl_smem_bytes(c.P);
+    cfg.dynamicSmemBytes = (size_t)cl_smem_bytes(c.P, c.C);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
