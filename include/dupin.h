@@ -66,6 +66,8 @@ extern "C" {
 #define DUPIN_DG 0
 #define DUPIN_DW 1
 #define DUPIN_FD 2
+#define DUPIN_TDS 3 /* triangle density (Sec. 2.1): f(S) = triangles of G[S], w_u = those through u;
+                       plain counts, not Q32.32 (the paper's k for TDS is 3); dupin_peel only */
 
 /* --------------------------------------------------------- graph loading */
 
@@ -147,7 +149,7 @@ int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs
 #define DUPIN_TAIL_CLUSTER 64u /* every tail runs in the cluster kernel (never one CTA) */
 
 typedef struct {
-    int32_t metric;     /* DUPIN_DG, DUPIN_DW or DUPIN_FD */
+    int32_t metric;     /* DUPIN_DG, DUPIN_DW, DUPIN_FD or DUPIN_TDS */
     int32_t k_mult;     /* k of Algorithm 2, 1..64 (2 is the paper's value for DG/DW/FD) */
     int64_t eps_num;    /* eps = eps_num / eps_den, eps_num >= 0 */
     int64_t eps_den;    /* 1 .. 2^24 */
@@ -214,6 +216,13 @@ typedef struct {
  * when the result is complete.  Errors: INVALID_ARG (params), NO_PROGRESS
  * (max_rounds), BUFFER_TOO_SMALL (trace_cap < n_rounds + 1 with a non-NULL
  * trace; everything else is still filled), OOM, TIMEOUT, CUDA.
+ *
+ * With metric DUPIN_TDS, f and the weights are triangle counts (not Q32.32):
+ * the trace's f words and best_f hold counts, best_density is f / |S|, the
+ * graph's weights are ignored, and each round runs as a few short launches
+ * (the graph's triangles are listed once at the start, and every round
+ * lists only the triangles through its removed vertices).  f must stay
+ * below 2^63.  The tail fields of the result are 0.
  */
 int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result, void *stream);
 

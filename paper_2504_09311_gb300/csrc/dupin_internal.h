@@ -134,6 +134,9 @@ long long cluster_cap_limit();
 int cluster_ctas();
 int launch_cluster_tail(const PeelArgs &A, cudaStream_t s);
 
+// dupin_peel under the triangle-density metric (tds.cu)
+int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_t s);
+
 // the largest live set the single-CTA tail accepts, and the default caps
 long long tail_cap_limit();
 long long tail_cap_default();

@@ -1360,7 +1360,7 @@ static long long tail_smem_bytes(long long cap) {
 
 static int check_params(const dupin_graph *g, const dupin_params *p) {
     if (!p) return dupin_fail(DUPIN_ERR_INVALID_ARG, "params is NULL");
-    if (p->metric < DUPIN_DG || p->metric > DUPIN_FD) return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown metric");
+    if (p->metric < DUPIN_DG || p->metric > DUPIN_TDS) return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown metric");
     if (p->k_mult < 1 || p->k_mult > 64) return dupin_fail(DUPIN_ERR_INVALID_ARG, "k_mult must be in 1..64");
     if (p->eps_den < 1 || p->eps_den > (1LL << 24) || p->eps_num < 0 || p->eps_num > (1LL << 30))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "eps must be eps_num/eps_den with 0 <= eps_num <= 2^30, 1 <= eps_den <= 2^24");
@@ -1369,7 +1369,7 @@ static int check_params(const dupin_graph *g, const dupin_params *p) {
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown flag");
     if ((p->flags & DUPIN_TAIL_ONE_CTA) && (p->flags & DUPIN_TAIL_CLUSTER))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TAIL_ONE_CTA and DUPIN_TAIL_CLUSTER exclude each other");
-    if (p->metric != DUPIN_DG && g->cw == nullptr)
+    if (p->metric != DUPIN_DG && p->metric != DUPIN_TDS && g->cw == nullptr)
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "DW/FD need edge weights; the graph was loaded without them");
     return DUPIN_OK;
 }
@@ -1827,6 +1827,7 @@ extern "C" int dupin_peel(dupin_graph *g, const dupin_params *p, dupin_result *r
     if (rc) return rc;
     DUPIN_CUDA_TRY(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->metric == DUPIN_TDS) return tds_peel(g, p, r, s);
     rc = workspace_ensure(g, plan);
     if (rc) return rc;
     rc = enqueue_peel(g, g->ws, p, plan, s);

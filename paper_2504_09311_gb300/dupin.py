@@ -17,8 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdupin.so")
 
-DG, DW, FD = 0, 1, 2
-METRICS = {"dg": DG, "dw": DW, "fd": FD}
+DG, DW, FD, TDS = 0, 1, 2, 3
+METRICS = {"dg": DG, "dw": DW, "fd": FD, "tds": TDS}
 DEVICE_PTRS = 1
 GPO = 1
 LPO = 2  # Algorithm 4 (implies GPO)

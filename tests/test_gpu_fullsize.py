@@ -1,15 +1,20 @@
 """Full-size workloads on the GPU, checked against the oracle.
 
-* FD transaction graph, 2M users x 1M items, 40.7M edges (the benchmark
-  workload): bit-exact against the oracle's full replay of Algorithm 2 for
-  eps = 1/20, and through the oracle's verifier for eps = 0 and 1/5.
+* R-MAT scale 24 (16.8M vertices, 260M edges, c in 1..100): the benchmark
+  graph.  DG, FD and DW (a in 0..10) each at k = 1 and k = 2, eps = 1/10,
+  bit-exact against the oracle's full replay of Algorithm 2: every vertex's
+  peel round, the whole density trace, the per-round sizes, the minimum-rule
+  count and the best prefix.  k = 1 peels run 3k to 13k rounds, nearly all of
+  them through the cluster tail.
+* FD transaction graph, 2M users x 1M items, 40.7M edges: bit-exact against
+  the full replay for eps = 1/20, and through the oracle's verifier for
+  eps = 0 and 1/5.
 * R-MAT scale 18 (DW): bit-exact against the full replay, k = 1 and k = 2.
-* R-MAT scale 22 and scale 24 (DW, c in 1..100, a in 0..10; 64M and ~260M
-  edges): the replay would take too long single-threaded, so the verifier
-  checks every vertex's round against the definitions (its peeling weight at
-  the start of its round is at most the threshold recomputed from the trace,
-  or equals the minimum), recomputes the whole density trace from the peel
-  rounds, checks the best round, and checks every survivor at sampled rounds.
+* R-MAT scale 22 (DW): the verifier checks every vertex's round against the
+  definitions (its peeling weight at the start of its round is at most the
+  threshold recomputed from the trace, or equals the minimum), recomputes the
+  whole density trace from the peel rounds, checks the best round, and checks
+  every survivor at sampled rounds.
 """
 import numpy as np
 import pytest
@@ -69,14 +74,42 @@ def test_rmat18_exact(dupin):
     og.close()
 
 
-@pytest.mark.parametrize("scale", [22, 24])
-def test_rmat_large_verified(dupin, scale):
-    g = synth.rmat_weighted(scale, 16, "dw", seed=1)
+def test_rmat22_verified(dupin):
+    g = synth.rmat_weighted(22, 16, "dw", seed=1)
     dg = dupin.Graph.from_synth(g)
     og = oracle.Graph.from_synth(g, "dw")
-    for k in ((1, 2) if scale == 22 else (1,)):
+    for k in (1, 2):
         out = dupin.peel(dg, "dw", k, (1, 10))
-        assert verify(og, out, k, (1, 10), nsample=2 if scale == 24 else 3) == (0, "")
+        assert verify(og, out, k, (1, 10)) == (0, "")
         assert out.trace_size[-1] == 0 and out.trace_f[-1] == 0
+    dg.free()
+    og.close()
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    return synth.rmat_weighted(24, 16, "fd", seed=1)
+
+
+@pytest.mark.parametrize("metric", ["dg", "fd", "dw"])
+def test_rmat24_exact(dupin, rmat24, metric):
+    g = rmat24
+    if metric == "dw":  # same topology, DW weights
+        g = synth.SynthGraph(rmat24.n_left, rmat24.n_right, rmat24.eu, rmat24.ev)
+        synth.with_weights(g, "dw", 1, a_range=(0, 10), c_range=(1, 100))
+    dg = dupin.Graph.from_synth(g)
+    og = oracle.Graph.from_synth(g, metric)
+    for k in (1, 2):
+        out = dupin.peel(dg, metric, k, (1, 10), want_mask=False)
+        ref = oracle.peel_batch(og, k, (1, 10))
+        assert ref.violations == 0
+        assert out.n_rounds == ref.n_rounds, (metric, k)
+        assert np.array_equal(out.peel_round, ref.peel_round), (metric, k)
+        assert out.trace_f == ref.trace_f, (metric, k)
+        assert np.array_equal(out.trace_size, ref.trace_size) and np.array_equal(out.trace_peeled, ref.trace_peeled)
+        assert (out.best_round, out.best_size, out.best_f) == (ref.best_round, ref.best_size, ref.best_f)
+        assert out.n_min_rule == ref.n_min_rule
+        if k == 1:
+            assert out.tail_ctas > 1  # the rounds after the bulk phase ran in the cluster tail
     dg.free()
     og.close()
