@@ -10,41 +10,45 @@
 // memory: local vertex p (0 <= p < L, the tail sub-graph's numbering) is
 // owned by CTA p mod C at slot p / C, which holds its peeling weight (>= 0
 // while live, -i once removed in round i), its arc range and, per 64 slots,
-// the segment's exact minimum.  Every CTA also keeps its own copy of two
-// bitmaps over all local ids: the vertices removed through the previous round
-// and through the current one.  A round:
+// the segment's exact minimum.  The tail sub-graph's rows are stored with
+// each row's arcs grouped by the owner of their head, with every group's
+// bounds, so that each CTA reads exactly the arcs into its own vertices and
+// every update of a vertex's state is made by its owner.  A round i:
 //
-//   S  every CTA selects from its own slots (only segments whose minimum can
-//      pass the round's threshold are scanned), lists the selected slots with
-//      the prefix of their arc counts, prefetches their arcs into L2 (one bulk
-//      request per vertex), and pushes its count, arcs, weight sum and
-//      survivors' minimum into every CTA's inbox;
-//   -- cluster barrier --
-//   E  every CTA reads all CTAs' lists once: it extends its bitmap with U_i
-//      and, when the lists are short (the common case), builds the window of
-//      all listed vertices' arc ranges in the same pass; it walks an equal
-//      share of the round's arcs: an arc into an earlier round's removals is
-//      skipped, one into U_i adds c to the sum over arcs inside U_i, and one
-//      into a survivor subtracts c in its owner's shared memory with a
-//      returning 64-bit atomic add and lowers the owner's segment minimum by
-//      compare-and-swap; it pushes that sum and the smallest decremented
-//      weight into every CTA's inbox;
-//   -- cluster barrier --
+//   S  the removed set U_i.  When round i takes the minimum rule (the common
+//      case of a skewed graph at k(1+eps) < 2), U_i is every live vertex at
+//      the minimum weight, and every CTA already holds it: each CTA listed its
+//      own vertices at its own minimum with its results of round i-1.  The
+//      CTAs at the cluster's minimum mark theirs; nothing is exchanged.
+//      Otherwise every CTA selects from its own slots (only segments whose
+//      minimum can pass the round's threshold are scanned), lists them,
+//      prefetches their arcs and group bounds into L2, and pushes its count
+//      and weight sum -- and a short list itself -- into every CTA's inbox,
+//      followed by a cluster barrier.
+//   E  every CTA walks the round's list and, for each removed vertex u, the
+//      group of u's arcs whose heads it owns: an arc into an earlier round's
+//      removal is skipped, one into U_i adds c to the sum over arcs inside
+//      U_i, and one into a survivor subtracts c with a shared-memory atomic
+//      and lowers the segment minimum -- all local.
+//   P  every CTA finds its minimum live weight and its live vertices at that
+//      weight (prefetching their arcs into L2), and pushes them with its
+//      internal sum into every CTA's inbox by asynchronous shared-memory
+//      stores that complete on the receiver's mbarrier.
+//   -- every CTA waits on its own mbarrier: all C pushes have arrived --
 //   C  every CTA closes the round from its inbox, identically:
 //      f_i = f_{i-1} - (sum_{u in U_i} w_u - internal/2), |S_i|, the best
-//      prefix, the exact minimum live weight (survivors' minima before the
-//      round and every decrement's result) and the plan of round i+1.
+//      prefix, the cluster's minimum live weight and the plan of round i+1.
 //
-// A 64-bit atomic minimum on another CTA's shared memory was measured to lose
-// updates when several SMs hit one word, while 64-bit adds and
-// compare-and-swap there stay atomic: so the segment minima are lowered by a
-// compare-and-swap loop.  The selection inbox is double-buffered by round
-// parity; lists, prefixes and bitmaps are rewritten only after the barrier
-// that follows every CTA's last read of them.  Every decision that ends the
-// loop is taken from cluster-wide values, so all CTAs leave together; a last
-// barrier keeps every CTA's shared memory alive until no other CTA can read
-// it.  All arithmetic is exact integer arithmetic, identical to the one-CTA
-// tail's.
+// So a minimum-rule round has no cluster barrier at all: each CTA waits only
+// for the data it needs.  The only traffic between CTAs is the inboxes (and
+// the list of a CTA that selected more than a short list holds, read
+// remotely).  No CTA can get more than one round ahead of another (it needs
+// everyone's results of a round to start the next), so inboxes
+// double-buffered by round parity are never overwritten before they are
+// read.  Every decision that ends the loop is taken from cluster-wide
+// values, so all CTAs leave together; a last barrier keeps every CTA's
+// shared memory alive until no other CTA can read it.  All arithmetic is
+// exact integer arithmetic, identical to the one-CTA tail's.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -59,6 +63,9 @@
 #define CL_THREADS 256
 #define CL_WARPS (CL_THREADS / 32)
 #define CL_WIN 512  // list entries per expand window
+#define CL_INL 32   // a list this short travels in the inboxes
+#define CL_SPEC 32  // a CTA lists its vertices at its minimum weight up to this many ...
+#define CL_PUSH 8   // ... and pushes them into the inboxes up to this many
 #define CL_ILP 4    // arcs in flight per thread in the expand
 #define CL_MAXC 16
 static const long long kPad = (long long)0x8000000000000000ULL;  // slots past the owned ones
@@ -151,44 +158,50 @@ __device__ __forceinline__ long long warp_search_last_le_fn(long long U, LeF le)
 
 // ------------------------------------------------------------ shared state
 
-// One CTA's selection of a round, pushed into every CTA's inbox before the
-// first barrier (double-buffered by round parity).
+// One CTA's selection of a round that is not taken by the minimum rule from
+// the listed minima, pushed into every CTA's inbox before the first barrier
+// (double-buffered by round parity).
 struct ClSel {
-    unsigned cnt;                 // vertices selected
-    unsigned arcs;                // their arcs
+    unsigned cnt;                   // vertices selected
+    unsigned pad;
     unsigned long long w_lo, w_hi;  // sum of their weights
-    long long mins;               // minimum over the CTA's survivors before the decrements
 };
 
-// One CTA's expand results, pushed into every CTA's inbox before the second barrier.
-struct ClRes {
+// One CTA's results of a round, pushed into every CTA's inbox before the
+// round's last barrier (double-buffered by round parity).
+// (64 bytes: four 16-byte asynchronous stores that complete on the
+// receiver's mbarrier)
+struct __align__(16) ClRes {
     unsigned long long i_lo, i_hi;  // sum of c over the arcs it expanded that end inside U_i
-    long long mind;                 // minimum weight after one of its decrements
+    long long mn;                   // minimum weight of its live vertices after the round (kMaxLL: none)
+    unsigned long long scnt;        // its live vertices at that weight ...
+    unsigned spec[CL_PUSH];         // ... by local id, when scnt <= CL_PUSH
 };
 
 struct ClShared {
-    ClSel sel[2][CL_MAXC];  // [parity][CTA]
-    ClRes res[CL_MAXC];     // [CTA]
-    unsigned F[2];          // list counter, by round parity
-    long long initmin;
+    ClSel sel[2][CL_MAXC];                // [parity][CTA]
+    ClRes res[2][CL_MAXC];                // [parity][CTA]
+    unsigned long long mb[2];             // [parity]: complete once every CTA's ClRes has arrived
+    unsigned inl[CL_MAXC][CL_INL];        // [CTA]: its selected local ids, when it selected at most CL_INL
+    unsigned F;                           // list counter
+    unsigned nspec, nseg;                 // this CTA's vertices at its minimum ...
+    unsigned short myslot[CL_SPEC];       // ... their slots ...
+    int myseg[CL_SPEC];                   // ... their segments ...
+    long long myalt[CL_SPEC];             // ... and each segment's minimum over its other live vertices
     long long red_mn[CL_WARPS];
     unsigned long long red_lo[CL_WARPS], red_hi[CL_WARPS];
     long long scan[CL_WARPS];
-    unsigned qcnt[CL_MAXC], qarc[CL_MAXC];  // the round: per CTA selected vertices and arcs ...
-    unsigned qcex[CL_MAXC], qaex[CL_MAXC];  // ... and their exclusive prefixes
+    unsigned qcnt[CL_MAXC], qcex[CL_MAXC];  // the round: per CTA selected vertices, exclusive prefix
     unsigned wbase[CL_WIN + 1];             // expand window: arc prefix of its entries ...
-    unsigned wstart[CL_WIN + 1];            // ... and their first arcs in the sub-graph
-    long long win_e0;
+    unsigned wstart[CL_WIN + 1];            // ... and the first arc of each entry's group
     int err;
 };
 
-// Dynamic shared memory per CTA for P slots (P a multiple of 64) in a cluster
-// of C CTAs: tw (8 B), arc start and degree (4 + 4 B), the list entry (2 B),
-// its arc prefix (4 B) and first arc (4 B) per slot, one exact minimum per
-// 64-slot segment, and two bitmaps over all C P local ids.
-__host__ __device__ __forceinline__ long long cl_smem_bytes(long long P, long long C) {
-    const long long nw = (C * P + 31) / 32;
-    return 8 * P + 4 * P + 4 * P + 8 * (P / 64) + 4 * (P + 1) + 4 * P + 2 * P + 32 + 8 * nw;
+// Dynamic shared memory per CTA for P slots (P a multiple of 64): tw (8 B),
+// arc start and degree (4 + 4 B) and the list entry (2 B) per slot, and one
+// exact minimum per 64-slot segment.
+__host__ __device__ __forceinline__ long long cl_smem_bytes(long long P, long long) {
+    return 8 * P + 4 * P + 4 * P + 8 * (P / 64) + 2 * P + 16;
 }
 
 __device__ __forceinline__ long long block_min64(long long x, long long *s) {
@@ -211,6 +224,53 @@ __device__ __forceinline__ long long cl_cas_b64(uint32_t a, long long cmp, long 
 __device__ __forceinline__ void cl_st_u32(uint32_t a, unsigned x) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(x) : "memory");
 }
+
+__device__ __forceinline__ void cl_st_v2u64(uint32_t a, unsigned long long x, unsigned long long y) {
+    asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(x), "l"(y) : "memory");
+}
+
+__device__ __forceinline__ void cl_st_v4u32(uint32_t a, unsigned x, unsigned y, unsigned z, unsigned w) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+// 16 bytes into another CTA's shared memory, completing (as 16 transaction
+// bytes) on the mbarrier at 'mbar' in that CTA
+__device__ __forceinline__ void cl_st_async_v4(uint32_t a, uint32_t mbar, unsigned x, unsigned y, unsigned z,
+                                               unsigned w) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(a),
+                 "r"(x), "r"(y), "r"(z), "r"(w), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mb_init(unsigned long long *mb, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(mb)), "r"(count)
+                 : "memory");
+}
+
+// this thread's arrival, announcing 'tx' transaction bytes for the current phase
+__device__ __forceinline__ void mb_arrive_expect_tx(unsigned long long *mb, unsigned tx) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            (unsigned)__cvta_generic_to_shared(mb)),
+        "r"(tx)
+        : "memory");
+}
+
+// has the phase of parity 'parity' completed? (acquire at cluster scope: the
+// asynchronous stores that completed it are visible)
+__device__ __forceinline__ bool mb_try_wait(unsigned long long *mb, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, "
+        "1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"((unsigned)__cvta_generic_to_shared(mb)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// L1 prefetch of the line holding p (no data returned)
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 __device__ __forceinline__ void cl_st_u64(uint32_t a, unsigned long long x) {
     asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(x) : "memory");
@@ -240,20 +300,16 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
     const long long L = ctl->live_len;
     const int *live = ctl->live_sel ? A.live1 : A.live0;
     const long long nown = L > (long long)r ? (L - (long long)r + C - 1) / C : 0;
-    const int nsl = (int)((nown + 63) / 64);           // segments that hold this CTA's vertices
-    const long long NW = ((long long)C * P + 31) / 32;  // bitmap words
-    const int nwl = (int)((L + 31) / 32);               // ... that cover the live set
-    long long *tw = (long long *)smem;                         // [P]
-    unsigned *tst = (unsigned *)(smem + 8 * (size_t)P);        // [P] first arc
-    unsigned *tdg = tst + P;                                   // [P] arcs
-    long long *segmin = (long long *)(tdg + P);                // [P / 64]
-    unsigned *pre = (unsigned *)(segmin + P / 64);             // [P + 1] list arc prefix
-    unsigned *first = pre + P + 1;                             // [P] first arc of each list entry
-    unsigned short *lst = (unsigned short *)(first + P);       // [P] list of selected slots
-    unsigned *bm = (unsigned *)(((uintptr_t)(lst + P) + 15) & ~(uintptr_t)15);  // [2][NW]
+    const int nsl = (int)((nown + 63) / 64);  // segments that hold this CTA's vertices
+    long long *tw = (long long *)smem;                          // [P]
+    unsigned *tst = (unsigned *)(smem + 8 * (size_t)P);         // [P] first arc
+    unsigned *tdg = tst + P;                                    // [P] arcs
+    long long *segmin = (long long *)(tdg + P);                 // [P / 64]
+    unsigned short *lst = (unsigned short *)(segmin + P / 64);  // [P] list of selected slots
     const bool dg = A.tcw == nullptr;
     const int *tcol = A.tcol;
     const long long *tcw = A.tcw;
+    const unsigned long long grp_bytes = 4ull * DUPIN_GRP_STRIDE * (unsigned long long)(A.hcap + 1);
 
     for (long long s = tid; s < P; s += CL_THREADS) {
         if (s < nown) {
@@ -282,224 +338,353 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
     st.n_min_rule = ctl->n_min_rule;
     st.scan = ctl->scan_volume;
     if (tid == 0) {
-        S.F[0] = 0;
-        S.F[1] = 0;
+        S.F = 0;
         S.err = 0;
     }
-    {  // nothing of the live set is removed before the first round
-        unsigned *b0 = bm + (st.round & 1) * NW;
-        for (int k = tid; k < nwl; k += CL_THREADS) b0[k] = 0;
+    __syncthreads();
+    for (int q = wid; q < nsl; q += CL_WARPS) {  // exact segment minima
+        const longlong2 v = *(const longlong2 *)&tw[(long long)q * 64 + 2 * lane];
+        long long m = kMaxLL;
+        if (v.x >= 0) m = v.x;
+        if (v.y >= 0 && v.y < m) m = v.y;
+        m = warp_min64(m);
+        if (lane == 0) segmin[q] = m;
+    }
+
+    // The results of a round (and, once, of the state before the first): this
+    // CTA's minimum live weight, its live vertices at that weight -- the
+    // minimum rule's choice here, should the next round take it and this CTA
+    // hold the cluster's minimum -- with each of their segments' minimum over
+    // its other live vertices, L2 prefetches of their arcs and group bounds,
+    // and the push of all that and the round's internal sum into every CTA's
+    // inbox (buffer pb).
+    auto publish = [&](int pb, unsigned long long il, unsigned long long ih) {
+        if (NARROW) il = warp_sum64_redux(il);
+        else warp_sum128(il, ih);
+        if (lane == 0) {
+            S.red_lo[wid] = il;
+            S.red_hi[wid] = ih;
+        }
+        if (tid == 0) {
+            S.nspec = 0;
+            S.nseg = 0;
+        }
+        __syncthreads();  // the round's decrements and segment minima are final
+        long long mn = kMaxLL;
+        for (int q = tid; q < nsl; q += CL_THREADS) mn = segmin[q] < mn ? segmin[q] : mn;
+        mn = block_min64(mn, S.red_mn);
+        if (mn != kMaxLL) {
+            for (int q0 = wid * 32; q0 < nsl; q0 += CL_THREADS) {  // warp-uniform
+                const int q = q0 + lane;
+                unsigned cm = __ballot_sync(0xffffffffu, q < nsl && segmin[q] == mn);
+                while (cm) {
+                    const int qq = q0 + __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    const long long p = (long long)qq * 64 + 2 * lane;
+                    const longlong2 v = *(const longlong2 *)&tw[p];
+                    const bool s0 = v.x == mn, s1 = v.y == mn;
+                    long long m = kMaxLL;
+                    if (v.x >= 0 && !s0) m = v.x;
+                    if (v.y >= 0 && !s1 && v.y < m) m = v.y;
+                    m = warp_min64(m);
+                    const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
+                    unsigned base = 0;
+                    if (lane == 0) {
+                        base = atomicAdd(&S.nspec, (unsigned)(__popc(b0) + __popc(b1)));
+                        const unsigned k = atomicAdd(&S.nseg, 1u);
+                        if (k < CL_SPEC) {
+                            S.myseg[k] = qq;
+                            S.myalt[k] = m;
+                        }
+                    }
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const unsigned lt = (1u << lane) - 1u;
+                    unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
+                    if (s0) {
+                        if (slot < CL_SPEC) S.myslot[slot] = (unsigned short)p;
+                        slot++;
+                    }
+                    if (s1 && slot < CL_SPEC) S.myslot[slot] = (unsigned short)(p + 1);
+                }
+            }
+        }
+        __syncthreads();
+        const unsigned ns = S.nspec;
+        if (ns <= CL_SPEC && tid >= 32) {  // one prefetch per thread (warp 0 pushes)
+            const unsigned x = (unsigned)tid - 32, e = x / 3, k = x - 3 * e;
+            if (e < ns && (k != 1 || !dg)) {
+                const unsigned sl = S.myslot[e];
+                if (k == 0) prefetch_l2(tcol, 4ull * A.tarc_cap, 4ull * tst[sl], 4ull * tdg[sl]);
+                else if (k == 1) prefetch_l2(tcw, 8ull * A.tarc_cap, 8ull * tst[sl], 8ull * tdg[sl]);
+                else
+                    prefetch_l2(A.tgrp, grp_bytes, 4ull * DUPIN_GRP_STRIDE * ((unsigned long long)sl * C + r),
+                                4ull * DUPIN_GRP_STRIDE);
+            }
+        }
+        if (wid == 0) {  // lane o pushes this CTA's results into CTA o's inbox
+            unsigned long long l = lane < CL_WARPS ? S.red_lo[lane] : 0, h = lane < CL_WARPS ? S.red_hi[lane] : 0;
+            warp_sum128(l, h);
+            l = __shfl_sync(0xffffffffu, l, 0);
+            h = __shfl_sync(0xffffffffu, h, 0);
+            if (lane < (int)C) {
+                const uint32_t b = cl_map(&S.res[pb][r], lane), m = cl_map(&S.mb[pb], lane);
+                unsigned x[CL_PUSH];
+#pragma unroll
+                for (int k = 0; k < CL_PUSH; k++) x[k] = (unsigned)k < ns ? (unsigned)S.myslot[k] * C + r : 0u;
+                cl_st_async_v4(b, m, (unsigned)l, (unsigned)(l >> 32), (unsigned)h, (unsigned)(h >> 32));
+                cl_st_async_v4(b + 16, m, (unsigned)mn, (unsigned)((unsigned long long)mn >> 32), ns, 0u);
+                cl_st_async_v4(b + 32, m, x[0], x[1], x[2], x[3]);
+                cl_st_async_v4(b + 48, m, x[4], x[5], x[6], x[7]);
+            }
+        }
+    };
+    // every CTA's results (buffer pb), read by every warp alike: the
+    // cluster's minimum live weight, whether a CTA holding it listed more
+    // vertices than its inbox list takes, and the round's internal sum
+    auto results = [&](int pb, long long &Mn, bool &over, unsigned long long &Il, unsigned long long &Ih) {
+        long long mn = kMaxLL;
+        unsigned sc = 0;
+        unsigned long long il = 0, ih = 0;
+        if (lane < (int)C) {
+            const ClRes &x = S.res[pb][lane];
+            mn = x.mn;
+            sc = x.scnt;
+            il = x.i_lo;
+            ih = x.i_hi;
+        }
+        Mn = warp_min64(mn);
+        over = __any_sync(0xffffffffu, lane < (int)C && mn == Mn && sc > CL_PUSH) != 0;
+        if (NARROW) {
+            Il = warp_sum64_redux(il);
+            Ih = 0;
+        } else {
+            warp_sum128(il, ih);
+            Il = __shfl_sync(0xffffffffu, il, 0);
+            Ih = __shfl_sync(0xffffffffu, ih, 0);
+        }
+    };
+
+    // every CTA's results of a round arrive by asynchronous stores that
+    // complete on the receiver's mbarrier of the round's parity: one local
+    // arrival (announcing C ClRes of transaction bytes) and the C pushes
+    // complete a phase.  A CTA can push round i+2's results (same parity)
+    // only after it has received this CTA's results of round i+1, which this
+    // CTA sends after its wait for round i: phases never overlap.
+    unsigned phase = 0;  // bit b: parity of mbarrier b's current phase
+    int werr = 0;
+    auto expect = [&](int pb) {
+        if (tid == 0) mb_arrive_expect_tx(&S.mb[pb], (unsigned)(C * sizeof(ClRes)));
+    };
+    auto wait_results = [&](int pb) {
+        int bad = 0;
+        if (!mb_try_wait(&S.mb[pb], (phase >> pb) & 1)) {
+            const long long t0 = clock64();
+            while (!mb_try_wait(&S.mb[pb], (phase >> pb) & 1)) {
+                if (clock64() - t0 > (1ll << 32)) {  // a lost push: cannot happen; give up rather than hang
+                    bad = 1;
+                    break;
+                }
+            }
+        }
+        phase ^= 1u << pb;
+        if (__syncthreads_or(bad)) werr = DUPIN_ERR_TIMEOUT;
+    };
+    if (tid == 0) {
+        mb_init(&S.mb[0], 1);
+        mb_init(&S.mb[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    expect((int)(st.round & 1));
+    cl_sync();  // every CTA's mbarriers are set up before any push
+    publish((int)(st.round & 1), 0, 0);
+    wait_results((int)(st.round & 1));
+    TailRound R;
+    bool fast;
     {
-        long long mn = kMaxLL;
-        for (int q = wid; q < nsl; q += CL_WARPS) {
-            const longlong2 v = *(const longlong2 *)&tw[(long long)q * 64 + 2 * lane];
-            long long m = kMaxLL;
-            if (v.x >= 0) m = v.x;
-            if (v.y >= 0 && v.y < m) m = v.y;
-            m = warp_min64(m);
-            if (lane == 0) segmin[q] = m;
-            mn = m < mn ? m : mn;
-        }
-        mn = block_min64(mn, S.red_mn);
-        if (tid == 0) S.initmin = mn;
+        long long m0;
+        bool over;
+        unsigned long long il, ih;
+        results((int)(st.round & 1), m0, over, il, ih);
+        R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, m0);
+        fast = R.minrule && !over;
     }
-    cl_sync();
-    long long m0 = kMaxLL;
-    if (lane < (int)C) m0 = cl_ld_s64(cl_map(&S.initmin, lane));
-    m0 = warp_min64(m0);
-    TailRound R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, m0);
-    int err = 0;
-    while (!R.done) {
+    int err = werr;
+    while (!R.done && !err) {
         if (R.i > A.max_rounds) {
             err = DUPIN_ERR_NO_PROGRESS;
             break;
         }
         const long long i = R.i;
-        const int par = (int)(i & 1);
-        unsigned *bmc = bm + par * NW;              // removed through round i (built below)
-        const unsigned *bmp = bm + (par ^ 1) * NW;  // removed through round i-1
-        // ---- S: select this CTA's slots (segments that may hold selected vertices)
-        unsigned long long wlo = 0, whi = 0;
-        long long mins = kMaxLL;  // survivors' minimum over the segments this lane looked at
-        for (int q0 = wid * 32; q0 < nsl; q0 += CL_THREADS) {
-            const int q = q0 + lane;
-            const long long sm = q < nsl ? segmin[q] : kMaxLL;
-            const bool cand = seg_candidate(sm, R);
-            if (!cand) mins = sm < mins ? sm : mins;
-            unsigned cm = __ballot_sync(0xffffffffu, cand);
-            __syncwarp();
-            while (cm) {
-                const int qq = q0 + __ffs(cm) - 1;
-                cm &= cm - 1;
-                const long long p = (long long)qq * 64 + 2 * lane;
-                const longlong2 v = *(const longlong2 *)&tw[p];
-                bool s0, s1;
-                if (R.minrule) {
-                    s0 = v.x >= 0 && v.x <= R.minw;
-                    s1 = v.y >= 0 && v.y <= R.minw;
-                } else {
-                    s0 = v.x >= 0 && (v.x <= R.gle || mul_le(v.x, R.Y, R.Xhi, R.Xlo));
-                    s1 = v.y >= 0 && (v.y <= R.gle || mul_le(v.y, R.Y, R.Xhi, R.Xlo));
-                }
-                long long m = kMaxLL;
-                if (v.x >= 0 && !s0) m = v.x;
-                if (v.y >= 0 && !s1 && v.y < m) m = v.y;
-                m = warp_min64(m);
-                if (lane == 0) {
-                    segmin[qq] = m;  // the survivors' minimum; the expand lowers it further
-                    mins = m < mins ? m : mins;
-                }
-                const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
-                if (b0 | b1) {
-                    unsigned base = 0;
-                    if (lane == 0) base = atomicAdd(&S.F[par], (unsigned)(__popc(b0) + __popc(b1)));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    const unsigned lt = (1u << lane) - 1u;
-                    unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
-                    if (s0) {
-                        tw[p] = -i;
-                        if (NARROW) wlo += (unsigned long long)v.x;
-                        else add128(wlo, whi, (unsigned long long)v.x, 0);
-                        lst[slot++] = (unsigned short)p;
-                    }
-                    if (s1) {
-                        tw[p + 1] = -i;
-                        if (NARROW) wlo += (unsigned long long)v.y;
-                        else add128(wlo, whi, (unsigned long long)v.y, 0);
-                        lst[slot] = (unsigned short)(p + 1);
-                    }
-                }
+        const int par = (int)(i & 1), ppar = par ^ 1;
+        expect(par);
+        unsigned long long Wl = 0, Wh = 0;  // sum of the removed vertices' weights
+        if (fast) {
+            // U_i: the vertices at the minimum weight, listed by the CTAs that
+            // hold it with the previous round's results; each marks its own
+            if (S.res[ppar][r].mn == R.minw) {
+                const unsigned ns = (unsigned)S.res[ppar][r].scnt;
+                const unsigned ng = S.nseg < ns ? S.nseg : ns;
+                for (unsigned e = tid; e < ns; e += CL_THREADS) tw[S.myslot[e]] = -i;
+                for (unsigned k = tid; k < ng; k += CL_THREADS) segmin[S.myseg[k]] = S.myalt[k];
             }
-        }
-        if (NARROW) wlo = warp_sum64_redux(wlo);
-        else warp_sum128(wlo, whi);
-        mins = warp_min64(mins);
-        if (lane == 0) {
-            S.red_lo[wid] = wlo;
-            S.red_hi[wid] = whi;
-            S.red_mn[wid] = mins;
-        }
-        __syncthreads();
-        const unsigned F = S.F[par];
-        if (tid == 0) S.F[par ^ 1] = 0;  // round i+1's counter (last read in round i-1)
-        // the list's arc prefix and first arcs; each listed vertex's arcs are
-        // prefetched into L2 now (the expand reads them after the barrier)
-        if (F <= 32) {
             if (wid == 0) {
-                unsigned d = 0;
-                if (lane < (int)F) {
-                    const unsigned sl = lst[lane];
-                    d = tdg[sl];
-                    first[lane] = tst[sl];
-                    prefetch_l2(tcol, 4ull * A.tarc_cap, 4ull * tst[sl], 4ull * d);
-                    if (!dg) prefetch_l2(tcw, 8ull * A.tarc_cap, 8ull * tst[sl], 8ull * d);
-                }
-                unsigned incl = d;
+                const unsigned c =
+                    lane < (int)C && S.res[ppar][lane].mn == R.minw ? (unsigned)S.res[ppar][lane].scnt : 0;
+                unsigned ic = c;
 #pragma unroll
                 for (int k = 1; k < 32; k <<= 1) {
-                    const unsigned o = __shfl_up_sync(0xffffffffu, incl, k);
-                    if (lane >= k) incl += o;
+                    const unsigned oc = __shfl_up_sync(0xffffffffu, ic, k);
+                    if (lane >= k) ic += oc;
                 }
-                if (lane < (int)F) pre[lane] = incl - d;
-                if (lane == 31) pre[F] = incl;
+                if (lane < (int)C) {
+                    S.qcnt[lane] = c;
+                    S.qcex[lane] = ic - c;
+                }
             }
+            __syncthreads();
+            const unsigned Un = S.qcex[C - 1] + S.qcnt[C - 1];
+            const u128 W = (u128)(unsigned long long)R.minw * Un;
+            Wl = (unsigned long long)W;
+            Wh = (unsigned long long)(W >> 64);
         } else {
-            unsigned carry = 0;
-            for (unsigned e0 = 0; e0 < F; e0 += CL_THREADS) {
-                const unsigned e = e0 + tid;
-                unsigned d = 0;
-                if (e < F) {
-                    const unsigned sl = lst[e];
-                    d = tdg[sl];
-                    first[e] = tst[sl];
-                    prefetch_l2(tcol, 4ull * A.tarc_cap, 4ull * tst[sl], 4ull * d);
-                    if (!dg) prefetch_l2(tcw, 8ull * A.tarc_cap, 8ull * tst[sl], 8ull * d);
+            // ---- S: select this CTA's slots (segments that may hold selected vertices)
+            unsigned long long wlo = 0, whi = 0;
+            for (int q0 = wid * 32; q0 < nsl; q0 += CL_THREADS) {
+                const int q = q0 + lane;
+                const long long sm = q < nsl ? segmin[q] : kMaxLL;
+                unsigned cm = __ballot_sync(0xffffffffu, seg_candidate(sm, R));
+                __syncwarp();
+                while (cm) {
+                    const int qq = q0 + __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    const long long p = (long long)qq * 64 + 2 * lane;
+                    const longlong2 v = *(const longlong2 *)&tw[p];
+                    bool s0, s1;
+                    if (R.minrule) {
+                        s0 = v.x >= 0 && v.x <= R.minw;
+                        s1 = v.y >= 0 && v.y <= R.minw;
+                    } else {
+                        s0 = v.x >= 0 && (v.x <= R.gle || mul_le(v.x, R.Y, R.Xhi, R.Xlo));
+                        s1 = v.y >= 0 && (v.y <= R.gle || mul_le(v.y, R.Y, R.Xhi, R.Xlo));
+                    }
+                    long long m = kMaxLL;
+                    if (v.x >= 0 && !s0) m = v.x;
+                    if (v.y >= 0 && !s1 && v.y < m) m = v.y;
+                    m = warp_min64(m);
+                    if (lane == 0) segmin[qq] = m;  // the survivors' minimum; the expand lowers it further
+                    const unsigned b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
+                    if (b0 | b1) {
+                        unsigned base = 0;
+                        if (lane == 0) base = atomicAdd(&S.F, (unsigned)(__popc(b0) + __popc(b1)));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        const unsigned lt = (1u << lane) - 1u;
+                        unsigned slot = base + __popc(b0 & lt) + __popc(b1 & lt);
+                        if (s0) {
+                            tw[p] = -i;
+                            if (NARROW) wlo += (unsigned long long)v.x;
+                            else add128(wlo, whi, (unsigned long long)v.x, 0);
+                            lst[slot++] = (unsigned short)p;
+                        }
+                        if (s1) {
+                            tw[p + 1] = -i;
+                            if (NARROW) wlo += (unsigned long long)v.y;
+                            else add128(wlo, whi, (unsigned long long)v.y, 0);
+                            lst[slot] = (unsigned short)(p + 1);
+                        }
+                    }
                 }
-                long long tot;
-                const long long ex = block_excl_scan<CL_WARPS>((long long)d, S.scan, tot);
-                if (e < F) pre[e] = carry + (unsigned)ex;
-                carry += (unsigned)tot;
             }
-            if (tid == 0) pre[F] = carry;
-        }
-        if (wid == 0) {  // the CTA's totals, pushed into every CTA's inbox
-            unsigned long long l = lane < CL_WARPS ? S.red_lo[lane] : 0, h = lane < CL_WARPS ? S.red_hi[lane] : 0;
-            long long m = lane < CL_WARPS ? S.red_mn[lane] : kMaxLL;
-            warp_sum128(l, h);
-            m = warp_min64(m);
-            l = __shfl_sync(0xffffffffu, l, 0);
-            h = __shfl_sync(0xffffffffu, h, 0);
-            m = __shfl_sync(0xffffffffu, m, 0);
-            __syncwarp();
-            const unsigned arcs = pre[F];
-            if (lane < (int)C) {
-                const uint32_t b = cl_map(&S.sel[par][r], lane);
-                cl_st_u32(b + offsetof(ClSel, cnt), F);
-                cl_st_u32(b + offsetof(ClSel, arcs), arcs);
-                cl_st_u64(b + offsetof(ClSel, w_lo), l);
-                cl_st_u64(b + offsetof(ClSel, w_hi), h);
-                cl_st_u64(b + offsetof(ClSel, mins), (unsigned long long)m);
+            if (NARROW) wlo = warp_sum64_redux(wlo);
+            else warp_sum128(wlo, whi);
+            if (lane == 0) {
+                S.red_lo[wid] = wlo;
+                S.red_hi[wid] = whi;
             }
-        }
-        cl_sync();  // A: every CTA's selection, list and prefix are visible
-        // ---- E: the removed set U_i and the round's arcs
-        if (wid == 0) {  // per CTA: selected vertices and arcs, and their prefixes
-            unsigned c = 0, a = 0;
-            if (lane < (int)C) {
-                c = S.sel[par][lane].cnt;
-                a = S.sel[par][lane].arcs;
+            __syncthreads();
+            const unsigned F = S.F;
+            // each listed vertex's arcs and group bounds are prefetched into
+            // L2 now (the owners read them after the barrier); a short list
+            // goes into every CTA's inbox
+            for (unsigned e = tid; e < F; e += CL_THREADS) {
+                const unsigned sl = lst[e];
+                const unsigned long long p = (unsigned long long)sl * C + r;
+                prefetch_l2(tcol, 4ull * A.tarc_cap, 4ull * tst[sl], 4ull * tdg[sl]);
+                if (!dg) prefetch_l2(tcw, 8ull * A.tarc_cap, 8ull * tst[sl], 8ull * tdg[sl]);
+                prefetch_l2(A.tgrp, grp_bytes, 4ull * DUPIN_GRP_STRIDE * p, 4ull * DUPIN_GRP_STRIDE);
             }
-            unsigned ic = c, ia = a;
+            if (F <= CL_INL)
+                for (unsigned x = tid; x < F * C; x += CL_THREADS) {
+                    const unsigned e = x >> lg, o = x & (C - 1);
+                    cl_st_u32(cl_map(&S.inl[r][e], o), (unsigned)lst[e] * C + r);
+                }
+            if (wid == 0) {  // the CTA's count and weight sum, pushed into every CTA's inbox
+                unsigned long long l = lane < CL_WARPS ? S.red_lo[lane] : 0, h = lane < CL_WARPS ? S.red_hi[lane] : 0;
+                warp_sum128(l, h);
+                l = __shfl_sync(0xffffffffu, l, 0);
+                h = __shfl_sync(0xffffffffu, h, 0);
+                if (lane < (int)C) {
+                    const uint32_t b = cl_map(&S.sel[par][r], lane);
+                    cl_st_u32(b + offsetof(ClSel, cnt), F);
+                    cl_st_u64(b + offsetof(ClSel, w_lo), l);
+                    cl_st_u64(b + offsetof(ClSel, w_hi), h);
+                }
+            }
+            cl_sync();  // A: every CTA's selection and list are visible
+            if (tid == 0) S.F = 0;  // every thread has read it
+            if (wid == 0) {  // per CTA: selected vertices and their prefix
+                const unsigned c = lane < (int)C ? S.sel[par][lane].cnt : 0;
+                unsigned ic = c;
 #pragma unroll
-            for (int k = 1; k < 32; k <<= 1) {
-                const unsigned oc = __shfl_up_sync(0xffffffffu, ic, k), oa = __shfl_up_sync(0xffffffffu, ia, k);
-                if (lane >= k) {
-                    ic += oc;
-                    ia += oa;
+                for (int k = 1; k < 32; k <<= 1) {
+                    const unsigned oc = __shfl_up_sync(0xffffffffu, ic, k);
+                    if (lane >= k) ic += oc;
+                }
+                if (lane < (int)C) {
+                    S.qcnt[lane] = c;
+                    S.qcex[lane] = ic - c;
                 }
             }
-            if (lane < (int)C) {
-                S.qcnt[lane] = c;
-                S.qarc[lane] = a;
-                S.qcex[lane] = ic - c;
-                S.qaex[lane] = ia - a;
+            Wl = lane < (int)C ? S.sel[par][lane].w_lo : 0;
+            Wh = lane < (int)C ? S.sel[par][lane].w_hi : 0;
+            if (NARROW) {
+                Wl = warp_sum64_redux(Wl);
+                Wh = 0;
+            } else {
+                warp_sum128(Wl, Wh);
+                Wl = __shfl_sync(0xffffffffu, Wl, 0);
+                Wh = __shfl_sync(0xffffffffu, Wh, 0);
             }
+            __syncthreads();
         }
-        // removed through round i = removed through round i-1, plus U_i
-        for (int k = tid; k < nwl; k += CL_THREADS) bmc[k] = bmp[k];
-        __syncthreads();
+        // ---- E: this CTA's groups of the removed vertices' arcs
         const unsigned Ltot = S.qcex[C - 1] + S.qcnt[C - 1];
-        const unsigned Atot = S.qaex[C - 1] + S.qarc[C - 1];
-        // A short round (its lists fit one window): the window over all CTAs'
-        // lists is built here, in the same pass that extends the bitmap
-        const bool gwin = Ltot <= CL_WIN;
-        for (unsigned g = tid; g < Ltot; g += CL_THREADS) {
+        unsigned long long ilo = 0, ihi = 0;
+        // entry g of the round's list (CTA by CTA) -> its local id
+        auto entry = [&](unsigned g) -> unsigned {
             int q = 0;  // the last CTA whose entries start at or before g
             for (int step = 8; step > 0; step >>= 1)
                 if (q + step < (int)C && S.qcex[q + step] <= g) q += step;
             const unsigned e = g - S.qcex[q];
-            const unsigned sl = cl_ld_u16(cl_map(lst, q) + 2 * e);
-            if (gwin) {
-                S.wbase[g] = S.qaex[q] + cl_ld_u32(cl_map(pre, q) + 4 * e);
-                S.wstart[g] = cl_ld_u32(cl_map(first, q) + 4 * e);
-            }
-            const unsigned p = sl * C + q;
-            atomicOr(&bmc[p >> 5], 1u << (p & 31));
-        }
-        if (gwin)
-            for (unsigned t = Ltot + tid; t <= CL_WIN; t += CL_THREADS) S.wbase[t] = t == Ltot ? Atot : 0xffffffffu;
-        __syncthreads();
-        unsigned long long ilo = 0, ihi = 0;
-        long long mind = kMaxLL;
-        // one arc: a survivor loses c in its owner's shared memory (returning
-        // 64-bit add; the owner's segment minimum lowered by compare-and-swap),
-        // an arc into U_i adds c to 'internal', an arc into an earlier round's
-        // removals is skipped (the bitmaps are local copies)
+            if (fast) return S.res[ppar][q].spec[e];
+            if (S.qcnt[q] <= CL_INL) return S.inl[q][e];
+            return cl_ld_u16(cl_map(lst, q) + 2 * e) * C + q;
+        };
+        // the group bounds of entry g's row for this CTA
+        auto group = [&](unsigned g, unsigned &gs, unsigned &len) {
+            const unsigned p = entry(g);
+            const unsigned *gr = A.tgrp + (size_t)p * DUPIN_GRP_STRIDE + r;
+            gs = gr[0];
+            len = gr[1] - gs;
+        };
+        // arcs into vertices this CTA owns: a survivor loses c (a returning
+        // 64-bit shared-memory atomic; the segment minimum lowered by
+        // atomicMin), an arc into U_i adds c to 'internal', an arc into an
+        // earlier round's removals is skipped.  The heads' states are read
+        // before any update (removal marks do not change during the expand).
         auto arcs = [&](const long long (&pos)[CL_ILP]) {
             int cv[CL_ILP];
-            long long cc[CL_ILP];
+            long long cc[CL_ILP], wv[CL_ILP];
 #pragma unroll
             for (int u = 0; u < CL_ILP; u++) {
                 if (pos[u] >= 0) {
@@ -507,163 +692,107 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
                     cc[u] = dg ? DUPIN_Q_ONE : tcw[pos[u]];
                 }
             }
-            uint32_t sa[CL_ILP];
-            long long nv[CL_ILP], sm[CL_ILP];
 #pragma unroll
             for (int u = 0; u < CL_ILP; u++) {
-                nv[u] = kMaxLL;
+                wv[u] = kPad;
                 if (pos[u] < 0) continue;
-                const unsigned v = (unsigned)cv[u];
-                if (!((bmc[v >> 5] >> (v & 31)) & 1u)) {
-                    const unsigned o = v & (C - 1), sl = v >> lg;
-                    sa[u] = cl_map(&segmin[sl >> 6], o);
-                    sm[u] = cl_ld_s64(sa[u]);
-                    nv[u] = (long long)cl_atom_add_u64(cl_map(&tw[sl], o), (unsigned long long)(-cc[u])) - cc[u];
-                    mind = nv[u] < mind ? nv[u] : mind;
-                } else if (!((bmp[v >> 5] >> (v & 31)) & 1u)) {
+                const unsigned v = (unsigned)cv[u], sl = v >> lg;
+                if ((v & (C - 1)) != r || (long long)sl >= nown) {  // not this CTA's vertex: a broken group
+                    S.err = DUPIN_ERR_CUDA;
+                    continue;
+                }
+                wv[u] = tw[sl];
+            }
+#pragma unroll
+            for (int u = 0; u < CL_ILP; u++) {
+                if (wv[u] >= 0) {
+                    const unsigned sl = (unsigned)cv[u] >> lg;
+                    const long long nv =
+                        (long long)atomicAdd((unsigned long long *)&tw[sl], (unsigned long long)(-cc[u])) - cc[u];
+                    atomicMin(&segmin[sl >> 6], nv);
+                } else if (wv[u] == -i) {
                     if (NARROW) ilo += (unsigned long long)cc[u];
                     else add128(ilo, ihi, (unsigned long long)cc[u], 0);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < CL_ILP; u++) {
-                if (nv[u] == kMaxLL) continue;
-                long long cur = sm[u];
-                while (nv[u] < cur) {
-                    const long long prev = cl_cas_b64(sa[u], cur, nv[u]);
-                    if (prev == cur) break;
-                    cur = prev;
-                }
-            }
         };
-        {
-            const unsigned E0 = (unsigned)split_at(Atot, r, C), E1 = (unsigned)split_at(Atot, r + 1, C);
-            if (gwin) {
-                for (unsigned xb = E0 + tid; xb < E1; xb += CL_ILP * CL_THREADS) {
-                    long long pos[CL_ILP];
+        for (unsigned w0 = 0; w0 < Ltot; w0 += CL_WIN) {  // block-uniform: a window of list entries
+            const unsigned nw = Ltot - w0 < CL_WIN ? Ltot - w0 : CL_WIN;
+            if (nw <= 32) {
+                if (wid == 0) {
+                    unsigned gs = 0, len = 0;
+                    if (lane < (int)nw) group(w0 + lane, gs, len);
+                    unsigned incl = len;
 #pragma unroll
-                    for (int u = 0; u < CL_ILP; u++) {
-                        const unsigned xx = xb + u * CL_THREADS;
-                        pos[u] = -1;
-                        if (xx < E1) {
-                            int lo2 = 0, hi2 = (int)Ltot;  // last t with wbase[t] <= xx
-                            while (lo2 < hi2) {
-                                const int mid = (lo2 + hi2 + 1) >> 1;
-                                if (S.wbase[mid] <= xx) lo2 = mid;
-                                else hi2 = mid - 1;
-                            }
-                            pos[u] = (long long)S.wstart[lo2] + (xx - S.wbase[lo2]);
-                        }
+                    for (int k = 1; k < 32; k <<= 1) {
+                        const unsigned o = __shfl_up_sync(0xffffffffu, incl, k);
+                        if (lane >= k) incl += o;
                     }
-                    arcs(pos);
+                    if (lane < (int)nw) {
+                        S.wbase[lane] = incl - len;
+                        S.wstart[lane] = gs;
+                    }
+                    if (lane == 31) S.wbase[nw] = incl;
                 }
             } else {
-                unsigned x = E0;
-                int q = 0;
-                while (x < E1) {  // block-uniform: a window of one CTA's list at a time
-                    while (q + 1 < (int)C && (S.qaex[q + 1] <= x || S.qarc[q] == 0)) q++;
-                    if (!(S.qaex[q] <= x && x < S.qaex[q] + S.qarc[q])) {  // cannot happen for x < Atot
-                        if (tid == 0) S.err = DUPIN_ERR_CUDA;
-                        break;
+                unsigned carry = 0;
+                for (unsigned t0 = 0; t0 < nw; t0 += CL_THREADS) {
+                    const unsigned t = t0 + tid;
+                    unsigned gs = 0, len = 0;
+                    if (t < nw) group(w0 + t, gs, len);
+                    long long tot;
+                    const long long ex = block_excl_scan<CL_WARPS>((long long)len, S.scan, tot);
+                    if (t < nw) {
+                        S.wbase[t] = carry + (unsigned)ex;
+                        S.wstart[t] = gs;
                     }
-                    const unsigned qbase = S.qaex[q], qcnt = S.qarc[q], Fq = S.qcnt[q];
-                    const unsigned lo = x - qbase;
-                    const unsigned hi = (E1 - qbase < qcnt ? E1 - qbase : qcnt);
-                    const uint32_t rpre = cl_map(pre, q), rfirst = cl_map(first, q);
-                    if (wid == 0) {  // the window's first entry: the last e with pre_q[e] <= lo
-                        const long long e = warp_search_last_le_fn(
-                            (long long)Fq - 1, [&](long long k) { return cl_ld_u32(rpre + 4 * (uint32_t)k) <= lo; });
-                        if (lane == 0) S.win_e0 = e;
-                    }
-                    __syncthreads();
-                    const long long e0 = S.win_e0;
-                    for (int t = tid; t <= CL_WIN; t += CL_THREADS) {
-                        const long long e = e0 + t;
-                        unsigned b = 0xffffffffu, s0 = 0;
-                        if (e <= (long long)Fq) b = cl_ld_u32(rpre + 4 * (uint32_t)e);
-                        if (e < (long long)Fq) s0 = cl_ld_u32(rfirst + 4 * (uint32_t)e);
-                        S.wbase[t] = b;
-                        S.wstart[t] = s0;
-                    }
-                    __syncthreads();
-                    const unsigned wend = S.wbase[CL_WIN] < hi ? S.wbase[CL_WIN] : hi;
-                    for (unsigned xb = lo + tid; xb < wend; xb += CL_ILP * CL_THREADS) {
-                        long long pos[CL_ILP];
-#pragma unroll
-                        for (int u = 0; u < CL_ILP; u++) {
-                            const unsigned xx = xb + u * CL_THREADS;
-                            pos[u] = -1;
-                            if (xx < wend) {
-                                int lo2 = 0, hi2 = CL_WIN;  // last t with wbase[t] <= xx
-                                while (lo2 < hi2) {
-                                    const int mid = (lo2 + hi2 + 1) >> 1;
-                                    if (S.wbase[mid] <= xx) lo2 = mid;
-                                    else hi2 = mid - 1;
-                                }
-                                pos[u] = (long long)S.wstart[lo2] + (xx - S.wbase[lo2]);
-                            }
-                        }
-                        arcs(pos);
-                    }
-                    x = qbase + wend;
-                    __syncthreads();  // the window is reused
+                    carry += (unsigned)tot;
                 }
+                if (tid == 0) S.wbase[nw] = carry;
             }
-        }
-        if (NARROW) ilo = warp_sum64_redux(ilo);
-        else warp_sum128(ilo, ihi);
-        mind = warp_min64(mind);
-        if (lane == 0) {
-            S.red_lo[wid] = ilo;
-            S.red_hi[wid] = ihi;
-            S.red_mn[wid] = mind;
-        }
-        __syncthreads();
-        if (wid == 0) {  // this CTA's results, pushed into every CTA's inbox
-            unsigned long long l = lane < CL_WARPS ? S.red_lo[lane] : 0, h = lane < CL_WARPS ? S.red_hi[lane] : 0;
-            long long m = lane < CL_WARPS ? S.red_mn[lane] : kMaxLL;
-            warp_sum128(l, h);
-            m = warp_min64(m);
-            l = __shfl_sync(0xffffffffu, l, 0);
-            h = __shfl_sync(0xffffffffu, h, 0);
-            m = __shfl_sync(0xffffffffu, m, 0);
-            if (lane < (int)C) {
-                const uint32_t b = cl_map(&S.res[r], lane);
-                cl_st_u64(b + offsetof(ClRes, i_lo), l);
-                cl_st_u64(b + offsetof(ClRes, i_hi), h);
-                cl_st_u64(b + offsetof(ClRes, mind), (unsigned long long)m);
+            __syncthreads();
+            const unsigned wt = S.wbase[nw];
+            for (unsigned xb = tid; xb < wt; xb += CL_ILP * CL_THREADS) {
+                long long pos[CL_ILP];
+#pragma unroll
+                for (int u = 0; u < CL_ILP; u++) {
+                    const unsigned xx = xb + u * CL_THREADS;
+                    pos[u] = -1;
+                    if (xx < wt) {
+                        int lo2 = 0, hi2 = (int)nw - 1;  // last t with wbase[t] <= xx
+                        while (lo2 < hi2) {
+                            const int mid = (lo2 + hi2 + 1) >> 1;
+                            if (S.wbase[mid] <= xx) lo2 = mid;
+                            else hi2 = mid - 1;
+                        }
+                        pos[u] = (long long)S.wstart[lo2] + (xx - S.wbase[lo2]);
+                    }
+                }
+                arcs(pos);
             }
+            __syncthreads();  // the window is reused
         }
-        cl_sync();  // B: every decrement and every CTA's results of round i are visible
+        publish(par, ilo, ihi);
+        wait_results(par);  // every CTA's results of round i have arrived
+        if (werr) {
+            err = werr;
+            break;
+        }
         // ---- C: close round i and plan round i+1 (every warp, same values, local reads)
-        unsigned long long Wl = 0, Wh = 0, Il = 0, Ih = 0;
-        unsigned Uq = 0;
-        long long Mn = kMaxLL;
-        if (lane < (int)C) {
-            const ClSel &x = S.sel[par][lane];
-            const ClRes &y = S.res[lane];
-            Uq = x.cnt;
-            Wl = x.w_lo;
-            Wh = x.w_hi;
-            Il = y.i_lo;
-            Ih = y.i_hi;
-            Mn = x.mins < y.mind ? x.mins : y.mind;
+        long long Mn;
+        bool over;
+        unsigned long long Il, Ih;
+        results(par, Mn, over, Il, Ih);
+        if (wid == 0) {
+            // should round i+1 take the minimum rule, its list is the CTAs at
+            // Mn: their group bounds for this CTA are prefetched into L1 now,
+            // while the round closes
+            const unsigned c = lane < (int)C && S.res[par][lane].mn == Mn ? (unsigned)S.res[par][lane].scnt : 0;
+            if (!over && c > 0)
+                for (unsigned e = 0; e < c; e++)
+                    prefetch_l1(A.tgrp + (size_t)S.res[par][lane].spec[e] * DUPIN_GRP_STRIDE + r);
         }
-        const long long Un = (long long)__reduce_add_sync(0xffffffffu, Uq);
-        if (NARROW) {
-            Wl = warp_sum64_redux(Wl);
-            Il = warp_sum64_redux(Il);
-            Wh = 0;
-            Ih = 0;
-        } else {
-            warp_sum128(Wl, Wh);
-            warp_sum128(Il, Ih);
-            Wl = __shfl_sync(0xffffffffu, Wl, 0);
-            Wh = __shfl_sync(0xffffffffu, Wh, 0);
-            Il = __shfl_sync(0xffffffffu, Il, 0);
-            Ih = __shfl_sync(0xffffffffu, Ih, 0);
-        }
-        Mn = warp_min64(Mn);
+        const long long Un = (long long)Ltot;
         const u128 wsel = mk128(Wl, Wh), internal = mk128(Il, Ih);
         st.f = st.f - (wsel - (internal >> 1));
         st.scan += st.size;
@@ -686,6 +815,7 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
             break;
         }
         R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, Mn);
+        fast = R.minrule && !over;
     }
     if (tid == 0 && S.err) set_error(ctl, S.err);
     // peel rounds of this CTA's vertices
@@ -738,7 +868,7 @@ ClConfig g_cl[64];
 // where a cluster that large can be resident, else 8; P slots per CTA as the
 // shared memory allows (a multiple of 64, at most 65,536).
 static long long slots_for(int C, int dyn) {
-    long long P = (long long)dyn / (26 + C / 4);
+    long long P = (long long)dyn / 18;
     P = (P / 64) * 64;
     while (P > 0 && cl_smem_bytes(P, C) > dyn) P -= 64;
     return P > 65536 ? 65536 : P;  // a list entry keeps the slot in 16 bits

@@ -34,6 +34,7 @@ typedef unsigned __int128 u128;
 #define DUPIN_ONE_CTA_ARCS (1LL << 20)
 // ... provided its live sub-graph fits the tail's arc buffer (2^27 arcs)
 #define DUPIN_TAIL_BUF_ARCS (1LL << 27)
+#define DUPIN_GRP_STRIDE 17  // per tail row: its first arc, then each owner group's end (16 owners at most)
 
 // Peeling phases recorded in PeelCtl::status
 #define ST_RUNNING 0
@@ -143,6 +144,11 @@ struct PeelArgs {
     int *tcol;          // tail arcs: local neighbour ids
     long long *tcw;     // tail arcs: weights (nullptr for DG)
     long long tarc_cap;
+    // cluster tail: each row's arcs grouped by the owner of their head (local
+    // id mod cl_c); row p's group o is [tgrp[p G + o], tgrp[p G + o + 1]) for
+    // G = DUPIN_GRP_STRIDE
+    unsigned *tgrp;
+    int cl_c;           // CTAs of the cluster tail (0: none)
 };
 
 // ---------------------------------------------------------------- helpers

@@ -44,6 +44,7 @@ struct PeelWorkspace {
     int *loc = nullptr;
     long long *tdeg = nullptr, *tlrp = nullptr;
     int *tcnt = nullptr, *tfill = nullptr;
+    unsigned *tgrp = nullptr;
     int *tcol = nullptr;
     long long *tcw = nullptr;
     uint8_t *mask = nullptr;

@@ -950,6 +950,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
     const int *hubs = A.g.hubs;
     const long long *cw = A.g.cw;
     const int *pr = A.pr;
+    const bool grp = c->status == ST_CLUSTER && A.tgrp != nullptr && A.cl_c > 0;
     walk_arcs([=](long long k) { return tdeg[k]; },
               [=](long long k) { return rp[live[k]]; }, L, e0, e1, k0, s_base, s_start,
               [&](long long k, long long pos) {
@@ -957,12 +958,33 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
                   if (pr[v] != DUPIN_LIVE) return;
                   if (PASS == 0) {
                       atomicAdd(&A.tcnt[k], 1);
+                      if (grp) atomicAdd(&A.tgrp[k * DUPIN_GRP_STRIDE + 1 + (A.loc[v] & (A.cl_c - 1))], 1u);
                   } else {
-                      long long slot = A.tlrp[k] + atomicAdd(&A.tfill[k], 1);
+                      const long long slot =
+                          grp ? (long long)atomicAdd(&A.tgrp[k * DUPIN_GRP_STRIDE + 1 + (A.loc[v] & (A.cl_c - 1))], 1u)
+                              : A.tlrp[k] + atomicAdd(&A.tfill[k], 1);
                       A.tcol[slot] = A.loc[v];
                       if (A.tcw) A.tcw[slot] = cw ? cw[pos] : DUPIN_Q_ONE;
                   }
               });
+}
+
+// For the cluster tail: each row's owner-group counts become the groups' first
+// arcs (the fill pointers of pass 1, which leaves each group's end there).
+__global__ void k_tail_grp(PeelArgs A) {
+    const PeelCtl *c = A.ctl;
+    if (c->status != ST_CLUSTER || c->error || A.tgrp == nullptr || A.cl_c <= 0) return;
+    const long long L = c->live_len;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < L; k += (long long)gridDim.x * blockDim.x) {
+        unsigned *g = A.tgrp + k * DUPIN_GRP_STRIDE;
+        unsigned run = (unsigned)A.tlrp[k];
+        g[0] = run;
+        for (int o = 0; o < A.cl_c; o++) {
+            const unsigned cnt = g[1 + o];
+            g[1 + o] = run;
+            run += cnt;
+        }
+    }
 }
 
 // One CTA finishes the peel on the live sub-graph held in shared memory.
@@ -1403,7 +1425,7 @@ long long workspace_bytes(long long n, long long arcs, bool has_cw, const PeelPl
     b += n * (8 + 4 + 4 + 4 + 4 + 8 + 8 + 8 + 4 + 1) + 8 * (n + 1);
     b += 8 * (grid + 1) + (long long)sizeof(BlockPart) * grid + (long long)sizeof(PeelCtl);
     b += 32 * tr_cap;
-    b += (tail_cap + 1) * (8 + 8 + 4 + 4);
+    b += (tail_cap + 1) * (8 + 8 + 4 + 4 + 4 * DUPIN_GRP_STRIDE);
     b += tarc * (4 + (has_cw ? 8 : 0));
     return b;
 }
@@ -1413,7 +1435,7 @@ void workspace_free(PeelWorkspace *ws, cudaStream_t s) {
     void *ptrs[] = {ws->w, ws->pr, ws->live0, ws->live1, ws->stage_id, ws->stage_start, ws->stage_off,
                     ws->fstart, ws->fbase, ws->cstart, ws->part, ws->ctl, ws->tr_f_hi, ws->tr_f_lo,
                     ws->tr_size, ws->tr_peeled, ws->loc, ws->tdeg, ws->tlrp, ws->tcnt, ws->tfill,
-                    ws->tcol, ws->tcw, ws->mask};
+                    ws->tgrp, ws->tcol, ws->tcw, ws->mask};
     for (void *q : ptrs) {
         if (!q) continue;
         if (ws->async) cudaFreeAsync(q, s);
@@ -1466,6 +1488,7 @@ PeelWorkspace *workspace_create(long long n, long long arcs, bool has_cw, const 
     A(&ws->tlrp, tail_cap + 1);
     A(&ws->tcnt, tail_cap + 1);
     A(&ws->tfill, tail_cap + 1);
+    A(&ws->tgrp, (tail_cap + 1) * DUPIN_GRP_STRIDE);
     A(&ws->tcol, ws->tarc_cap);
     if (has_cw) A(&ws->tcw, ws->tarc_cap);
     A(&ws->mask, n);
@@ -1607,6 +1630,8 @@ static PeelArgs make_args(const dupin_graph *g, const PeelWorkspace *ws, const d
     A.tcol = ws->tcol;
     A.tcw = p->metric == DUPIN_DG ? nullptr : ws->tcw;
     A.tarc_cap = ws->tarc_cap;
+    A.tgrp = ws->tgrp;
+    A.cl_c = plan.cl_cap > 0 ? cluster_ctas() : 0;
     return A;
 }
 
@@ -1679,12 +1704,15 @@ int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_par
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[4], s));
         DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tcnt, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
         DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tfill, 0, sizeof(int) * (size_t)(tail_cap + 1), s));
+        if (A.cl_c > 0)
+            DUPIN_CUDA_TRY(cudaMemsetAsync(ws->tgrp, 0, sizeof(unsigned) * (size_t)(tail_cap + 1) * DUPIN_GRP_STRIDE, s));
         k_tail_prep<<<sms * 2, 256, 0, s>>>(A);
         k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A, ws->tdeg, nullptr);
         k_tail_arcs<0><<<sms * 2, BULK_THREADS, 0, s>>>(A);
         // tcnt -> tlrp
         PeelArgs A2 = A;
         k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A2, ws->tlrp, ws->tcnt);
+        if (A.cl_c > 0) k_tail_grp<<<sms, 256, 0, s>>>(A);
         k_tail_arcs<1><<<sms * 2, BULK_THREADS, 0, s>>>(A);
         if (timing) DUPIN_CUDA_TRY(cudaEventRecord(ws->ev[5], s));
     }
