@@ -374,12 +374,14 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
         for (int q = tid; q < nsl; q += CL_THREADS) mn = segmin[q] < mn ? segmin[q] : mn;
         mn = block_min64(mn, S.red_mn);
         if (mn != kMaxLL) {
-            for (int q0 = wid * 32; q0 < nsl; q0 += CL_THREADS) {  // warp-uniform
+            unsigned k = 0;  // rank of the next segment at the minimum (the same in every warp)
+            for (int q0 = 0; q0 < nsl; q0 += 32) {  // every warp finds every such segment ...
                 const int q = q0 + lane;
                 unsigned cm = __ballot_sync(0xffffffffu, q < nsl && segmin[q] == mn);
                 while (cm) {
                     const int qq = q0 + __ffs(cm) - 1;
                     cm &= cm - 1;
+                    if ((k++ & (CL_WARPS - 1)) != (unsigned)wid) continue;  // ... and scans its share
                     const long long p = (long long)qq * 64 + 2 * lane;
                     const longlong2 v = *(const longlong2 *)&tw[p];
                     const bool s0 = v.x == mn, s1 = v.y == mn;
@@ -391,10 +393,10 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
                     unsigned base = 0;
                     if (lane == 0) {
                         base = atomicAdd(&S.nspec, (unsigned)(__popc(b0) + __popc(b1)));
-                        const unsigned k = atomicAdd(&S.nseg, 1u);
-                        if (k < CL_SPEC) {
-                            S.myseg[k] = qq;
-                            S.myalt[k] = m;
+                        const unsigned j = atomicAdd(&S.nseg, 1u);
+                        if (j < CL_SPEC) {
+                            S.myseg[j] = qq;
+                            S.myalt[j] = m;
                         }
                     }
                     base = __shfl_sync(0xffffffffu, base, 0);
@@ -472,8 +474,8 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
     // CTA sends after its wait for round i: phases never overlap.
     unsigned phase = 0;  // bit b: parity of mbarrier b's current phase
     int werr = 0;
-    auto expect = [&](int pb) {
-        if (tid == 0) mb_arrive_expect_tx(&S.mb[pb], (unsigned)(C * sizeof(ClRes)));
+    auto expect = [&](int pb) {  // warp 1: warp 0's loads in flight need not complete first
+        if (tid == 32) mb_arrive_expect_tx(&S.mb[pb], (unsigned)(C * sizeof(ClRes)));
     };
     auto wait_results = [&](int pb) {
         int bad = 0;
@@ -499,6 +501,28 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
     cl_sync();  // every CTA's mbarriers are set up before any push
     publish((int)(st.round & 1), 0, 0);
     wait_results((int)(st.round & 1));
+    // Warp 0, after a round's results: should the next round take the
+    // minimum rule, its list is every CTA's vertices at the minimum Mn; lane
+    // q (a CTA at Mn) loads the bounds of its entries' groups for this CTA
+    // now, so that the loads are in flight while the round closes (nothing
+    // here waits for them).
+    bool pre = false;
+    unsigned pc = 0, ptot = 0, pg0[CL_PUSH], pg1[CL_PUSH];
+    auto preload = [&](int pb, long long Mn, bool over) {
+        if (wid != 0) return;
+        pc = lane < (int)C && S.res[pb][lane].mn == Mn ? (unsigned)S.res[pb][lane].scnt : 0;
+        ptot = __reduce_add_sync(0xffffffffu, pc);
+        pre = !over && ptot <= 32;
+        if (!pre) return;
+#pragma unroll
+        for (int e = 0; e < CL_PUSH; e++) {
+            if ((unsigned)e < pc) {
+                const unsigned *gr = A.tgrp + (size_t)S.res[pb][lane].spec[e] * DUPIN_GRP_STRIDE + r;
+                pg0[e] = __ldg(gr);
+                pg1[e] = __ldg(gr + 1);
+            }
+        }
+    };
     TailRound R;
     bool fast;
     {
@@ -506,8 +530,10 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
         bool over;
         unsigned long long il, ih;
         results((int)(st.round & 1), m0, over, il, ih);
+        preload((int)(st.round & 1), m0, over);
         R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, m0);
         fast = R.minrule && !over;
+        pre = pre && fast;
     }
     int err = werr;
     while (!R.done && !err) {
@@ -519,16 +545,81 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
         const int par = (int)(i & 1), ppar = par ^ 1;
         expect(par);
         unsigned long long Wl = 0, Wh = 0;  // sum of the removed vertices' weights
+        // entry g of the round's list (CTA by CTA) -> its local id
+        auto entry = [&](unsigned g) -> unsigned {
+            int q = 0;  // the last CTA whose entries start at or before g
+            for (int step = 8; step > 0; step >>= 1)
+                if (q + step < (int)C && S.qcex[q + step] <= g) q += step;
+            const unsigned e = g - S.qcex[q];
+            if (fast) return S.res[ppar][q].spec[e];
+            if (S.qcnt[q] <= CL_INL) return S.inl[q][e];
+            return cl_ld_u16(cl_map(lst, q) + 2 * e) * C + q;
+        };
+        // the group bounds of entry g's row for this CTA
+        auto group = [&](unsigned g, unsigned &gs, unsigned &len) {
+            const unsigned p = entry(g);
+            const unsigned *gr = A.tgrp + (size_t)p * DUPIN_GRP_STRIDE + r;
+            gs = gr[0];
+            len = gr[1] - gs;
+        };
+        // warp 0: the window of list entries [w0, w0 + nw), nw <= 32: each
+        // entry's group start and the prefix of the group lengths
+        auto build_window = [&](unsigned w0, unsigned nw) {
+            unsigned gs = 0, len = 0;
+            if (lane < (int)nw) group(w0 + lane, gs, len);
+            unsigned incl = len;
+#pragma unroll
+            for (int k = 1; k < 32; k <<= 1) {
+                const unsigned o = __shfl_up_sync(0xffffffffu, incl, k);
+                if (lane >= k) incl += o;
+            }
+            if (lane < (int)nw) {
+                S.wbase[lane] = incl - len;
+                S.wstart[lane] = gs;
+            }
+            if (lane == 31) S.wbase[nw] = incl;
+        };
         if (fast) {
             // U_i: the vertices at the minimum weight, listed by the CTAs that
             // hold it with the previous round's results; each marks its own
-            if (S.res[ppar][r].mn == R.minw) {
+            if (wid > 0 && S.res[ppar][r].mn == R.minw) {  // warp 0 builds the list's window meanwhile
                 const unsigned ns = (unsigned)S.res[ppar][r].scnt;
                 const unsigned ng = S.nseg < ns ? S.nseg : ns;
-                for (unsigned e = tid; e < ns; e += CL_THREADS) tw[S.myslot[e]] = -i;
-                for (unsigned k = tid; k < ng; k += CL_THREADS) segmin[S.myseg[k]] = S.myalt[k];
+                for (unsigned e = tid - 32; e < ns; e += CL_THREADS - 32) tw[S.myslot[e]] = -i;
+                for (unsigned k = tid - 32; k < ng; k += CL_THREADS - 32) segmin[S.myseg[k]] = S.myalt[k];
             }
-            if (wid == 0) {
+            if (wid == 0 && pre) {  // the list and its group bounds, loaded while round i-1 closed
+                unsigned len[CL_PUSH], tot = 0;
+#pragma unroll
+                for (int e = 0; e < CL_PUSH; e++) {
+                    len[e] = (unsigned)e < pc ? pg1[e] - pg0[e] : 0u;
+                    tot += len[e];
+                }
+                unsigned ic = pc, it = tot;
+#pragma unroll
+                for (int k = 1; k < 32; k <<= 1) {
+                    const unsigned oc = __shfl_up_sync(0xffffffffu, ic, k), ot = __shfl_up_sync(0xffffffffu, it, k);
+                    if (lane >= k) {
+                        ic += oc;
+                        it += ot;
+                    }
+                }
+                const unsigned exc = ic - pc;
+                if (lane < (int)C) {
+                    S.qcnt[lane] = pc;
+                    S.qcex[lane] = exc;
+                }
+                unsigned run = it - tot;
+#pragma unroll
+                for (int e = 0; e < CL_PUSH; e++) {
+                    if ((unsigned)e < pc) {
+                        S.wbase[exc + e] = run;
+                        S.wstart[exc + e] = pg0[e];
+                        run += len[e];
+                    }
+                }
+                if (lane == 31) S.wbase[ptot] = it;
+            } else if (wid == 0) {
                 const unsigned c =
                     lane < (int)C && S.res[ppar][lane].mn == R.minw ? (unsigned)S.res[ppar][lane].scnt : 0;
                 unsigned ic = c;
@@ -541,6 +632,9 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
                     S.qcnt[lane] = c;
                     S.qcex[lane] = ic - c;
                 }
+                __syncwarp();
+                const unsigned Un = __shfl_sync(0xffffffffu, ic, 31);
+                if (Un <= 32) build_window(0, Un);  // the list's only window, before the barrier below
             }
             __syncthreads();
             const unsigned Un = S.qcex[C - 1] + S.qcnt[C - 1];
@@ -660,28 +754,12 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
         // ---- E: this CTA's groups of the removed vertices' arcs
         const unsigned Ltot = S.qcex[C - 1] + S.qcnt[C - 1];
         unsigned long long ilo = 0, ihi = 0;
-        // entry g of the round's list (CTA by CTA) -> its local id
-        auto entry = [&](unsigned g) -> unsigned {
-            int q = 0;  // the last CTA whose entries start at or before g
-            for (int step = 8; step > 0; step >>= 1)
-                if (q + step < (int)C && S.qcex[q + step] <= g) q += step;
-            const unsigned e = g - S.qcex[q];
-            if (fast) return S.res[ppar][q].spec[e];
-            if (S.qcnt[q] <= CL_INL) return S.inl[q][e];
-            return cl_ld_u16(cl_map(lst, q) + 2 * e) * C + q;
-        };
-        // the group bounds of entry g's row for this CTA
-        auto group = [&](unsigned g, unsigned &gs, unsigned &len) {
-            const unsigned p = entry(g);
-            const unsigned *gr = A.tgrp + (size_t)p * DUPIN_GRP_STRIDE + r;
-            gs = gr[0];
-            len = gr[1] - gs;
-        };
         // arcs into vertices this CTA owns: a survivor loses c (a returning
         // 64-bit shared-memory atomic; the segment minimum lowered by
-        // atomicMin), an arc into U_i adds c to 'internal', an arc into an
-        // earlier round's removals is skipped.  The heads' states are read
-        // before any update (removal marks do not change during the expand).
+        // atomicMin when the result falls below it), an arc into U_i adds c
+        // to 'internal', an arc into an earlier round's removals is skipped.
+        // The heads' states are read before any update (removal marks do not
+        // change during the expand).
         auto arcs = [&](const long long (&pos)[CL_ILP]) {
             int cv[CL_ILP];
             long long cc[CL_ILP], wv[CL_ILP];
@@ -709,31 +787,19 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
                     const unsigned sl = (unsigned)cv[u] >> lg;
                     const long long nv =
                         (long long)atomicAdd((unsigned long long *)&tw[sl], (unsigned long long)(-cc[u])) - cc[u];
-                    atomicMin(&segmin[sl >> 6], nv);
+                    if (nv < segmin[sl >> 6]) atomicMin(&segmin[sl >> 6], nv);  // segment minima only fall here
                 } else if (wv[u] == -i) {
                     if (NARROW) ilo += (unsigned long long)cc[u];
                     else add128(ilo, ihi, (unsigned long long)cc[u], 0);
                 }
             }
         };
+        const bool built = fast && Ltot <= 32;  // the fast path built the only window
         for (unsigned w0 = 0; w0 < Ltot; w0 += CL_WIN) {  // block-uniform: a window of list entries
             const unsigned nw = Ltot - w0 < CL_WIN ? Ltot - w0 : CL_WIN;
-            if (nw <= 32) {
-                if (wid == 0) {
-                    unsigned gs = 0, len = 0;
-                    if (lane < (int)nw) group(w0 + lane, gs, len);
-                    unsigned incl = len;
-#pragma unroll
-                    for (int k = 1; k < 32; k <<= 1) {
-                        const unsigned o = __shfl_up_sync(0xffffffffu, incl, k);
-                        if (lane >= k) incl += o;
-                    }
-                    if (lane < (int)nw) {
-                        S.wbase[lane] = incl - len;
-                        S.wstart[lane] = gs;
-                    }
-                    if (lane == 31) S.wbase[nw] = incl;
-                }
+            if (built) {
+            } else if (nw <= 32) {
+                if (wid == 0) build_window(w0, nw);
             } else {
                 unsigned carry = 0;
                 for (unsigned t0 = 0; t0 < nw; t0 += CL_THREADS) {
@@ -750,7 +816,7 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
                 }
                 if (tid == 0) S.wbase[nw] = carry;
             }
-            __syncthreads();
+            if (!built) __syncthreads();
             const unsigned wt = S.wbase[nw];
             for (unsigned xb = tid; xb < wt; xb += CL_ILP * CL_THREADS) {
                 long long pos[CL_ILP];
@@ -783,15 +849,7 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
         bool over;
         unsigned long long Il, Ih;
         results(par, Mn, over, Il, Ih);
-        if (wid == 0) {
-            // should round i+1 take the minimum rule, its list is the CTAs at
-            // Mn: their group bounds for this CTA are prefetched into L1 now,
-            // while the round closes
-            const unsigned c = lane < (int)C && S.res[par][lane].mn == Mn ? (unsigned)S.res[par][lane].scnt : 0;
-            if (!over && c > 0)
-                for (unsigned e = 0; e < c; e++)
-                    prefetch_l1(A.tgrp + (size_t)S.res[par][lane].spec[e] * DUPIN_GRP_STRIDE + r);
-        }
+        preload(par, Mn, over);
         const long long Un = (long long)Ltot;
         const u128 wsel = mk128(Wl, Wh), internal = mk128(Il, Ih);
         st.f = st.f - (wsel - (internal >> 1));
@@ -816,6 +874,7 @@ __device__ __forceinline__ void cluster_body(const PeelArgs &A, const int P, uns
         }
         R = tail_plan<NARROW>(A.kD, A.D, A.use_min, A.gpo, A.lpo, st, Mn);
         fast = R.minrule && !over;
+        pre = pre && fast;
     }
     if (tid == 0 && S.err) set_error(ctl, S.err);
     // peel rounds of this CTA's vertices
