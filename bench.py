@@ -255,23 +255,41 @@ def bench_serving(dupin, args, requests=2000, rate=2000.0):
     graph_of = lambda w: gbig[w[1]] if w[0] == "big" else gpool[w[1]]
 
     def run(paced: bool):
+        """Submit every request (at its Poisson arrival time when paced); the
+        client polls its outstanding tickets between submissions, so each
+        request's latency as the client sees it is recorded too."""
         srv = dupin.Server(memory_budget=16 << 30, max_slots=8)
-        tickets = []
+        pend, outs, lat = {}, [None] * requests, [0.0] * requests
+
+        def sweep():
+            for t, (j, ts) in list(pend.items()):
+                if srv.poll(t)[0]:
+                    lat[j] = (time.perf_counter() - ts) * 1e3
+                    outs[j] = (which[j], srv.wait(t))
+                    del pend[t]
+
         t0 = time.perf_counter()
         for j in range(requests):
-            if paced:
-                dt = arrivals[j] - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-            tickets.append((which[j], srv.submit(graph_of(which[j]), p, want_rounds=True)))
-        outs = [(w, srv.wait(t)) for w, t in tickets]
+            while paced and arrivals[j] > time.perf_counter() - t0:
+                sweep()
+            pend[srv.submit(graph_of(which[j]), p, want_rounds=True)] = (j, time.perf_counter())
+        while pend:
+            sweep()
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
-        return outs, wall, st
+        return outs, wall, st, lat
 
-    outs, wall, st = run(True)
-    outs_sat, wall_sat, st_sat = run(False)
+    def by_class(lat):
+        out = {}
+        for cls in ("pool", "big"):
+            x = np.array([lat[j] for j in range(requests) if which[j][0] == cls])
+            out["windows" if cls == "pool" else "rmat21"] = {
+                "requests": int(x.size), "p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99))}
+        return out
+
+    outs, wall, st, lat = run(True)
+    outs_sat, wall_sat, st_sat, lat_sat = run(False)
     # every result equals the graph's own peel alone, and each distinct graph's equals the oracle's
     ref, orc = {}, {}
     mismatch = omis = 0
@@ -290,10 +308,11 @@ def bench_serving(dupin, args, requests=2000, rate=2000.0):
         g.free()
     return {"workload": f"{requests} requests, Poisson {rate:.0f}/s, 256 windows + 1% on 2 R-MAT-21 (ef 10) graphs",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "graphs_per_s": requests / wall,
+            "client_latency_by_class": by_class(lat),
             "completed": st["completed"], "mismatches_vs_alone": mismatch, "oracle_mismatches": omis,
             "oracle_graphs_checked": len(orc),
             "saturation": {"graphs_per_s": requests / wall_sat, "p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"],
-                           "how": "the same requests submitted at once"}}
+                           "client_latency_by_class": by_class(lat_sat), "how": "the same requests submitted at once"}}
 
 
 def cpu_baseline(g, metric, eps, k):
@@ -667,7 +686,11 @@ def main():
         cpu = cpu_baseline(g, metric_b, eps_b, k)
         cpu_par = cpu_parallel_baseline(g, metric_b, eps_b, k)
 
-    launches_per_peel = 14  # reset, init x4, bulk, tail build x5, one-CTA tail, cluster tail
+    # kernels per peel: control reset, initial weights (DG: one kernel; FD/DW: three), the
+    # set-up's finish, the grid-wide rounds, the tail build (prep, two scans, two arc passes,
+    # owner groups), the one-CTA tail and the cluster tail (one of the two returns at once),
+    # and the final mask
+    launches_per_peel = {"dg": 13, "fd": 15, "dw": 15}
     line = {
         "metric": "edges peeled/s", "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -682,7 +705,7 @@ def main():
         "cpu_baseline": cpu,
         "cpu_parallel_baseline": cpu_par,
         "e2e": e2e,
-        "gpu_launches": launches_per_peel * len(params) * args.steps,
+        "gpu_launches": sum(launches_per_peel[m] for m, _ in peels) * args.steps,
         "clocks": clocks.summary(),
         "side": side,
         "batched": batched,
