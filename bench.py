@@ -458,7 +458,7 @@ def run_reference(args, wl, rank, world):
 
 def kernel_of(phase: str, tail_ctas: int) -> str:
     return {"init": "k_init_vertex+k_init_arcs+k_init_reduce", "bulk": "k_peel_bulk",
-            "build": "k_tail_prep+k_tail_scan+k_tail_arcs",
+            "build": "k_tail_prep+k_tail_scan+k_tail_arcs+k_tail_grp",
             "tail": "k_peel_cluster" if tail_ctas > 1 else "k_peel_tail"}[phase]
 
 

@@ -184,7 +184,7 @@ typedef struct {
  * peel on the live sub-graph -- one CTA with the state in its shared memory
  * (live sets of at most about 14,900 vertices whose sub-graph has at most
  * 2^20 arcs), or a thread-block cluster of 8 or 16 CTAs with the state
- * spread over their shared memory (live sets of up to about 160,000
+ * spread over their shared memory (live sets of up to about 195,000
  * vertices).  Both give identical results; the flags DUPIN_TAIL_ONE_CTA and
  * DUPIN_TAIL_CLUSTER force one of them.
  */
