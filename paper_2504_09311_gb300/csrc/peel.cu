@@ -958,9 +958,9 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
               [&](long long k, long long pos) {
                   const int v = arc_head(col[pos], hubs);
                   if (pr[v] != DUPIN_LIVE) return;
-                  if (PASS == 0) {
-                      atomicAdd(&A.tcnt[k], 1);
+                  if (PASS == 0) {  // per row (per row and owner for the cluster; k_tail_rowcnt adds them up)
                       if (grp) atomicAdd(&A.tgrp[k * DUPIN_GRP_STRIDE + 1 + (A.loc[v] & (A.cl_c - 1))], 1u);
+                      else atomicAdd(&A.tcnt[k], 1);
                   } else {
                       const long long slot =
                           grp ? (long long)atomicAdd(&A.tgrp[k * DUPIN_GRP_STRIDE + 1 + (A.loc[v] & (A.cl_c - 1))], 1u)
@@ -969,6 +969,19 @@ __global__ void __launch_bounds__(BULK_THREADS) k_tail_arcs(PeelArgs A) {
                       if (A.tcw) A.tcw[slot] = cw ? cw[pos] : DUPIN_Q_ONE;
                   }
               });
+}
+
+// For the cluster tail: each row's live-arc count, from its owner groups' counts
+__global__ void k_tail_rowcnt(PeelArgs A) {
+    const PeelCtl *c = A.ctl;
+    if (c->status != ST_CLUSTER || c->error || A.tgrp == nullptr || A.cl_c <= 0) return;
+    const long long L = c->live_len;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < L; k += (long long)gridDim.x * blockDim.x) {
+        const unsigned *g = A.tgrp + k * DUPIN_GRP_STRIDE + 1;
+        unsigned t = 0;
+        for (int o = 0; o < A.cl_c; o++) t += g[o];
+        A.tcnt[k] = (int)t;
+    }
 }
 
 // For the cluster tail: each row's owner-group counts become the groups' first
@@ -1711,6 +1724,7 @@ int enqueue_peel_stages(const dupin_graph *g, PeelWorkspace *ws, const dupin_par
         k_tail_prep<<<sms * 2, 256, 0, s>>>(A);
         k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A, ws->tdeg, nullptr);
         k_tail_arcs<0><<<sms * 2, BULK_THREADS, 0, s>>>(A);
+        if (A.cl_c > 0) k_tail_rowcnt<<<sms, 256, 0, s>>>(A);
         // tcnt -> tlrp
         PeelArgs A2 = A;
         k_tail_scan<<<1, SCAN_THREADS, 0, s>>>(A2, ws->tlrp, ws->tcnt);
