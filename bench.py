@@ -462,7 +462,7 @@ def run_reference(args, wl, rank, world):
 
 def kernel_of(phase: str, tail_ctas: int) -> str:
     return {"init": "k_init_vertex+k_init_arcs+k_init_reduce", "bulk": "k_peel_bulk",
-            "build": "k_tail_prep+k_tail_scan+k_tail_arcs+k_tail_grp",
+            "build": "k_tail_prep+k_tail_scan+k_tail_arcs+k_tail_rowcnt+k_tail_grp",
             "tail": "k_peel_cluster" if tail_ctas > 1 else "k_peel_tail"}[phase]
 
 
@@ -695,9 +695,9 @@ def main():
 
     # kernels per peel: control reset, initial weights (DG: one kernel; FD/DW: three), the
     # set-up's finish, the grid-wide rounds, the tail build (prep, two scans, two arc passes,
-    # owner groups), the one-CTA tail and the cluster tail (one of the two returns at once),
-    # and the final mask
-    launches_per_peel = {"dg": 13, "fd": 15, "dw": 15}
+    # row counts and owner groups), the one-CTA tail and the cluster tail (one of the two
+    # returns at once), and the final mask
+    launches_per_peel = {"dg": 14, "fd": 16, "dw": 16}
     line = {
         "metric": "edges peeled/s", "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
