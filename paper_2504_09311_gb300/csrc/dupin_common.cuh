@@ -69,6 +69,11 @@ struct PeelCtl {
     long long init_min;
     int init_overflow;
     int tail_ctas;  // CTAs of the tail that finished the peel (0: none ran)
+    // loading checks (the initial-weight pass with its checks on): a row not
+    // strictly increasing, and the symmetry fingerprint (0 when symmetric)
+    int check_unsorted;
+    int pad1;
+    unsigned long long check_fp;
 };
 
 // Per-block partial results of one bulk round (one 128-byte line each)
@@ -104,6 +109,7 @@ struct DevGraph {
     const long long *a;   // nullptr: 0
     const int *hubs;      // hub number -> vertex id
     int n_hubs;
+    unsigned long long key;  // the symmetry fingerprint's key (loading checks only)
 };
 
 // neighbour id of an arc's stored column value

@@ -144,31 +144,6 @@ __global__ void k_encode_hub_arcs(int *col, long long arcs, const int *slot_of) 
     }
 }
 
-// Every row strictly increasing (flags[0] = 1 otherwise) and the symmetry
-// fingerprint sum over arcs u -> v of sym_mix(u, v, c) - sym_mix(v, u, c)
-// (flags + 2, a wrapping 64-bit sum: 0 for a symmetric adjacency).  One warp
-// per row, lanes striding over its arcs.
-__global__ void k_check_rows(const long long *rp, const int *col, const long long *cw, long long n,
-                             unsigned long long key, int *flags) {
-    const int lane = threadIdx.x & 31;
-    const long long W = (long long)gridDim.x * (blockDim.x >> 5);
-    unsigned long long fp = 0;
-    bool bad = false;
-    for (long long u = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += W) {
-        const long long b = rp[u], e = rp[u + 1];
-        for (long long p = b + lane; p < e; p += 32) {
-            const int v = col[p];
-            if (p + 1 < e && col[p + 1] <= v) bad = true;
-            const long long c = cw ? cw[p] : DUPIN_Q_ONE;
-            fp += sym_mix(key, u, v, c) - sym_mix(key, v, u, c);
-        }
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&flags[0], 1);
-    // wrapping sum over the warp, then one atomic per warp
-    for (int d = 16; d > 0; d >>= 1) fp += __shfl_down_sync(0xffffffffu, fp, d);
-    if (lane == 0 && fp) atomicAdd((unsigned long long *)(flags + 2), fp);
-}
-
 __global__ void k_fill_i32(int *x, long long n, int v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         x[i] = v;
@@ -379,6 +354,7 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
         }
         dg.cw = has_w ? g->cw : unit;
         dg.a = g->a;
+        dg.key = fingerprint_key();
         rc = DUPIN_OK;
         if (e == cudaSuccess && dg.cw) rc = launch_init_weights(dg, DUPIN_DW, w, nullptr, nullptr, ctl, true, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s);
@@ -400,27 +376,12 @@ extern "C" int dupin_graph_load(const dupin_graph_desc *d, void *stream, dupin_g
                               "invalid graph: a neighbour id out of range, a self-loop, a negative weight, or a "
                               "peeling weight >= 2^63");
         }
-    }
-    // sorted rows without repeats, and symmetry (ids are in range by now)
-    if (arcs > 0) {
-        int *fl = nullptr;
-        TRY(galloc((void **)&fl, 16, s));
-        e = cudaMemsetAsync(fl, 0, 16, s);
-        if (e == cudaSuccess) {
-            k_check_rows<<<sms * 8, 256, 0, s>>>(g->rp, g->col, g->cw, n, fingerprint_key(), fl);
-            e = cudaGetLastError();
-        }
-        int hf[4] = {0, 0, 0, 0};
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hf, fl, 16, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        gfree(fl, s);
-        TRY(e);
-        unsigned long long fp = 0;
-        memcpy(&fp, hf + 2, sizeof(fp));
-        if (hf[0] || fp) {
+        // sorted rows without repeats, and symmetry: checked in the same pass
+        // (k_init_arcs with its checks on), read here once the ids are known valid
+        if (arcs > 0 && (hc.check_unsorted || hc.check_fp)) {
             graph_release(g);
             gfree(bad, s);
-            if (hf[0])
+            if (hc.check_unsorted)
                 return dupin_fail(DUPIN_ERR_INVALID_ARG, "invalid graph: a row's neighbour ids are not strictly "
                                                          "increasing (unsorted, or a repeated pair)");
             return dupin_fail(DUPIN_ERR_INVALID_ARG,

@@ -84,7 +84,7 @@ __global__ void k_init_vertex(DevGraph g, int dg, long long *w, int *pr, int *li
 // R-MAT-24 than the default budget).  CHECK also validates ids, self-loops
 // and int64 overflow.
 template <bool CHECK>
-__global__ void __launch_bounds__(INIT_THREADS, 6) k_init_arcs(DevGraph g, long long *w, PeelCtl *ctl) {
+__global__ void __launch_bounds__(INIT_THREADS, CHECK ? 1 : 6) k_init_arcs(DevGraph g, long long *w, PeelCtl *ctl) {
     const int lane = threadIdx.x & 31;
     const long long NW = (long long)gridDim.x * INIT_WARPS;
     const long long W = blockIdx.x * (long long)INIT_WARPS + (threadIdx.x >> 5);
@@ -95,6 +95,29 @@ __global__ void __launch_bounds__(INIT_THREADS, 6) k_init_arcs(DevGraph g, long 
     long long r = warp_search_last_le(g.rp, n, we0);  // row of the first arc
     long long carry_own = -1, carry_val = 0;
     bool bad = false;
+    // CHECK: rows strictly increasing (each arc against the next, across
+    // chunks through the last arc seen, across warps through the arc before
+    // the range) and the symmetry fingerprint
+    bool unsorted = false;
+    unsigned long long fp = 0;
+    long long prev_row = -1;
+    int prev_col = 0;
+    if (CHECK && g.rp[r] < we0) {  // the range starts inside row r: compare with the arc before it
+        prev_row = r;
+        prev_col = g.col[we0 - 1];
+    }
+    auto check_chunk = [&](const long long own, const int cvx, const long long val, const long long x,
+                           const bool valid) {
+        const int ncol = __shfl_down_sync(0xffffffffu, cvx, 1);
+        const long long nown = __shfl_down_sync(0xffffffffu, own, 1);
+        if (valid && lane < 31 && x + 1 < we1 && nown == own && ncol <= cvx) unsorted = true;
+        if (lane == 0 && valid && own == prev_row && cvx <= prev_col) unsorted = true;
+        if (valid) fp += sym_mix(g.key, own, cvx, val) - sym_mix(g.key, cvx, own, val);
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        const int lst = 31 - __clz(vm);
+        prev_row = __shfl_sync(0xffffffffu, own, lst);
+        prev_col = __shfl_sync(0xffffffffu, cvx, lst);
+    };
     long long r_end = g.rp[r + 1];  // end of row r
     long long lacc = 0;             // per-lane partial sum of row r over whole-row chunks
     // one 32-arc chunk whose weights (and, with CHECK, heads) are already loaded
@@ -107,6 +130,7 @@ __global__ void __launch_bounds__(INIT_THREADS, 6) k_init_arcs(DevGraph g, long 
         // fast path: the whole chunk lies in row r (long rows, hubs)
         const long long cend = x0 + 32 < we1 ? x0 + 32 : we1;
         if (cend <= r_end) {
+            if (CHECK) check_chunk(r, cvx, val, x, valid);
             if (CHECK && valid && cvx == r) bad = true;  // self-loop
             if (CHECK && (unsigned long long)lacc + (unsigned long long)val < (unsigned long long)lacc) bad = true;
             lacc += val;
@@ -152,6 +176,7 @@ __global__ void __launch_bounds__(INIT_THREADS, 6) k_init_arcs(DevGraph g, long 
             rr += 32;
         }
         if (CHECK && valid && cvx == owner) bad = true;
+        if (CHECK) check_chunk(owner, cvx, val, x, valid);
         // segmented inclusive scan by owner
         long long sv = val;
 #pragma unroll
@@ -233,6 +258,11 @@ __global__ void __launch_bounds__(INIT_THREADS, 6) k_init_arcs(DevGraph g, long 
         }
     }
     if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&ctl->init_overflow, 1);
+    if (CHECK) {
+        if (__any_sync(0xffffffffu, unsorted) && lane == 0) atomicExch(&ctl->check_unsorted, 1);
+        for (int d = 16; d > 0; d >>= 1) fp += __shfl_down_sync(0xffffffffu, fp, d);  // wrapping sum
+        if (lane == 0 && fp) atomicAdd(&ctl->check_fp, fp);
+    }
 }
 
 // sum over u of (w_u + a_u) and min w (DW/FD)
