@@ -98,62 +98,10 @@ __device__ __forceinline__ uint32_t cl_map(const void *p, unsigned rank) {
     return o;
 }
 
-__device__ __forceinline__ long long cl_ld_s64(uint32_t a) {
-    long long v;
-    asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long cl_ld_u64(uint32_t a) {
-    unsigned long long v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned cl_ld_u32(uint32_t a) {
-    unsigned v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ unsigned cl_ld_u16(uint32_t a) {
     unsigned short v;
     asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
     return v;
-}
-
-__device__ __forceinline__ unsigned long long cl_atom_add_u64(uint32_t a, unsigned long long x) {
-    unsigned long long v;
-    asm volatile("atom.shared::cluster.add.u64 %0, [%1], %2;" : "=l"(v) : "r"(a), "l"(x) : "memory");
-    return v;
-}
-
-// Largest k in [0, U] with le(k) true, for a predicate that is true on a
-// prefix of [0, U] and at k = 0.  One warp, 32 probes per step.
-template <class LeF>
-__device__ __forceinline__ long long warp_search_last_le_fn(long long U, LeF le) {
-    const int lane = threadIdx.x & 31;
-    long long lo = 0, hi = U;
-    while (lo < hi) {
-        const long long span = hi - lo;  // candidates lo+1 .. hi
-        long long p;
-        if (span <= 32) p = lo + 1 + lane;
-        else p = lo + 1 + (long long)(((unsigned long long)(span - 1) * (unsigned)lane) / 31u);
-        const bool valid = p <= hi;
-        const bool ok = valid && le(p);
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (m == 0) {
-            hi = __shfl_sync(0xffffffffu, p, 0) - 1;
-        } else {
-            const int Lh = 31 - __clz(m);
-            const long long pl = __shfl_sync(0xffffffffu, p, Lh);
-            const long long pn = __shfl_sync(0xffffffffu, p, Lh < 31 ? Lh + 1 : 31);
-            const bool nvalid = __shfl_sync(0xffffffffu, (int)valid, Lh < 31 ? Lh + 1 : 31);
-            lo = pl;
-            if (Lh < 31 && nvalid) hi = pn - 1;
-        }
-    }
-    return lo;
 }
 
 // ------------------------------------------------------------ shared state
@@ -167,10 +115,9 @@ struct ClSel {
     unsigned long long w_lo, w_hi;  // sum of their weights
 };
 
-// One CTA's results of a round, pushed into every CTA's inbox before the
-// round's last barrier (double-buffered by round parity).
-// (64 bytes: four 16-byte asynchronous stores that complete on the
-// receiver's mbarrier)
+// One CTA's results of a round, pushed into every CTA's inbox at the round's
+// end (double-buffered by round parity): 64 bytes, four 16-byte asynchronous
+// stores that complete on the receiver's mbarrier.
 struct __align__(16) ClRes {
     unsigned long long i_lo, i_hi;  // sum of c over the arcs it expanded that end inside U_i
     long long mn;                   // minimum weight of its live vertices after the round (kMaxLL: none)
@@ -215,22 +162,8 @@ __device__ __forceinline__ long long block_min64(long long x, long long *s) {
     return m;
 }
 
-__device__ __forceinline__ long long cl_cas_b64(uint32_t a, long long cmp, long long x) {
-    long long v;
-    asm volatile("atom.shared::cluster.cas.b64 %0, [%1], %2, %3;" : "=l"(v) : "r"(a), "l"(cmp), "l"(x) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void cl_st_u32(uint32_t a, unsigned x) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(x) : "memory");
-}
-
-__device__ __forceinline__ void cl_st_v2u64(uint32_t a, unsigned long long x, unsigned long long y) {
-    asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(x), "l"(y) : "memory");
-}
-
-__device__ __forceinline__ void cl_st_v4u32(uint32_t a, unsigned x, unsigned y, unsigned z, unsigned w) {
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 
 // 16 bytes into another CTA's shared memory, completing (as 16 transaction
@@ -268,9 +201,6 @@ __device__ __forceinline__ bool mb_try_wait(unsigned long long *mb, unsigned par
         : "memory");
     return done != 0;
 }
-
-// L1 prefetch of the line holding p (no data returned)
-__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 __device__ __forceinline__ void cl_st_u64(uint32_t a, unsigned long long x) {
     asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(x) : "memory");
