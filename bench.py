@@ -4,7 +4,7 @@
 Default workload (the largest single-GPU configuration): an undirected R-MAT
 graph of scale 24 (16,777,216 vertices, 16 * 2^24 draws with a = 0.57,
 b = c = 0.19, self-loops dropped and pairs merged: 260,377,346 edges) with
-Fraudar weights c = 1/ln(d_obj + 5) in Q32.32, peeled with the DG and the FD
+Fraudar weights c = 1/ln(d_obj + 5) in Q32.32, peeled with the FD and the DG
 metric at the threshold (1 + eps) g(S) (k_mult = 1, eps = 1/10).  One step =
 the two peels of the whole hot path (initial weights, grid-wide rounds, tail
 sub-graph, tail rounds on one CTA or a thread-block cluster) in one batched
