@@ -739,6 +739,8 @@ static int peel_large_concurrent(dupin_graph *const *graphs, const dupin_params 
             rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BULK, s, nullptr,
                                      grid > 0 ? grid : 1);
             if (rc) break;
+            // the later peels' grid-wide rounds run narrow beside this one's tail if it is a cluster
+            for (size_t q2 = q + 1; q2 < k; q2++) enqueue_note_cluster(ws[q], ws[q2], s);
         }
         rc = enqueue_peel_stages(graphs[idx[q]], ws[q], &params[idx[q]], plans[q], PEEL_BUILD, s);
         if (rc) break;

@@ -72,7 +72,7 @@ struct PeelCtl {
     // loading checks (the initial-weight pass with its checks on): a row not
     // strictly increasing, and the symmetry fingerprint (0 when symmetric)
     int check_unsorted;
-    int pad1;
+    int beside_cluster;  // a batched call's earlier peel is on a cluster tail: the grid-wide rounds run narrow
     unsigned long long check_fp;
 };
 

@@ -132,6 +132,8 @@ int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStrea
 // its CTAs per cluster, and its launch (the kernel returns at once unless the
 // peel's status says the cluster finishes it)
 long long cluster_cap_limit();
+// records in 'next' whether 'prev' (its grid-wide rounds enqueued on s) went to the cluster tail
+void enqueue_note_cluster(const PeelWorkspace *prev, PeelWorkspace *next, cudaStream_t s);
 int cluster_ctas();
 int launch_cluster_tail(const PeelArgs &A, cudaStream_t s);
 

@@ -914,7 +914,27 @@ __device__ __forceinline__ void peel_bulk_body(const PeelArgs &A, const int b, c
     }
 }
 
-__global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) { peel_bulk_body(A, blockIdx.x, gridDim.x); }
+// Beside a cluster tail (a batched call's earlier peel) the rounds run on a
+// quarter of the launched blocks and the rest leave at once: the cluster's
+// rounds are bound by the latency of their loads, which a full-width stage's
+// memory traffic raises.  The flag is set before the launch, so every block
+// reads the same value.
+__global__ void __launch_bounds__(BULK_THREADS, 1) k_peel_bulk(PeelArgs A) {
+    unsigned G = gridDim.x;
+    if (A.ctl->beside_cluster) G = G / 4 > 0 ? G / 4 : 1;
+    if (blockIdx.x >= G) return;
+    peel_bulk_body(A, blockIdx.x, G);
+}
+
+// a later peel of a batched call learns whether this one's tail is a cluster
+// (read right after this peel's grid-wide rounds, before its tail starts)
+__global__ void k_note_cluster(const PeelCtl *prev, PeelCtl *next) {
+    if (prev->status == ST_CLUSTER) next->beside_cluster = 1;
+}
+
+void enqueue_note_cluster(const PeelWorkspace *prev, PeelWorkspace *next, cudaStream_t s) {
+    k_note_cluster<<<1, 1, 0, s>>>(prev->ctl, next->ctl);
+}
 
 // ------------------------------------------------------- (d) tail sub-graph
 
