@@ -712,7 +712,8 @@ def main():
         "cpu_baseline": cpu,
         "cpu_parallel_baseline": cpu_par,
         "e2e": e2e,
-        "gpu_launches": sum(launches_per_peel[m] for m, _ in peels) * args.steps,
+        # (+ one note per pair of the call's large peels: an earlier peel's tail kind for a later one)
+        "gpu_launches": (sum(launches_per_peel[m] for m, _ in peels) + len(peels) * (len(peels) - 1) // 2) * args.steps,
         "clocks": clocks.summary(),
         "side": side,
         "batched": batched,
