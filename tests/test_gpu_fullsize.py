@@ -10,6 +10,8 @@
   the full replay for eps = 1/20, and through the oracle's verifier for
   eps = 0 and 1/5.
 * R-MAT scale 18 (DW): bit-exact against the full replay, k = 1 and k = 2.
+* R-MAT scale 22 (FD weights): the benchmark step's batched call (FD then DG)
+  against the oracle's replay of each peel.
 * R-MAT scale 22 (DW): the verifier checks every vertex's round against the
   definitions (its peeling weight at the start of its round is at most the
   threshold recomputed from the trace, or equals the minimum), recomputes the
@@ -113,3 +115,28 @@ def test_rmat24_exact(dupin, rmat24, metric):
             assert out.tail_ctas > 1  # the rounds after the bulk phase ran in the cluster tail
     dg.free()
     og.close()
+
+
+def test_rmat22_batched_step_matches_oracle(dupin):
+    """The benchmark step's own path at scale 22: FD then DG (eps = 1/10,
+    k = 1) in one batched call -- the grid-wide stages in turn, the DG stage
+    narrowed beside the FD cluster tail, the two cluster tails side by side --
+    equals the oracle's replay of each peel."""
+    import torch
+
+    g = synth.rmat_weighted(22, 16, "fd", seed=1)
+    dg = dupin.Graph.from_synth(g)
+    params = [dupin.make_params(m, 1, (1, 10)) for m in ("fd", "dg")]
+    prs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in params]
+    mks = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for _ in params]
+    R = dupin.peel_batch_device([dg] * 2, params, prs, mks)
+    torch.cuda.synchronize()
+    for j, metric in enumerate(("fd", "dg")):
+        og = oracle.Graph.from_synth(g, metric)
+        ref = oracle.peel_batch(og, 1, (1, 10))
+        og.close()
+        assert R[j].tail_ctas > 1, metric  # the cluster tail ran
+        assert np.array_equal(prs[j].cpu().numpy(), ref.peel_round), metric
+        assert np.array_equal(mks[j].cpu().numpy(), ref.best_mask), metric
+        assert (R[j].n_rounds, R[j].best_round, R[j].best_size) == (ref.n_rounds, ref.best_round, ref.best_size)
+    dg.free()
