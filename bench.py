@@ -387,6 +387,27 @@ def round_latency(tail_ms: float, tail_rounds: float, sm_mhz: float) -> Optional
                      f"at {sm_mhz:.0f} MHz"}
 
 
+# the cluster tail's result exchange: every CTA's asynchronous stores into
+# every inbox and the wait on its own mbarrier (measured in the kernel with
+# clock64 on R-MAT-24: 0.3 us at 2,070 MHz)
+CLUSTER_EXCHANGE_CYCLES = 620
+
+
+def cluster_round_latency(tail_ms: float, tail_rounds: float, sm_mhz: float) -> Optional[dict]:
+    """The cluster tail's time per round against the latency every round pays
+    in sequence: the removed vertices' arc groups are read from L2, their
+    heads' weights updated by shared atomics whose results decide the next
+    round's minimum, and the CTAs' results exchanged before the next round."""
+    if tail_rounds <= 0 or tail_ms <= 0 or sm_mhz <= 0:
+        return None
+    us = tail_ms * 1e3 / tail_rounds
+    floor_us = (L2_HIT_CYCLES + SMEM_ATOMIC64_CYCLES + CLUSTER_EXCHANGE_CYCLES) / sm_mhz
+    return {"tail_rounds_per_step": round(tail_rounds, 1), "us_per_round": round(us, 3),
+            "floor_us": round(floor_us, 3), "frac": round(floor_us / us, 3),
+            "floor": f"L2 hit {L2_HIT_CYCLES} + dependent 64-bit shared atomic {SMEM_ATOMIC64_CYCLES} + result "
+                     f"exchange {CLUSTER_EXCHANGE_CYCLES} cycles at {sm_mhz:.0f} MHz"}
+
+
 def max_over_ranks(ms: float, dist) -> float:
     """The step time every rank reports is the slowest rank's (host tensors, so
     the gloo process group carries it)."""
@@ -633,6 +654,9 @@ def main():
     cl = [(p["ms"]["tail"], p["rounds"] - p["bulk_rounds"]) for p in per_peel if p["tail_ctas"] > 1]
     if cl and sum(r for _, r in cl) > 0:
         roofline["cluster_tail_us_per_round"] = round(sum(t for t, _ in cl) * 1e3 / sum(r for _, r in cl), 3)
+        lat = cluster_round_latency(sum(t for t, _ in cl), sum(r for _, r in cl), sm_mhz)
+        if lat is not None:
+            roofline["cluster_round_latency"] = lat
 
     # end to end through the C ABI with host buffers
     e2e = None
