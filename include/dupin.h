@@ -227,6 +227,22 @@ typedef struct {
 int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result, void *stream);
 
 /*
+ * The hand-over autotuner.  tail_arc_cap decides when the grid-wide rounds
+ * hand over to a tail although their last round was large (once |S| fits a
+ * tail and 2 |E(S)| <= tail_arc_cap; small rounds hand over regardless).
+ * dupin_tune_handover peels 'g' under each of the DUPIN_TUNE_HANDOVER_N
+ * candidates 2^16, 2^18, ..., 2^26 (params otherwise as given; results are
+ * identical under every candidate, and none is returned), once to warm up
+ * and twice more timed on the host, and writes the fastest candidate to
+ * *best and each candidate's best time in ms to times_ms[0 ..
+ * DUPIN_TUNE_HANDOVER_N - 1] (either may be NULL).  The caller passes the
+ * winner as params.tail_arc_cap to later peels of similar graphs.  Errors as
+ * dupin_peel; INVALID_ARG for DUPIN_TDS.
+ */
+#define DUPIN_TUNE_HANDOVER_N 6
+int dupin_tune_handover(dupin_graph *g, const dupin_params *params, void *stream, int64_t *best, float *times_ms);
+
+/*
  * Peel 'count' independent graphs in few launches (one persistent launch
  * for all graphs small enough for one CTA, the single-graph path for the
  * rest).  params and results are arrays of length count; results are

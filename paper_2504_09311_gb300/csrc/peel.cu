@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <string>
 
+#include <chrono>
 #include <mutex>
 
 #include "dupin_internal.h"
@@ -1910,6 +1911,42 @@ int launch_small_graph_peel(const PeelArgs &A, int metric, bool check, cudaStrea
     k_peel_tail<<<1, TAIL_THREADS, (size_t)tail_smem_bytes(A.tail_cap), s>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return dupin_cuda_fail(e, "small-graph peel kernels");
+    return DUPIN_OK;
+}
+
+// The hand-over autotuner: the peel of this graph under each candidate
+// tail_arc_cap (the live-arc count below which the grid-wide rounds hand
+// over to a tail even when their last round was large), once to warm up and
+// twice more timed; the fastest candidate wins.
+static const long long kHandover[DUPIN_TUNE_HANDOVER_N] = {1ll << 16, 1ll << 18, 1ll << 20,
+                                                           1ll << 22, 1ll << 24, 1ll << 26};
+
+extern "C" int dupin_tune_handover(dupin_graph *g, const dupin_params *params, void *stream, int64_t *best,
+                                   float *times_ms) {
+    if (!g || !params) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph and params must be non-NULL");
+    if (params->metric == DUPIN_TDS) return dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TDS has no tail to hand over to");
+    double t_best[DUPIN_TUNE_HANDOVER_N];
+    for (int i = 0; i < DUPIN_TUNE_HANDOVER_N; i++) t_best[i] = 1e300;
+    for (int rep = 0; rep < 3; rep++) {
+        for (int i = 0; i < DUPIN_TUNE_HANDOVER_N; i++) {
+            dupin_params p = *params;
+            p.tail_arc_cap = kHandover[i];
+            p.flags &= ~(DUPIN_RESULT_DEVICE | DUPIN_TIMING);
+            dupin_result r;
+            memset(&r, 0, sizeof(r));
+            const auto t0 = std::chrono::steady_clock::now();
+            const int rc = dupin_peel(g, &p, &r, stream);  // returns once the peel is complete
+            const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (rc) return rc;
+            if (rep > 0) t_best[i] = std::min(t_best[i], t);  // the first pass warms up
+        }
+    }
+    int pick = 0;
+    for (int i = 1; i < DUPIN_TUNE_HANDOVER_N; i++)
+        if (t_best[i] < t_best[pick]) pick = i;
+    if (best) *best = kHandover[pick];
+    if (times_ms)
+        for (int i = 0; i < DUPIN_TUNE_HANDOVER_N; i++) times_ms[i] = (float)(t_best[i] * 1e3);
     return DUPIN_OK;
 }
 

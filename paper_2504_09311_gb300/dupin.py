@@ -75,7 +75,8 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ["dupin_graph_load", "dupin_graph_free", "dupin_graph_info", "dupin_peel", "dupin_peel_batch",
            "dupin_serve_create", "dupin_serve_submit", "dupin_serve_poll", "dupin_serve_wait", "dupin_serve_stats",
            "dupin_serve_destroy", "dupin_last_error", "dupin_version", "dupin_peel_noalloc", "dupin_struct_size",
-           "dupin_trim_cache", "dupin_batch_set_threads", "dupin_batch_get_threads", "dupin_batch_tune"]
+           "dupin_trim_cache", "dupin_batch_set_threads", "dupin_batch_get_threads", "dupin_batch_tune",
+           "dupin_tune_handover"]
 
 NOALLOC_MAX_N = 8192
 BATCH_CTA_MAX_N = 131072
@@ -110,6 +111,7 @@ def lib():
         L.dupin_batch_set_threads.argtypes = [ctypes.c_int]
         L.dupin_batch_get_threads.argtypes = [P]
         L.dupin_batch_tune.argtypes = [P, P, i64, P, P]
+        L.dupin_tune_handover.argtypes = [P, ctypes.POINTER(Params), P, P, P]
         for nm in EXPORTS:
             if nm not in ("dupin_version", "dupin_struct_size"):
                 getattr(L, nm).restype = ctypes.c_int
@@ -464,6 +466,19 @@ def batch_tune(graphs: Sequence[Graph], params: Sequence[Params], stream=None) -
     check(lib().dupin_batch_tune(ctypes.cast(G, ctypes.c_void_p), ctypes.cast(P, ctypes.c_void_p), k,
                                  _stream(stream), ctypes.byref(t)))
     return t.value
+
+
+TUNE_HANDOVER_N = 6
+
+
+def tune_handover(g: Graph, metric="dg", k_mult=1, eps=(1, 10), flags=0, stream=None):
+    """dupin_tune_handover: time the peel under each hand-over candidate;
+    returns (the fastest tail_arc_cap, {candidate: best ms})."""
+    p = make_params(metric, k_mult, eps, flags=flags)
+    best = ctypes.c_int64()
+    times = (ctypes.c_float * TUNE_HANDOVER_N)()
+    check(lib().dupin_tune_handover(g.handle, ctypes.byref(p), _stream(stream), ctypes.byref(best), times))
+    return best.value, {1 << (16 + 2 * i): float(times[i]) for i in range(TUNE_HANDOVER_N)}
 
 
 def peel_noalloc(n, row_ptr, col_idx, arc_w, vertex_w, params: Params, peel_round, best_mask=None, trace=None,

@@ -334,3 +334,25 @@ def test_device_pointer_load(dupin):
     assert np.array_equal(a.peel_round, b.peel_round) and a.trace_f == b.trace_f
     dgd.free()
     dgh.free()
+
+
+def test_handover_autotuner(dupin):
+    """dupin_tune_handover times the peel under each hand-over candidate and
+    returns one of them; the peel under the winner equals the default peel and
+    the oracle (the hand-over point never changes a result)."""
+    g = synth.rmat_weighted(16, 16, "fd", seed=3)
+    dg = dupin.Graph.from_synth(g)
+    best, times = dupin.tune_handover(dg, "fd", 1, (1, 10))
+    assert best in times and len(times) == dupin.TUNE_HANDOVER_N
+    assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+    ref = dupin.peel(dg, "fd", 1, (1, 10))
+    out = dupin.peel(dg, "fd", 1, (1, 10), tail_arc_cap=best)
+    assert np.array_equal(out.peel_round, ref.peel_round) and out.trace_f == ref.trace_f
+    og = oracle.Graph.from_synth(g, "fd")
+    orc = oracle.peel_batch(og, 1, (1, 10))
+    og.close()
+    assert np.array_equal(out.peel_round, orc.peel_round) and out.trace_f == orc.trace_f
+    with pytest.raises(dupin.DupinError) as e:
+        dupin.tune_handover(dg, "tds", 3, (1, 10))
+    assert e.value.code == dupin.ERR_INVALID_ARG
+    dg.free()
