@@ -86,3 +86,13 @@ def test_round_latency_reading():
     assert r["floor_us"] == round((bench.L2_HIT_CYCLES + bench.SMEM_ATOMIC64_CYCLES) / 2070.0, 3)
     assert 0 < r["frac"] < 1
     assert bench.round_latency(0.0, 10, 2070.0) is None and bench.round_latency(1.0, 0, 2070.0) is None
+
+
+def test_cluster_round_latency_reading():
+    """The cluster tail's time per round against its floor: one L2 hit, one
+    dependent shared atomic and the result exchange, in cycles at the SM clock."""
+    r = bench.cluster_round_latency(72.4, 16616.0, 2070.0)
+    assert abs(r["us_per_round"] - 72.4e3 / 16616) < 1e-3
+    floor = (bench.L2_HIT_CYCLES + bench.SMEM_ATOMIC64_CYCLES + bench.CLUSTER_EXCHANGE_CYCLES) / 2070.0
+    assert abs(r["floor_us"] - floor) < 1e-3 and abs(r["frac"] - floor / r["us_per_round"]) < 2e-3
+    assert bench.cluster_round_latency(0.0, 10, 2070.0) is None and bench.cluster_round_latency(1.0, 0, 2070.0) is None
