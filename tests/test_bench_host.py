@@ -91,6 +91,8 @@ def test_round_latency_reading():
 def test_cluster_round_latency_reading():
     """The cluster tail's time per round against its floor: one L2 hit, one
     dependent shared atomic and the result exchange, in cycles at the SM clock."""
+    import bench
+
     r = bench.cluster_round_latency(72.4, 16616.0, 2070.0)
     assert abs(r["us_per_round"] - 72.4e3 / 16616) < 1e-3
     floor = (bench.L2_HIT_CYCLES + bench.SMEM_ATOMIC64_CYCLES + bench.CLUSTER_EXCHANGE_CYCLES) / 2070.0
