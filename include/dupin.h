@@ -68,6 +68,11 @@ extern "C" {
 #define DUPIN_FD 2
 #define DUPIN_TDS 3 /* triangle density (Sec. 2.1): f(S) = triangles of G[S], w_u = those through u;
                        plain counts, not Q32.32 (the paper's k for TDS is 3); dupin_peel only */
+#define DUPIN_KCLIDS 4 /* q-clique density kCLiDS (Sec. 2.1): f(S) = q-cliques of G[S], w_u = those
+                          through u, q = dupin_params.clique_q (3 .. DUPIN_CLIQUE_MAX_Q; q = 3 gives
+                          the same results as DUPIN_TDS); plain counts (the paper's k for kCLiDS is
+                          q); dupin_peel only */
+#define DUPIN_CLIQUE_MAX_Q 8
 
 /* --------------------------------------------------------- graph loading */
 
@@ -149,7 +154,7 @@ int dupin_graph_info(const dupin_graph *g, int64_t *n, int64_t *m, int64_t *arcs
 #define DUPIN_TAIL_CLUSTER 64u /* every tail runs in the cluster kernel (never one CTA) */
 
 typedef struct {
-    int32_t metric;     /* DUPIN_DG, DUPIN_DW, DUPIN_FD or DUPIN_TDS */
+    int32_t metric;     /* DUPIN_DG, DUPIN_DW, DUPIN_FD, DUPIN_TDS or DUPIN_KCLIDS */
     int32_t k_mult;     /* k of Algorithm 2, 1..64 (2 is the paper's value for DG/DW/FD) */
     int64_t eps_num;    /* eps = eps_num / eps_den, eps_num >= 0 */
     int64_t eps_den;    /* 1 .. 2^24 */
@@ -162,6 +167,8 @@ typedef struct {
                              this many arcs (2 |E(S)|) or after a round that removed
                              at most 64 vertices or expanded at most 2^18 arcs (if the
                              sub-graph has at most 2^27 arcs), whichever comes first */
+    int32_t clique_q;   /* DUPIN_KCLIDS: the clique size q, 3 .. DUPIN_CLIQUE_MAX_Q;
+                           ignored by the other metrics */
 } dupin_params;
 
 /*
@@ -217,12 +224,15 @@ typedef struct {
  * (max_rounds), BUFFER_TOO_SMALL (trace_cap < n_rounds + 1 with a non-NULL
  * trace; everything else is still filled), OOM, TIMEOUT, CUDA.
  *
- * With metric DUPIN_TDS, f and the weights are triangle counts (not Q32.32):
- * the trace's f words and best_f hold counts, best_density is f / |S|, the
- * graph's weights are ignored, and each round runs as a few short launches
- * (the graph's triangles are listed once at the start, and every round
- * lists only the triangles through its removed vertices).  f must stay
- * below 2^63.  The tail fields of the result are 0.
+ * With metric DUPIN_TDS (DUPIN_KCLIDS), f and the weights are triangle
+ * (q-clique) counts, not Q32.32: the trace's f words and best_f hold counts,
+ * best_density is f / |S|, the graph's weights are ignored, and each round
+ * runs as a few short launches (the graph's cliques are listed once at the
+ * start, and every round lists only the cliques through its removed
+ * vertices).  The graph's rows must be sorted (the loader checks it); f
+ * stays below 2^63 (a count that large could not be listed).  The tail
+ * fields of the result are 0.  INVALID_ARG for DUPIN_KCLIDS with clique_q
+ * outside 3 .. DUPIN_CLIQUE_MAX_Q.
  */
 int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result, void *stream);
 
@@ -237,7 +247,7 @@ int dupin_peel(dupin_graph *g, const dupin_params *params, dupin_result *result,
  * *best and each candidate's best time in ms to times_ms[0 ..
  * DUPIN_TUNE_HANDOVER_N - 1] (either may be NULL).  The caller passes the
  * winner as params.tail_arc_cap to later peels of similar graphs.  Errors as
- * dupin_peel; INVALID_ARG for DUPIN_TDS.
+ * dupin_peel; INVALID_ARG for DUPIN_TDS and DUPIN_KCLIDS.
  */
 #define DUPIN_TUNE_HANDOVER_N 6
 int dupin_tune_handover(dupin_graph *g, const dupin_params *params, void *stream, int64_t *best, float *times_ms);

@@ -790,8 +790,8 @@ extern "C" int dupin_peel_batch(dupin_graph *const *graphs, const dupin_params *
         if (!graphs[j]) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph " + std::to_string((long long)j) + " is NULL");
         PeelPlan plan;
         int rc = peel_resolve(graphs[j], &params[j], &plan);
-        if (rc == DUPIN_OK && params[j].metric == DUPIN_TDS)
-            rc = dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TDS is served by dupin_peel only");
+        if (rc == DUPIN_OK && is_clique_metric(params[j].metric))
+            rc = dupin_fail(DUPIN_ERR_INVALID_ARG, "the clique metrics (TDS, kCLiDS) are served by dupin_peel only");
         if (rc) {
             char buf[512];
             dupin_last_error(buf, sizeof(buf));

@@ -137,8 +137,9 @@ void enqueue_note_cluster(const PeelWorkspace *prev, PeelWorkspace *next, cudaSt
 int cluster_ctas();
 int launch_cluster_tail(const PeelArgs &A, cudaStream_t s);
 
-// dupin_peel under the triangle-density metric (tds.cu)
+// dupin_peel under the clique metrics TDS and kCLiDS (tds.cu)
 int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_t s);
+inline bool is_clique_metric(int metric) { return metric == DUPIN_TDS || metric == DUPIN_KCLIDS; }
 
 // the largest live set the single-CTA tail accepts, and the default caps
 long long tail_cap_limit();

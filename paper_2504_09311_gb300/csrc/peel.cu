@@ -1448,7 +1448,9 @@ static long long tail_smem_bytes(long long cap) {
 
 static int check_params(const dupin_graph *g, const dupin_params *p) {
     if (!p) return dupin_fail(DUPIN_ERR_INVALID_ARG, "params is NULL");
-    if (p->metric < DUPIN_DG || p->metric > DUPIN_TDS) return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown metric");
+    if (p->metric < DUPIN_DG || p->metric > DUPIN_KCLIDS) return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown metric");
+    if (p->metric == DUPIN_KCLIDS && (p->clique_q < 3 || p->clique_q > DUPIN_CLIQUE_MAX_Q))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_KCLIDS needs clique_q in 3..DUPIN_CLIQUE_MAX_Q");
     if (p->k_mult < 1 || p->k_mult > 64) return dupin_fail(DUPIN_ERR_INVALID_ARG, "k_mult must be in 1..64");
     if (p->eps_den < 1 || p->eps_den > (1LL << 24) || p->eps_num < 0 || p->eps_num > (1LL << 30))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "eps must be eps_num/eps_den with 0 <= eps_num <= 2^30, 1 <= eps_den <= 2^24");
@@ -1457,7 +1459,7 @@ static int check_params(const dupin_graph *g, const dupin_params *p) {
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "unknown flag");
     if ((p->flags & DUPIN_TAIL_ONE_CTA) && (p->flags & DUPIN_TAIL_CLUSTER))
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TAIL_ONE_CTA and DUPIN_TAIL_CLUSTER exclude each other");
-    if (p->metric != DUPIN_DG && p->metric != DUPIN_TDS && g->cw == nullptr)
+    if (p->metric != DUPIN_DG && !is_clique_metric(p->metric) && g->cw == nullptr)
         return dupin_fail(DUPIN_ERR_INVALID_ARG, "DW/FD need edge weights; the graph was loaded without them");
     return DUPIN_OK;
 }
@@ -1924,7 +1926,8 @@ static const long long kHandover[DUPIN_TUNE_HANDOVER_N] = {1ll << 16, 1ll << 18,
 extern "C" int dupin_tune_handover(dupin_graph *g, const dupin_params *params, void *stream, int64_t *best,
                                    float *times_ms) {
     if (!g || !params) return dupin_fail(DUPIN_ERR_INVALID_ARG, "graph and params must be non-NULL");
-    if (params->metric == DUPIN_TDS) return dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TDS has no tail to hand over to");
+    if (is_clique_metric(params->metric))
+        return dupin_fail(DUPIN_ERR_INVALID_ARG, "the clique metrics have no tail to hand over to");
     double t_best[DUPIN_TUNE_HANDOVER_N];
     for (int i = 0; i < DUPIN_TUNE_HANDOVER_N; i++) t_best[i] = 1e300;
     for (int rep = 0; rep < 3; rep++) {
@@ -1958,7 +1961,7 @@ extern "C" int dupin_peel(dupin_graph *g, const dupin_params *p, dupin_result *r
     if (rc) return rc;
     DUPIN_CUDA_TRY(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->metric == DUPIN_TDS) return tds_peel(g, p, r, s);
+    if (is_clique_metric(p->metric)) return tds_peel(g, p, r, s);
     rc = workspace_ensure(g, plan);
     if (rc) return rc;
     rc = enqueue_peel(g, g->ws, p, plan, s);

@@ -314,8 +314,8 @@ extern "C" int dupin_serve_submit(dupin_server *s, dupin_graph *g, const dupin_p
     q->p = *p;
     q->r = r;
     int rc = peel_resolve(g, p, &q->plan);
-    if (rc == DUPIN_OK && p->metric == DUPIN_TDS)
-        rc = dupin_fail(DUPIN_ERR_INVALID_ARG, "DUPIN_TDS is served by dupin_peel only");
+    if (rc == DUPIN_OK && is_clique_metric(p->metric))
+        rc = dupin_fail(DUPIN_ERR_INVALID_ARG, "the clique metrics (TDS, kCLiDS) are served by dupin_peel only");
     if (rc) {
         delete q;
         return rc;

@@ -1,9 +1,10 @@
-// tds.cu -- batch peeling under the triangle-density metric TDS (Sec. 2.1):
-// f(S) = number of triangles of G[S], w_u(S) = the triangles of G[S] through
+// tds.cu -- batch peeling under the clique metrics of Sec. 2.1: TDS
+// (triangle density) and kCLiDS (q-clique density).  f(S) = number of
+// q-cliques of G[S] (q = 3 for TDS), w_u(S) = the q-cliques of G[S] through
 // u, so that removing u lowers f by w_u.  The rounds are Algorithm 2 (Sec.
-// 4.1; the paper's k for TDS is 3) with Algorithm 3's tau_max and Algorithm
-// 4's trims by flag, exactly as for the other metrics but on plain counts
-// (no Q32.32 scale): every comparison is between ratios of integers.
+// 4.1; the paper's k for these metrics is q) with Algorithm 3's tau_max and
+// Algorithm 4's trims by flag, exactly as for the other metrics but on plain
+// counts (no Q32.32 scale): every comparison is between ratios of integers.
 //
 // Device state lives in one control block; a round is five launches --
 //   min     the minimum live weight (the minimum rule and the trim test);
@@ -13,15 +14,18 @@
 //   select  every live u with w_u <= T leaves: its round is recorded and it
 //           joins the round's list;
 //   expand  one warp per removed vertex u, one lane per arc u -> v with v in
-//           S_{i-1}: the common neighbours x > v of u and v in S_{i-1} (a merge
-//           of the two sorted rows) are the triangles {u, v, x} of G[S_{i-1}]
-//           through u; each dies once, counted by its smallest member in U_i,
-//           and lowers f by one and each member outside U_i by one;
+//           S_{i-1}: the cliques of G[S_{i-1}] through u whose smallest
+//           member besides u is v (for TDS a merge of the two sorted rows,
+//           the common neighbours x > v; for kCLiDS a depth-first walk over
+//           u's row after v, each candidate kept when it is in the rows of
+//           every member chosen so far); each clique dies once, counted by
+//           its smallest member in U_i, and lowers f by one and each member
+//           outside U_i by one;
 //   close   one thread: f, |S|, the trace, the best prefix.
 // The host launches rounds in groups and reads the control block between
 // groups; launches after the peel ends return at once.  The initial counts
-// list every triangle once from its smallest vertex (u < v < x, merging u's
-// row after v with v's row after v).  Rows are sorted (the loader checks it).
+// list every clique once from its smallest vertex (the same walks, with the
+// other members above u).  Rows are sorted (the loader checks it).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +61,7 @@ struct TdsArgs {
     long long tr_cap;
     long long kD, D;
     int gpo, lpo;
+    int q;  // clique size (3 for TDS)
     long long max_rounds;
 };
 
@@ -251,6 +256,129 @@ __global__ void k_tds_expand(TdsArgs A) {
     if (lane == 0 && dead) atomicAdd((unsigned long long *)&A.ctl->df, (unsigned long long)dead);
 }
 
+// ---- kCLiDS: q-cliques, 3 <= q <= DUPIN_CLIQUE_MAX_Q
+
+constexpr int QMAX = DUPIN_CLIQUE_MAX_Q;
+// positions of depth d (2 <= d <= QMAX - 1) start at pos_base(d): d of them,
+// one in the row of each member chosen before depth d
+__host__ __device__ constexpr int pos_base(int d) { return d * (d - 1) / 2 - 1; }
+
+// The q-cliques {u, v, y_2, ..., y_{q-1}} with v < y_2 < ... < y_{q-1}, all in
+// u's row, whose members pass 'keep' (v is the caller's: u's arc at position
+// j).  c[0] = u, c[1] = v; at depth d the candidates y_d are the ids above
+// c[d-1] present in the rows of c[0..d-1], found by advancing one position per
+// row (rows are sorted, so every position only moves forward) until all d
+// rows show the same id.  'emit' gets the q members in c[0..q-1].  Every loop
+// advances a position within its row, so the walk ends.
+template <class Keep, class Emit>
+__device__ void clique_walk(const TdsArgs &A, int q, int u, long long j, long long e, int v, Keep keep, Emit emit) {
+    int c[QMAX];
+    long long end[QMAX];
+    long long pos[pos_base(QMAX)];
+    c[0] = u;
+    c[1] = v;
+    end[0] = e;
+    end[1] = A.rp[v + 1];
+    pos[pos_base(2)] = j + 1;
+    pos[pos_base(2) + 1] = row_after(A, v, v);
+    int d = 2;
+    while (d >= 2) {
+        long long *P = pos + pos_base(d);
+        bool found = false;
+        int y = 0;
+        while (P[0] < end[0]) {
+            y = head(A, P[0]);
+            int t = 1;
+            for (; t < d; t++) {
+                while (P[t] < end[t] && head(A, P[t]) < y) P[t]++;
+                if (P[t] >= end[t]) break;
+                if (head(A, P[t]) != y) break;
+            }
+            if (t == d) {  // y is in every row
+                if (keep(y)) {
+                    found = true;
+                    break;
+                }
+                P[0]++;
+                continue;
+            }
+            if (P[t] >= end[t]) break;  // a row is used up: no candidate left at this depth
+            const int h = head(A, P[t]);  // the next id that row can match
+            while (P[0] < end[0] && head(A, P[0]) < h) P[0]++;
+        }
+        if (!found) {
+            d--;
+            continue;
+        }
+        P[0]++;  // this depth resumes after y
+        c[d] = y;
+        if (d == q - 1) {
+            emit(c);
+            continue;
+        }
+        long long *N = pos + pos_base(d + 1);
+        for (int t = 0; t < d; t++) N[t] = P[t];
+        N[d] = row_after(A, y, y);
+        end[d] = A.rp[y + 1];
+        d++;
+    }
+}
+
+// every q-clique once, from its smallest vertex u (v > u, so all members above u)
+__global__ void k_clq_count(TdsArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int q = A.q;
+    const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+    long long cnt = 0;
+    for (long long u = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); u < A.n; u += W) {
+        const long long b = A.rp[u], e = A.rp[u + 1];
+        for (long long j = b + lane; j < e; j += 32) {
+            const int v = head(A, j);
+            if (v <= (int)u) continue;
+            clique_walk(
+                A, q, (int)u, j, e, v, [](int) { return true; },
+                [&](const int *c) {
+                    for (int t = 0; t < q; t++) atomicAdd((unsigned long long *)&A.w[c[t]], 1ull);
+                    cnt++;
+                });
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if (lane == 0 && cnt) atomicAdd((unsigned long long *)&A.ctl->f, (unsigned long long)cnt);
+}
+
+// the q-cliques of G[S_{i-1}] through each removed vertex u (one warp per u)
+__global__ void k_clq_expand(TdsArgs A) {
+    const TdsCtl *ctl = A.ctl;
+    if (ctl->status || ctl->error) return;
+    const int r = (int)(ctl->round + 1);
+    const long long U = ctl->ucnt;
+    const int q = A.q;
+    const int lane = threadIdx.x & 31;
+    const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+    long long dead = 0;
+    for (long long k = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); k < U; k += W) {
+        const int u = A.front[k];
+        const long long b = A.rp[u], e = A.rp[u + 1];
+        for (long long j = b + lane; j < e; j += 32) {
+            const int v = head(A, j);
+            if (A.pr[v] < r) continue;  // left in an earlier round
+            clique_walk(
+                A, q, u, j, e, v, [&](int y) { return A.pr[y] >= r; },
+                [&](const int *c) {
+                    // counted once: by its smallest member in U_i
+                    for (int t = 1; t < q; t++)
+                        if (c[t] < u && A.pr[c[t]] == r) return;
+                    dead++;
+                    for (int t = 1; t < q; t++)
+                        if (A.pr[c[t]] != r) atomicAdd((unsigned long long *)&A.w[c[t]], (unsigned long long)-1ll);
+                });
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, d);
+    if (lane == 0 && dead) atomicAdd((unsigned long long *)&A.ctl->df, (unsigned long long)dead);
+}
+
 __global__ void k_tds_close(TdsArgs A) {
     TdsCtl *c = A.ctl;
     if (c->status || c->error) return;
@@ -289,7 +417,7 @@ __global__ void k_tds_minw_init(TdsCtl *c) { c->minw = 0x7fffffffffffffffLL; }
 
 }  // namespace
 
-// dupin_peel for metric DUPIN_TDS (parameters checked by the caller).
+// dupin_peel for the metrics DUPIN_TDS and DUPIN_KCLIDS (parameters checked by the caller).
 int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_t s) {
     const long long n = g->n;
     const long long max_rounds = p->max_rounds > 0 ? p->max_rounds : n + 1;
@@ -306,6 +434,8 @@ int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_
     A.D = p->eps_den;
     A.gpo = (p->flags & (DUPIN_GPO | DUPIN_LPO)) ? 1 : 0;
     A.lpo = (p->flags & DUPIN_LPO) ? 1 : 0;
+    A.q = p->metric == DUPIN_KCLIDS ? p->clique_q : 3;
+    const bool tri = p->metric == DUPIN_TDS;  // the triangle kernels; kCLiDS (any q) walks
     A.max_rounds = max_rounds;
     A.tr_cap = tr_cap;
     cudaError_t e = cudaSuccess;
@@ -329,7 +459,7 @@ int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_
         release();
         cudaGetLastError();
         return dupin_fail(e == cudaErrorMemoryAllocation ? DUPIN_ERR_OOM : DUPIN_ERR_CUDA,
-                          std::string("TDS state: ") + cudaGetErrorString(e));
+                          std::string("clique peel state: ") + cudaGetErrorString(e));
     }
     A.w = (long long *)buf[0];
     A.pr = (int *)buf[1];
@@ -340,7 +470,8 @@ int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_
     A.tr_peeled = (long long *)buf[6];
     const int vgrid = sms * 8;
     k_tds_reset<<<vgrid, 256, 0, s>>>(A);
-    k_tds_count<<<vgrid, 256, 0, s>>>(A);
+    if (tri) k_tds_count<<<vgrid, 256, 0, s>>>(A);
+    else k_clq_count<<<vgrid, 256, 0, s>>>(A);
     k_tds_start<<<1, 1, 0, s>>>(A);
     k_tds_minw_init<<<1, 1, 0, s>>>(A.ctl);
     TdsCtl hc;
@@ -350,14 +481,15 @@ int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_
             k_tds_min<<<vgrid, 256, 0, s>>>(A);
             k_tds_plan<<<1, 1, 0, s>>>(A);
             k_tds_select<<<vgrid, 256, 0, s>>>(A);
-            k_tds_expand<<<vgrid, 256, 0, s>>>(A);
+            if (tri) k_tds_expand<<<vgrid, 256, 0, s>>>(A);
+            else k_clq_expand<<<vgrid, 256, 0, s>>>(A);
             k_tds_close<<<1, 1, 0, s>>>(A);
         }
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, A.ctl, sizeof(hc), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
-            rc = dupin_cuda_fail(e, "TDS rounds");
+            rc = dupin_cuda_fail(e, "clique peel rounds");
             break;
         }
         if (hc.error || hc.status) break;
@@ -368,7 +500,7 @@ int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_
     }
     if (rc == DUPIN_OK && hc.error)
         rc = dupin_fail(hc.error, hc.error == DUPIN_ERR_NO_PROGRESS ? "max_rounds reached before the set became empty"
-                                                                    : "TDS peel failed");
+                                                                    : "clique peel failed");
     if (rc == DUPIN_OK) {
         r->n_rounds = hc.round;
         r->best_round = hc.best_round;
@@ -408,7 +540,7 @@ int tds_peel(dupin_graph *g, const dupin_params *p, dupin_result *r, cudaStream_
                 e = cudaMemcpyAsync(r->trace_peeled, A.tr_peeled, 8 * (size_t)cnt, kind, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) rc = dupin_cuda_fail(e, "TDS results");
+        if (e != cudaSuccess) rc = dupin_cuda_fail(e, "clique peel results");
         if (rc == DUPIN_OK && (r->trace_f_hi || r->trace_f_lo || r->trace_size || r->trace_peeled) &&
             r->trace_cap < nt)
             rc = dupin_fail(DUPIN_ERR_BUFFER_TOO_SMALL, "trace_cap < n_rounds + 1 (n_rounds is filled)");

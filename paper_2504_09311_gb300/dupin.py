@@ -17,8 +17,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdupin.so")
 
-DG, DW, FD, TDS = 0, 1, 2, 3
-METRICS = {"dg": DG, "dw": DW, "fd": FD, "tds": TDS}
+DG, DW, FD, TDS, KCLIDS = 0, 1, 2, 3, 4
+METRICS = {"dg": DG, "dw": DW, "fd": FD, "tds": TDS, "kclids": KCLIDS}
+CLIQUE_MAX_Q = 8  # kCLiDS clique sizes 3 .. CLIQUE_MAX_Q
 DEVICE_PTRS = 1
 GPO = 1
 LPO = 2  # Algorithm 4 (implies GPO)
@@ -48,7 +49,7 @@ class GraphDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("metric", ctypes.c_int32), ("k_mult", ctypes.c_int32), ("eps_num", ctypes.c_int64),
                 ("eps_den", ctypes.c_int64), ("max_rounds", ctypes.c_int64), ("flags", ctypes.c_uint32),
-                ("tail_cap", ctypes.c_int32), ("tail_arc_cap", ctypes.c_int64)]
+                ("tail_cap", ctypes.c_int32), ("tail_arc_cap", ctypes.c_int64), ("clique_q", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -225,9 +226,10 @@ class Graph:
             pass
 
 
-def make_params(metric="dg", k_mult=1, eps=(1, 10), max_rounds=0, flags=0, tail_cap=0, tail_arc_cap=0) -> Params:
+def make_params(metric="dg", k_mult=1, eps=(1, 10), max_rounds=0, flags=0, tail_cap=0, tail_arc_cap=0,
+                clique_q=0) -> Params:
     m = METRICS[metric] if isinstance(metric, str) else int(metric)
-    return Params(m, k_mult, eps[0], eps[1], max_rounds, flags, tail_cap, tail_arc_cap)
+    return Params(m, k_mult, eps[0], eps[1], max_rounds, flags, tail_cap, tail_arc_cap, clique_q)
 
 
 @dataclass
@@ -339,9 +341,9 @@ def _output(r: Result, peel_round, best_mask, trace) -> PeelOutput:
 
 
 def peel(g: Graph, metric="dg", k_mult=1, eps=(1, 10), flags=0, max_rounds=0, tail_cap=0, want_rounds=True,
-         want_mask=True, want_trace=True, stream=None, tail_arc_cap=0) -> PeelOutput:
-    """dupin_peel with host result buffers (numpy)."""
-    p = make_params(metric, k_mult, eps, max_rounds, flags, tail_cap, tail_arc_cap)
+         want_mask=True, want_trace=True, stream=None, tail_arc_cap=0, clique_q=0) -> PeelOutput:
+    """dupin_peel with host result buffers (numpy); clique_q is kCLiDS's clique size."""
+    p = make_params(metric, k_mult, eps, max_rounds, flags, tail_cap, tail_arc_cap, clique_q)
     pr = np.empty(g.n, np.int32) if want_rounds else None
     mk = np.empty(g.n, np.uint8) if want_mask else None
     trace = None

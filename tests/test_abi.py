@@ -69,7 +69,7 @@ def test_struct_layouts_match_header():
 
     # 2 int64 + 7 pointers + uint32 (+ padding)
     assert ctypes.sizeof(dupin.GraphDesc) == 2 * 8 + 7 * 8 + 8
-    assert ctypes.sizeof(dupin.Params) == 4 + 4 + 8 + 8 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(dupin.Params) == 4 + 4 + 8 + 8 + 8 + 4 + 4 + 8 + 8  # ... + clique_q (+ padding)
     assert ctypes.sizeof(dupin.Result) == 6 * 8 + 10 * 8 + 4 * 4 + 8  # ... + phase_ms[4] + tail_ctas
     # and the library's own sizeof() of every public struct agrees
     L = dupin.lib()

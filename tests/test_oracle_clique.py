@@ -88,7 +88,7 @@ def test_q2_is_dg(seed, k, eps):
     assert a.n_min_rule == b.n_min_rule
 
 
-@pytest.mark.parametrize("p,q", [(3, 3), (5, 3), (6, 4), (7, 5), (5, 5)])
+@pytest.mark.parametrize("p,q", [(3, 3), (5, 3), (6, 4), (7, 5), (5, 5), (9, 6), (10, 7), (11, 8)])
 def test_clique_closed_form(p, q):
     edges = [(u, v) for u in range(p) for v in range(u + 1, p)]
     g = graph(p, edges)
@@ -114,10 +114,10 @@ def test_triangle_free(seed):
 
 
 @pytest.mark.parametrize("seed", range(5))
-@pytest.mark.parametrize("q", [3, 4])
+@pytest.mark.parametrize("q", [3, 4, 5, 6])
 def test_rounds_recounted(seed, q):
     n = 14
-    edges = random_edges(n, 0.55, seed)
+    edges = random_edges(n, 0.55 if q <= 4 else 0.75, seed)  # denser for q >= 5: some cliques exist
     adj = adjacency(n, edges)
     g = graph(n, edges)
     for k, eps in [(q, (1, 10)), (1, (0, 1))]:
