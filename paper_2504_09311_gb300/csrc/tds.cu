@@ -263,13 +263,39 @@ constexpr int QMAX = DUPIN_CLIQUE_MAX_Q;
 // one in the row of each member chosen before depth d
 __host__ __device__ constexpr int pos_base(int d) { return d * (d - 1) / 2 - 1; }
 
+// first position in [p, end) whose id is at least x (end if none): doubling
+// steps from p, then a binary search in the last step, so a long row is
+// crossed in O(log gap) reads
+__device__ __forceinline__ long long seek(const TdsArgs &A, long long p, long long end, int x) {
+    if (p >= end || head(A, p) >= x) return p;
+    long long lo = p, hi, step = 1;  // head(lo) < x
+    for (;;) {
+        hi = lo + step;
+        if (hi >= end) {
+            hi = end;
+            break;
+        }
+        if (head(A, hi) >= x) break;
+        lo = hi;
+        step <<= 1;
+    }
+    lo++;  // the answer is in [lo, hi]
+    while (lo < hi) {
+        const long long mid = lo + ((hi - lo) >> 1);
+        if (head(A, mid) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // The q-cliques {u, v, y_2, ..., y_{q-1}} with v < y_2 < ... < y_{q-1}, all in
 // u's row, whose members pass 'keep' (v is the caller's: u's arc at position
 // j).  c[0] = u, c[1] = v; at depth d the candidates y_d are the ids above
-// c[d-1] present in the rows of c[0..d-1], found by advancing one position per
-// row (rows are sorted, so every position only moves forward) until all d
-// rows show the same id.  'emit' gets the q members in c[0..q-1].  Every loop
-// advances a position within its row, so the walk ends.
+// c[d-1] present in the rows of c[0..d-1].  They are found by a leapfrog
+// join: the rows take turns, each seeking its position to the largest id
+// seen so far, until d rows in a row show the same id (rows are sorted, so
+// every position only moves forward and the largest id only grows; a long
+// row is crossed by doubling steps).  'emit' gets the q members in c[0..q-1].
 template <class Keep, class Emit>
 __device__ void clique_walk(const TdsArgs &A, int q, int u, long long j, long long e, int v, Keep keep, Emit emit) {
     int c[QMAX];
@@ -286,25 +312,32 @@ __device__ void clique_walk(const TdsArgs &A, int q, int u, long long j, long lo
         long long *P = pos + pos_base(d);
         bool found = false;
         int y = 0;
-        while (P[0] < end[0]) {
+        if (P[0] < end[0]) {
             y = head(A, P[0]);
-            int t = 1;
-            for (; t < d; t++) {
-                while (P[t] < end[t] && head(A, P[t]) < y) P[t]++;
-                if (P[t] >= end[t]) break;
-                if (head(A, P[t]) != y) break;
-            }
-            if (t == d) {  // y is in every row
-                if (keep(y)) {
-                    found = true;
-                    break;
+            int agree = 1, t = 1;  // rows in turn that show y
+            for (;;) {
+                if (agree == d) {  // y is in every row
+                    if (keep(y)) {
+                        found = true;
+                        break;
+                    }
+                    if (++P[0] >= end[0]) break;
+                    y = head(A, P[0]);
+                    agree = 1;
+                    t = 1;
+                    continue;
                 }
-                P[0]++;
-                continue;
+                P[t] = seek(A, P[t], end[t], y);
+                if (P[t] >= end[t]) break;  // a row is used up: no candidate left at this depth
+                const int h = head(A, P[t]);
+                if (h == y) {
+                    agree++;
+                } else {
+                    y = h;
+                    agree = 1;
+                }
+                t = t + 1 == d ? 0 : t + 1;
             }
-            if (P[t] >= end[t]) break;  // a row is used up: no candidate left at this depth
-            const int h = head(A, P[t]);  // the next id that row can match
-            while (P[0] < end[0] && head(A, P[0]) < h) P[0]++;
         }
         if (!found) {
             d--;
