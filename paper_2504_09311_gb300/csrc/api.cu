@@ -31,7 +31,7 @@ extern "C" int dupin_last_error(char *buf, size_t cap) {
     return DUPIN_OK;
 }
 
-extern "C" const char *dupin_version(void) { return "0.2.0"; }
+extern "C" const char *dupin_version(void) { return "0.3.0"; }
 
 extern "C" int64_t dupin_struct_size(const char *name) {
     if (!name) return -1;
