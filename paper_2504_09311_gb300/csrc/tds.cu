@@ -16,16 +16,19 @@
 //   expand  one warp per removed vertex u, one lane per arc u -> v with v in
 //           S_{i-1}: the cliques of G[S_{i-1}] through u whose smallest
 //           member besides u is v (for TDS a merge of the two sorted rows,
-//           the common neighbours x > v; for kCLiDS a depth-first walk over
-//           u's row after v, each candidate kept when it is in the rows of
-//           every member chosen so far); each clique dies once, counted by
-//           its smallest member in U_i, and lowers f by one and each member
-//           outside U_i by one;
+//           the common neighbours x > v, each triangle counted by its
+//           smallest member in U_i; for kCLiDS a depth-first walk over u's
+//           row after v, each candidate kept when it is in the rows of every
+//           member chosen so far and, if it leaves in this round too,
+//           outranks u in (degree, id), so that only the removed member of
+//           lowest rank lists the clique); each clique that dies lowers f by
+//           one and each member outside U_i by one;
 //   close   one thread: f, |S|, the trace, the best prefix.
 // The host launches rounds in groups and reads the control block between
 // groups; launches after the peel ends return at once.  The initial counts
-// list every clique once from its smallest vertex (the same walks, with the
-// other members above u).  Rows are sorted (the loader checks it).
+// list every clique once: TDS from its smallest vertex, kCLiDS from its
+// member of lowest degree (the same walks, keeping only members that outrank
+// u).  Rows are sorted (the loader checks it).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -357,7 +360,10 @@ __device__ void clique_walk(const TdsArgs &A, int q, int u, long long j, long lo
     }
 }
 
-// every q-clique once, from its smallest vertex u (v > u, so all members above u)
+// every q-clique once, from its member u of lowest rank (degree, then id):
+// the lane of arc u -> v walks when v outranks u and keeps only members that
+// outrank u, so a hub lists just the cliques whose other members have higher
+// degree still, and the listing spreads over the low-degree vertices' warps
 __global__ void k_clq_count(TdsArgs A) {
     const int lane = threadIdx.x & 31;
     const int q = A.q;
@@ -365,11 +371,15 @@ __global__ void k_clq_count(TdsArgs A) {
     long long cnt = 0;
     for (long long u = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); u < A.n; u += W) {
         const long long b = A.rp[u], e = A.rp[u + 1];
+        const auto above = [&](int x) {
+            const long long dx = A.rp[x + 1] - A.rp[x];
+            return dx > e - b || (dx == e - b && x > (int)u);
+        };
         for (long long j = b + lane; j < e; j += 32) {
             const int v = head(A, j);
-            if (v <= (int)u) continue;
+            if (!above(v)) continue;
             clique_walk(
-                A, q, (int)u, j, e, v, [](int) { return true; },
+                A, q, (int)u, j, e, v, above,
                 [&](const int *c) {
                     for (int t = 0; t < q; t++) atomicAdd((unsigned long long *)&A.w[c[t]], 1ull);
                     cnt++;
@@ -380,7 +390,10 @@ __global__ void k_clq_count(TdsArgs A) {
     if (lane == 0 && cnt) atomicAdd((unsigned long long *)&A.ctl->f, (unsigned long long)cnt);
 }
 
-// the q-cliques of G[S_{i-1}] through each removed vertex u (one warp per u)
+// the q-cliques of G[S_{i-1}] that die in round i (one warp per removed
+// vertex u): each is listed once, by its removed member of lowest rank
+// (degree, then id) -- u's walk keeps a member removed in this round only if
+// it outranks u -- and lowers f by one and each member outside U_i by one
 __global__ void k_clq_expand(TdsArgs A) {
     const TdsCtl *ctl = A.ctl;
     if (ctl->status || ctl->error) return;
@@ -393,19 +406,21 @@ __global__ void k_clq_expand(TdsArgs A) {
     for (long long k = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); k < U; k += W) {
         const int u = A.front[k];
         const long long b = A.rp[u], e = A.rp[u + 1];
+        const auto keep = [&](int x) {
+            const int px = A.pr[x];
+            if (px < r) return false;  // left in an earlier round
+            if (px > r) return true;   // survives the round
+            const long long dx = A.rp[x + 1] - A.rp[x];
+            return dx > e - b || (dx == e - b && x > u);
+        };
         for (long long j = b + lane; j < e; j += 32) {
             const int v = head(A, j);
-            if (A.pr[v] < r) continue;  // left in an earlier round
-            clique_walk(
-                A, q, u, j, e, v, [&](int y) { return A.pr[y] >= r; },
-                [&](const int *c) {
-                    // counted once: by its smallest member in U_i
-                    for (int t = 1; t < q; t++)
-                        if (c[t] < u && A.pr[c[t]] == r) return;
-                    dead++;
-                    for (int t = 1; t < q; t++)
-                        if (A.pr[c[t]] != r) atomicAdd((unsigned long long *)&A.w[c[t]], (unsigned long long)-1ll);
-                });
+            if (!keep(v)) continue;
+            clique_walk(A, q, u, j, e, v, keep, [&](const int *c) {
+                dead++;
+                for (int t = 1; t < q; t++)
+                    if (A.pr[c[t]] != r) atomicAdd((unsigned long long *)&A.w[c[t]], (unsigned long long)-1ll);
+            });
         }
     }
     for (int d = 16; d > 0; d >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, d);
