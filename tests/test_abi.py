@@ -90,3 +90,28 @@ def test_product_path_does_not_import_oracle():
     for path in glob.glob(os.path.join(ROOT, "paper_2504_09311_gb300", "csrc", "*")):
         src = open(path).read()
         assert "dupin_oracle" not in src and "liboracle" not in src, path
+
+
+def test_binding_constants_match_header():
+    """Every integer #define of include/dupin.h that the binding mirrors has the same value there."""
+    from paper_2504_09311_gb300 import dupin
+
+    src = open(os.path.join(ROOT, "include", "dupin.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define DUPIN_([A-Z0-9_]+)\s+(-?\d+)u?\b", src, re.M)}
+    mirrored = {k: v for k, v in defs.items() if hasattr(dupin, k)}
+    assert len(mirrored) >= 25, sorted(defs)
+    for k, v in mirrored.items():
+        assert getattr(dupin, k) == v, k
+    assert set(dupin.METRICS.values()) == {defs[k] for k in ("DG", "DW", "FD", "TDS", "KCLIDS")}
+
+
+def test_params_field_offsets():
+    """dupin_params as the header lays it out: clique_q after tail_arc_cap."""
+    from paper_2504_09311_gb300 import dupin
+
+    offs = {name: getattr(dupin.Params, name).offset for name, _ in dupin.Params._fields_}
+    assert offs == {"metric": 0, "k_mult": 4, "eps_num": 8, "eps_den": 16, "max_rounds": 24, "flags": 32,
+                    "tail_cap": 36, "tail_arc_cap": 40, "clique_q": 48}
+    p = dupin.make_params("kclids", 5, (1, 10), clique_q=6)
+    assert (p.metric, p.k_mult, p.clique_q) == (dupin.KCLIDS, 5, 6)
+    assert dupin.make_params("fd").clique_q == 0
